@@ -1,0 +1,143 @@
+/*
+ * eik.h -- C ABI of the GB300 (sm_103a) exactly monotone Eikonal solver.
+ *
+ * What it computes (arXiv 2103.05694, Henriksen, You, Pingali):
+ *   the arrival times t of the Dirichlet problem ||grad t|| = 1/v (Eq.
+ *   eikonal_bvp) discretised by the first-order upwind scheme (Eq.
+ *   finite_difference), i.e. the unique fixed point of the local update
+ *   operator (Theorem 1), where the operator is evaluated with the paper's
+ *   exactly monotone rounding d-bar (section "Achieving Exact Monotonicity
+ *   with Finite Precision Arithmetic"):
+ *
+ *     for a non-source cell n with axis minima a_k = min(t[n - e_k], t[n + e_k])
+ *     (off-grid neighbours count as +inf), r = fl(h / v_n), c = fl(r * r):
+ *       G(tau) = fl(fl(q_x + q_y) + q_z),  q_k = fl(m_k * m_k),
+ *       m_k = max(fl(tau - a_k), +0),
+ *       t[n] = the smallest binary64 tau with G(tau) >= c  (+inf if all a_k = +inf).
+ *   Source cells keep their given time t0 (duplicates: the smallest).
+ *
+ * The fixed point is reached by asynchronous relaxed-priority scheduling
+ * (Algorithm 6, "Asynchronous Marching Method"): a persistent CUDA kernel pops
+ * tiles of cells from integer buckets floor(t / delta) and relaxes them.
+ * Because d-bar is exactly monotone and causal, every schedule gives the same
+ * bits (Theorem 1); the result equals a single-threaded fast marching method
+ * (Algorithm 2) with the same d-bar bit for bit.
+ *
+ * Layout: every grid is C-order with x (the last dimension) contiguous;
+ * dims = {ny, nx} for ndim = 2 and {nz, ny, nx} for ndim = 3.  Terms of G are
+ * summed in axis order x, y, z.  Sources are flat C-order cell indices.
+ *
+ * Memory: pointer arguments may be device pointers (cudaMalloc, torch CUDA
+ * tensors) or host pointers (pageable or pinned); each is classified with
+ * cudaPointerGetAttributes.  Host inputs are copied to the device and host
+ * outputs copied back inside the call.  The caller owns every buffer it
+ * passes; the library owns its workspace (device scratch sized to the largest
+ * problem seen, kept per device until eik_release()).
+ *
+ * Streams: work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream).  Calls return after the stream has reached the end of the call's
+ * work (the status is read back from the device); they are not thread-safe
+ * against each other (a process-wide lock serialises them).
+ *
+ * Errors: inputs are checked on the host before launch where the data is
+ * host-visible (EIK_EINVAL, nothing launched), and on the device otherwise
+ * (speed <= 0, non-finite speed or h/v, source index out of range, negative or
+ * NaN source time: EIK_EINVAL, out_t contents unspecified).  A device wait
+ * that exceeds its limit ends the kernel with EIK_ETIMEOUT; it never traps.
+ * A frontier overflow is retried internally with a larger capacity; it is
+ * reported (EIK_ECAPACITY) only when the capacity limit is reached.
+ */
+#ifndef EIK_H
+#define EIK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EIK_OK = 0,
+    EIK_EINVAL = 1,     /* bad argument (host check) or bad input data (device check) */
+    EIK_ENOMEM = 2,     /* device or pinned-host allocation failed */
+    EIK_ECAPACITY = 3,  /* frontier overflow at the largest allowed capacity */
+    EIK_ETIMEOUT = 4,   /* a device wait reached its limit; the kernel returned */
+    EIK_ECUDA = 5       /* a CUDA runtime call failed (message: eik_last_error()) */
+} eik_status;
+
+/* Tuning knobs.  Zero (or a NULL pointer) selects the default / autotuned value. */
+typedef struct {
+    double delta;          /* bucket width in time units; <= 0: auto (k_delta * mean h/v) */
+    double k_delta;        /* auto bucket width in cell travel times; <= 0: default */
+    int64_t capacity;      /* initial frontier ring capacity per bucket slot; 0: auto */
+    int64_t timeout_ms;    /* limit of any single device wait; 0: 60000 */
+    int ctas_per_sm;       /* persistent CTAs per SM; 0: occupancy-derived default */
+    int counters;          /* nonzero: collect eik_stats counters (small cost) */
+    int test_stall;        /* testing aid, keep 0: the solve first waits on a device flag
+                              that nothing sets, so the wait reaches timeout_ms and the
+                              call returns EIK_ETIMEOUT (exercises the bounded waits) */
+    int reserved;
+} eik_opts;
+
+/* Work accounting (the paper's good/empty/bad updates, Results section). */
+typedef struct {
+    int64_t evals;         /* operator applications (cells flagged for update) */
+    int64_t decreases;     /* applications that lowered a value (good + bad) */
+    int64_t good;          /* reached non-source cells (one final-setting update each) */
+    int64_t visits;        /* tile visits by the persistent kernel */
+    int64_t pushes;        /* frontier entries pushed */
+    int64_t stale_pops;    /* frontier entries dropped as stale */
+    int64_t rounds;        /* relaxation rounds summed over tile visits */
+    int64_t retries;       /* capacity retries performed */
+} eik_stats;
+
+/* Solve one grid (Algorithm 6 with d-bar, result identical to Algorithm 2).
+ *   speed   [N] float64, v > 0 finite (device or host)
+ *   h       grid spacing, > 0 finite
+ *   ndim    2 or 3; dims[ndim] C-order extents, each >= 1, product N < 2^40
+ *   src_idx [nsrc] int64 flat indices in [0, N); src_t [nsrc] float64 >= 0
+ *           (NULL: all 0); nsrc >= 0 (0 leaves every cell at +inf)
+ *   out_t   [N] float64 arrival times (written; +inf where unreachable)
+ *   opts    NULL for defaults; stats NULL if not wanted.
+ */
+eik_status eik_solve(const double *speed, double h, int ndim, const int64_t *dims,
+                     const int64_t *src_idx, const double *src_t, int64_t nsrc,
+                     double *out_t, const eik_opts *opts, eik_stats *stats, void *stream);
+
+/* One problem of a batch.  All pointers of one batch must be of one kind:
+ * all device pointers (the batched path does not stage host memory).
+ * Problems may share a speed array. */
+typedef struct {
+    const double *speed;
+    double h;
+    int ndim;
+    int64_t dims[3];
+    const int64_t *src_idx;
+    const double *src_t;   /* NULL: all sources at 0 */
+    int64_t nsrc;
+    double *out_t;
+} eik_problem;
+
+/* Solve nprob independent problems in ONE persistent launch: tiles of every
+ * problem share the bucket scheduler (batching of sources and uneven grids).
+ * stats (optional) accumulates over the batch. */
+eik_status eik_solve_batched(const eik_problem *probs, int nprob, const eik_opts *opts,
+                             eik_stats *stats, void *stream);
+
+/* Release the library's device workspace on the current device. */
+void eik_release(void);
+
+/* Human-readable name of a status code (static string). */
+const char *eik_status_str(eik_status s);
+
+/* Message of the last EIK_ECUDA / EIK_EINVAL of this process (static buffer). */
+const char *eik_last_error(void);
+
+/* Version of the ABI (major * 100 + minor). */
+int eik_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EIK_H */

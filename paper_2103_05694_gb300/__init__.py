@@ -1,0 +1,239 @@
+"""GB300 (sm_103a) exactly monotone Eikonal solver: Python binding of include/eik.h.
+
+The binding only marshals arguments to the C ABI of ``_libeik.so`` (built in
+tree by ``build.py``); every step of the solve runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  If the library is
+missing, importing the binding's functions raises instead of falling back to
+anything else.
+
+Names follow the C ABI: ``eik_solve``, ``eik_solve_batched``,
+``eik_status_str``, ``eik_release``; ``solve`` and ``solve_batched`` are the
+same calls taking tensors/arrays and returning the arrival times.
+
+Method: arXiv 2103.05694 (Henriksen, You, Pingali), Algorithm 6 with the
+exactly monotone rounding d-bar; result identical to Algorithm 2 (FMM) with
+the same rounding (Theorem 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_libeik.so")
+
+EIK_OK, EIK_EINVAL, EIK_ENOMEM, EIK_ECAPACITY, EIK_ETIMEOUT, EIK_ECUDA = range(6)
+
+
+class EikOpts(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("k_delta", ctypes.c_double),
+                ("capacity", ctypes.c_int64), ("timeout_ms", ctypes.c_int64),
+                ("ctas_per_sm", ctypes.c_int), ("counters", ctypes.c_int),
+                ("test_stall", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+class EikStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in
+                ("evals", "decreases", "good", "visits", "pushes", "stale_pops", "rounds",
+                 "retries")]
+
+    def as_dict(self) -> dict:
+        d = {n: int(getattr(self, n)) for n, _ in self._fields_}
+        d["empty"] = d["evals"] - d["decreases"]
+        d["bad"] = d["decreases"] - d["good"]
+        return d
+
+
+class EikProblem(ctypes.Structure):
+    _fields_ = [("speed", ctypes.c_void_p), ("h", ctypes.c_double), ("ndim", ctypes.c_int),
+                ("dims", ctypes.c_int64 * 3), ("src_idx", ctypes.c_void_p),
+                ("src_t", ctypes.c_void_p), ("nsrc", ctypes.c_int64),
+                ("out_t", ctypes.c_void_p)]
+
+
+class EikError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{eik_status_str(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load _libeik.so (the CUDA path).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2103_05694_gb300.build` (needs nvcc)")
+    L = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    L.eik_solve.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp, vp, vp, i64, vp,
+                            ctypes.POINTER(EikOpts), ctypes.POINTER(EikStats), vp]
+    L.eik_solve.restype = ctypes.c_int
+    L.eik_solve_batched.argtypes = [ctypes.POINTER(EikProblem), ctypes.c_int,
+                                    ctypes.POINTER(EikOpts), ctypes.POINTER(EikStats), vp]
+    L.eik_solve_batched.restype = ctypes.c_int
+    L.eik_release.argtypes = []
+    L.eik_release.restype = None
+    L.eik_status_str.argtypes = [ctypes.c_int]
+    L.eik_status_str.restype = ctypes.c_char_p
+    L.eik_last_error.argtypes = []
+    L.eik_last_error.restype = ctypes.c_char_p
+    L.eik_abi_version.argtypes = []
+    L.eik_abi_version.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
+            "eik_abi_version"]
+
+
+def eik_status_str(status: int) -> str:
+    return load_library().eik_status_str(int(status)).decode()
+
+
+def eik_last_error() -> str:
+    return load_library().eik_last_error().decode()
+
+
+def eik_release() -> None:
+    load_library().eik_release()
+
+
+def eik_abi_version() -> int:
+    return int(load_library().eik_abi_version())
+
+
+def _make_opts(opts: dict | None) -> EikOpts | None:
+    if not opts:
+        return None
+    o = EikOpts()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    return o
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def eik_solve(speed_ptr: int, h: float, ndim: int, dims, src_ptr: int | None,
+              src_t_ptr: int | None, nsrc: int, out_ptr: int, opts: dict | None = None,
+              stream: int | None = None) -> dict:
+    """Raw call: pointers are integers (device or host addresses)."""
+    L = load_library()
+    d = (ctypes.c_int64 * ndim)(*[int(x) for x in dims])
+    st = EikStats()
+    o = _make_opts(opts)
+    rc = L.eik_solve(speed_ptr, float(h), int(ndim), d, src_ptr, src_t_ptr, int(nsrc), out_ptr,
+                     ctypes.byref(o) if o is not None else None, ctypes.byref(st), stream)
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    return st.as_dict()
+
+
+def _ptr(x):
+    """Address of a contiguous torch tensor or numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+@dataclass
+class SolveResult:
+    t: object          # torch tensor or numpy array, same kind and device as `out`/speed
+    stats: dict
+
+
+def solve(speed, h: float, sources, src_t=None, out=None, opts: dict | None = None,
+          stream=None) -> SolveResult:
+    """Arrival times on a 2D/3D grid.  ``speed`` is a float64 torch tensor (any
+    device) or numpy array, C-contiguous; ``sources`` flat int64 indices (same
+    kind); ``out`` optional preallocated float64 output."""
+    is_np = isinstance(speed, np.ndarray)
+    if is_np:
+        speed = np.ascontiguousarray(speed, dtype=np.float64)
+        src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).reshape(-1))
+        st = None if src_t is None else np.ascontiguousarray(np.asarray(src_t, np.float64).reshape(-1))
+        if out is None:
+            out = np.empty(speed.shape, dtype=np.float64)
+    else:
+        import torch
+        if speed.dtype != torch.float64 or not speed.is_contiguous():
+            raise ValueError("speed must be a contiguous float64 tensor")
+        src = sources if isinstance(sources, torch.Tensor) else torch.as_tensor(
+            np.asarray(sources, dtype=np.int64))
+        src = src.to(device=speed.device, dtype=torch.int64).contiguous().reshape(-1)
+        st = None
+        if src_t is not None:
+            st = src_t if isinstance(src_t, torch.Tensor) else torch.as_tensor(
+                np.asarray(src_t, dtype=np.float64))
+            st = st.to(device=speed.device, dtype=torch.float64).contiguous().reshape(-1)
+        if out is None:
+            out = torch.empty_like(speed)
+    stats = eik_solve(_ptr(speed), h, speed.ndim, speed.shape, _ptr(src), _ptr(st),
+                      int(src.shape[0]), _ptr(out), opts, _stream_handle(stream) if not is_np
+                      else None)
+    return SolveResult(out, stats)
+
+
+def eik_solve_batched(problems: list[dict], opts: dict | None = None, stream=None) -> dict:
+    """Batched call.  Each problem dict holds torch CUDA tensors: speed, sources,
+    optional src_t, out, and h.  All problems run in one persistent launch."""
+    L = load_library()
+    arr = (EikProblem * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        sp = p["speed"]
+        arr[i].speed = _ptr(sp)
+        arr[i].h = float(p["h"])
+        arr[i].ndim = sp.ndim
+        for k in range(3):
+            arr[i].dims[k] = int(sp.shape[k]) if k < sp.ndim else 1
+        arr[i].src_idx = _ptr(p["sources"])
+        arr[i].src_t = _ptr(p.get("src_t"))
+        arr[i].nsrc = int(p["sources"].numel())
+        arr[i].out_t = _ptr(p["out"])
+        keep.append(p)
+    st = EikStats()
+    o = _make_opts(opts)
+    rc = L.eik_solve_batched(arr, len(problems), ctypes.byref(o) if o is not None else None,
+                             ctypes.byref(st), _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    return st.as_dict()
+
+
+def solve_batched(problems: list[dict], opts: dict | None = None, stream=None) -> dict:
+    """Like eik_solve_batched, allocating ``out`` where missing."""
+    import torch
+    for p in problems:
+        if p.get("out") is None:
+            p["out"] = torch.empty_like(p["speed"])
+        src = p["sources"]
+        if not isinstance(src, torch.Tensor):
+            src = torch.as_tensor(np.asarray(src, dtype=np.int64))
+        p["sources"] = src.to(device=p["speed"].device, dtype=torch.int64).contiguous()
+        if p.get("src_t") is not None and not isinstance(p["src_t"], torch.Tensor):
+            p["src_t"] = torch.as_tensor(np.asarray(p["src_t"], np.float64)).to(p["speed"].device)
+    return eik_solve_batched(problems, opts, stream)

@@ -1,0 +1,518 @@
+// Host side of the C ABI declared in include/eik.h: argument checks, the
+// per-device workspace, host<->device staging, launch sequence, capacity
+// retries and status read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/eik.h"
+#include "eik_internal.h"
+
+namespace {
+
+using eik::Ctl;
+using eik::Prob;
+using eik::SeedItem;
+using eik::SolveParams;
+
+std::mutex g_mu;
+char g_err[512] = "";
+
+void set_err(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+constexpr int64_t kMaxCells = int64_t(1) << 40;
+constexpr uint64_t kMaxCapEntries = uint64_t(1) << 30;   // whole ring storage limit
+constexpr double kDefaultKDelta = 16.0;
+constexpr int kMaxRetries = 4;
+
+// Grow-only device buffer.
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t want) {
+    if (want <= n && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(want, 1) * sizeof(T));
+    if (e == cudaSuccess) n = std::max<size_t>(want, 1);
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+struct Workspace {
+  int device = -1;
+  DevBuf<double> r;            // fl(h/v) per cell, all problems
+  DevBuf<double> t_stage;      // host out_t staging
+  DevBuf<double> v_stage;      // host speed staging
+  DevBuf<unsigned long long> state;
+  DevBuf<unsigned char> tile_src;
+  DevBuf<unsigned long long> slots;
+  DevBuf<int64_t> src_idx;
+  DevBuf<double> src_t;
+  DevBuf<SeedItem> seeds;
+  DevBuf<Prob> probs;
+  DevBuf<Ctl> ctl;
+  DevBuf<unsigned long long> count;
+  Ctl *ctl_host = nullptr;     // pinned
+  bool slots_dirty = true;
+  uint64_t cap = 0;            // entries per slot
+
+  void release_all() {
+    r.release(); t_stage.release(); v_stage.release(); state.release(); tile_src.release();
+    slots.release(); src_idx.release(); src_t.release(); seeds.release(); probs.release();
+    ctl.release(); count.release();
+    if (ctl_host) cudaFreeHost(ctl_host);
+    ctl_host = nullptr;
+    slots_dirty = true;
+    cap = 0;
+    device = -1;
+  }
+};
+
+Workspace g_ws;
+
+eik_status cuda_fail(cudaError_t e, const char *what) {
+  set_err("%s: %s", what, cudaGetErrorString(e));
+  return EIK_ECUDA;
+}
+
+#define CK(call, what)                                            \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      if (e_ == cudaErrorMemoryAllocation) {                      \
+        set_err("%s: %s", what, cudaGetErrorString(e_));          \
+        cudaGetLastError();                                       \
+        return EIK_ENOMEM;                                        \
+      }                                                           \
+      return cuda_fail(e_, what);                                 \
+    }                                                             \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+struct HostProblem {
+  const double *speed;
+  bool speed_dev;
+  double h;
+  int ndim;
+  int64_t dims[3];
+  int64_t n;
+  std::vector<int64_t> src;    // sorted unique
+  std::vector<double> t0;
+  double *out;
+  bool out_dev;
+};
+
+eik_status check_problem(const double *speed, double h, int ndim, const int64_t *dims,
+                         const int64_t *src_idx, const double *src_t, int64_t nsrc,
+                         double *out_t, HostProblem &hp, cudaStream_t stream) {
+  if (ndim != 2 && ndim != 3) { set_err("ndim must be 2 or 3 (got %d)", ndim); return EIK_EINVAL; }
+  if (!dims) { set_err("dims is NULL"); return EIK_EINVAL; }
+  int64_t n = 1;
+  for (int k = 0; k < ndim; ++k) {
+    if (dims[k] < 1) { set_err("dims[%d] = %lld < 1", k, (long long)dims[k]); return EIK_EINVAL; }
+    if (dims[k] > kMaxCells || n > kMaxCells / dims[k]) { set_err("grid too large"); return EIK_EINVAL; }
+    n *= dims[k];
+  }
+  if (!(h > 0.0) || !std::isfinite(h)) { set_err("h must be finite and > 0"); return EIK_EINVAL; }
+  if (!speed || !out_t) { set_err("speed and out_t must not be NULL"); return EIK_EINVAL; }
+  if (nsrc < 0 || (nsrc > 0 && !src_idx)) { set_err("bad source arguments"); return EIK_EINVAL; }
+  hp.speed = speed;
+  hp.speed_dev = is_device_ptr(speed);
+  hp.h = h;
+  hp.ndim = ndim;
+  hp.dims[0] = hp.dims[1] = hp.dims[2] = 1;
+  for (int k = 0; k < ndim; ++k) hp.dims[3 - ndim + k] = dims[k];
+  hp.n = n;
+  hp.out = out_t;
+  hp.out_dev = is_device_ptr(out_t);
+  std::vector<int64_t> idx(static_cast<size_t>(nsrc));
+  std::vector<double> tt(static_cast<size_t>(nsrc), 0.0);
+  if (nsrc > 0) {
+    if (is_device_ptr(src_idx)) {
+      CK(cudaMemcpyAsync(idx.data(), src_idx, nsrc * sizeof(int64_t), cudaMemcpyDeviceToHost, stream),
+         "copy src_idx");
+    } else {
+      std::memcpy(idx.data(), src_idx, nsrc * sizeof(int64_t));
+    }
+    if (src_t) {
+      if (is_device_ptr(src_t)) {
+        CK(cudaMemcpyAsync(tt.data(), src_t, nsrc * sizeof(double), cudaMemcpyDeviceToHost, stream),
+           "copy src_t");
+      } else {
+        std::memcpy(tt.data(), src_t, nsrc * sizeof(double));
+      }
+    }
+    CK(cudaStreamSynchronize(stream), "sync sources");
+  }
+  std::vector<std::pair<int64_t, double>> st(static_cast<size_t>(nsrc));
+  for (int64_t i = 0; i < nsrc; ++i) {
+    if (idx[i] < 0 || idx[i] >= n) { set_err("source %lld index %lld out of range", (long long)i, (long long)idx[i]); return EIK_EINVAL; }
+    double v = tt[i];
+    if (!(v >= 0.0) || !std::isfinite(v)) { set_err("source %lld time must be finite and >= 0", (long long)i); return EIK_EINVAL; }
+    if (v == 0.0) v = 0.0;   // -0 -> +0
+    st[i] = {idx[i], v};
+  }
+  std::sort(st.begin(), st.end());
+  hp.src.clear();
+  hp.t0.clear();
+  for (auto &e : st) {
+    if (!hp.src.empty() && hp.src.back() == e.first) continue;   // sorted: first is the min
+    hp.src.push_back(e.first);
+    hp.t0.push_back(e.second);
+  }
+  return EIK_OK;
+}
+
+void tile_shape(int ndim, int64_t &tx, int64_t &ty, int64_t &tz) {
+  if (ndim == 3) { tx = eik::kTX3; ty = eik::kTY3; tz = eik::kTZ3; }
+  else { tx = eik::kTX2; ty = eik::kTY2; tz = 1; }
+}
+
+eik_status ensure_device() {
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  if (g_ws.device != dev) {
+    if (g_ws.device >= 0) g_ws.release_all();
+    g_ws.device = dev;
+  }
+  if (!g_ws.ctl_host) {
+    CK(cudaMallocHost(&g_ws.ctl_host, sizeof(Ctl)), "pinned control block");
+  }
+  return EIK_OK;
+}
+
+// The whole solve for a list of host-checked problems (1 = eik_solve).
+eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *stats,
+               cudaStream_t stream) {
+  eik_status st = ensure_device();
+  if (st != EIK_OK) return st;
+  const int ndim = hps[0].ndim;
+  for (auto &hp : hps) {
+    if (hp.ndim != ndim) { set_err("all problems of a batch must have the same ndim"); return EIK_EINVAL; }
+  }
+  int64_t tx, ty, tz;
+  tile_shape(ndim, tx, ty, tz);
+  // distinct speed arrays share one r array
+  std::vector<const double *> speeds;
+  std::vector<int64_t> speed_off, speed_n;
+  std::vector<double> speed_h;
+  std::vector<int> prob_speed(hps.size());
+  int64_t r_total = 0;
+  for (size_t i = 0; i < hps.size(); ++i) {
+    int found = -1;
+    for (size_t j = 0; j < speeds.size(); ++j)
+      if (speeds[j] == hps[i].speed && speed_n[j] == hps[i].n && speed_h[j] == hps[i].h) found = (int)j;
+    if (found < 0) {
+      found = (int)speeds.size();
+      speeds.push_back(hps[i].speed);
+      speed_off.push_back(r_total);
+      speed_n.push_back(hps[i].n);
+      speed_h.push_back(hps[i].h);
+      r_total += hps[i].n;
+    }
+    prob_speed[i] = found;
+  }
+  // tiles and sources
+  std::vector<Prob> probs(hps.size());
+  std::vector<SeedItem> seeds;
+  int64_t total_tiles = 0, total_src = 0, host_out_cells = 0, host_speed_cells = 0;
+  for (auto &hp : hps) {
+    total_src += (int64_t)hp.src.size();
+    if (!hp.out_dev) host_out_cells += hp.n;
+  }
+  for (size_t j = 0; j < speeds.size(); ++j) {
+    const HostProblem *owner = nullptr;
+    for (size_t i = 0; i < hps.size(); ++i) if (prob_speed[i] == (int)j) { owner = &hps[i]; break; }
+    if (!owner->speed_dev) host_speed_cells += speed_n[j];
+  }
+  CK(g_ws.r.ensure((size_t)r_total), "alloc r");
+  CK(g_ws.src_idx.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc src_idx");
+  CK(g_ws.src_t.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc src_t");
+  CK(g_ws.seeds.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc seeds");
+  CK(g_ws.probs.ensure(hps.size()), "alloc probs");
+  CK(g_ws.ctl.ensure(1), "alloc ctl");
+  CK(g_ws.count.ensure(1), "alloc count");
+  if (host_out_cells) CK(g_ws.t_stage.ensure((size_t)host_out_cells), "alloc t staging");
+  if (host_speed_cells) CK(g_ws.v_stage.ensure((size_t)host_speed_cells), "alloc speed staging");
+
+  std::vector<int64_t> all_src;
+  std::vector<double> all_t0;
+  all_src.reserve((size_t)total_src);
+  all_t0.reserve((size_t)total_src);
+  int64_t out_stage_off = 0;
+  for (size_t i = 0; i < hps.size(); ++i) {
+    HostProblem &hp = hps[i];
+    Prob &P = probs[i];
+    P.nx = hp.dims[2];
+    P.ny = hp.dims[1];
+    P.nz = hp.dims[0];
+    P.ntx = (P.nx + tx - 1) / tx;
+    P.nty = (P.ny + ty - 1) / ty;
+    P.ntz = (P.nz + tz - 1) / tz;
+    P.tile_base = total_tiles;
+    total_tiles += P.ntx * P.nty * P.ntz;
+    P.r = g_ws.r.p + speed_off[prob_speed[i]];
+    if (hp.out_dev) {
+      P.t = hp.out;
+    } else {
+      P.t = g_ws.t_stage.p + out_stage_off;
+      out_stage_off += hp.n;
+    }
+    P.src_idx = g_ws.src_idx.p + all_src.size();
+    P.src_t = g_ws.src_t.p + all_src.size();
+    P.nsrc = (int64_t)hp.src.size();
+    for (size_t k = 0; k < hp.src.size(); ++k) {
+      seeds.push_back(SeedItem{(int64_t)i, hp.src[k], hp.t0[k]});
+      all_src.push_back(hp.src[k]);
+      all_t0.push_back(hp.t0[k]);
+    }
+  }
+  if (total_tiles >= (int64_t(1) << 32)) { set_err("too many tiles"); return EIK_EINVAL; }
+  CK(g_ws.state.ensure((size_t)total_tiles), "alloc tile state");
+  CK(g_ws.tile_src.ensure((size_t)total_tiles), "alloc tile flags");
+
+  // frontier capacity per bucket slot
+  uint64_t want_cap = opts && opts->capacity > 0 ? (uint64_t)opts->capacity
+                                                 : (uint64_t)total_tiles / 4 + 4096;
+  want_cap = next_pow2(std::max<uint64_t>(want_cap, opts && opts->capacity > 0 ? 16 : 1024));
+  while (want_cap * eik::kNumSlots > kMaxCapEntries && want_cap > 1024) want_cap >>= 1;
+  // the ring layout depends on cap; storage only grows.  A clean solve leaves
+  // every entry EMPTY, so changing cap needs no clearing unless dirty.
+  if (g_ws.slots.n < want_cap * eik::kNumSlots) {
+    CK(g_ws.slots.ensure((size_t)(want_cap * eik::kNumSlots)), "alloc frontier");
+    g_ws.slots_dirty = true;
+  }
+  g_ws.cap = want_cap;
+
+  // uploads
+  if (!all_src.empty()) {
+    CK(cudaMemcpyAsync(g_ws.src_idx.p, all_src.data(), all_src.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, stream), "upload sources");
+    CK(cudaMemcpyAsync(g_ws.src_t.p, all_t0.data(), all_t0.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, stream), "upload source times");
+    CK(cudaMemcpyAsync(g_ws.seeds.p, seeds.data(), seeds.size() * sizeof(SeedItem),
+                       cudaMemcpyHostToDevice, stream), "upload seeds");
+  }
+  CK(cudaMemcpyAsync(g_ws.probs.p, probs.data(), probs.size() * sizeof(Prob),
+                     cudaMemcpyHostToDevice, stream), "upload problems");
+  CK(cudaMemsetAsync(g_ws.ctl.p, 0, sizeof(Ctl), stream), "clear control block");
+  CK(cudaMemsetAsync(g_ws.state.p, 0, (size_t)total_tiles * sizeof(unsigned long long), stream),
+     "clear tile states");
+  CK(cudaMemsetAsync(g_ws.tile_src.p, 0, (size_t)total_tiles, stream), "clear tile flags");
+  if (g_ws.slots_dirty) {
+    CK(cudaMemsetAsync(g_ws.slots.p, 0xff, g_ws.slots.n * sizeof(unsigned long long), stream),
+       "clear frontier");
+    g_ws.slots_dirty = false;
+  }
+
+  // r = h / v (staging host speeds first)
+  int64_t v_off = 0;
+  for (size_t j = 0; j < speeds.size(); ++j) {
+    const HostProblem *owner = nullptr;
+    for (size_t i = 0; i < hps.size(); ++i) if (prob_speed[i] == (int)j) { owner = &hps[i]; break; }
+    const double *vsrc = speeds[j];
+    if (!owner->speed_dev) {
+      CK(cudaMemcpyAsync(g_ws.v_stage.p + v_off, vsrc, speed_n[j] * sizeof(double),
+                         cudaMemcpyHostToDevice, stream), "upload speed");
+      vsrc = g_ws.v_stage.p + v_off;
+      v_off += speed_n[j];
+    }
+    CK(eik::launch_init_r(vsrc, speed_h[j], g_ws.r.p + speed_off[j], speed_n[j], g_ws.ctl.p, stream),
+       "init_r launch");
+  }
+  for (auto &P : probs) CK(eik::launch_init_t(P.t, P.nx * P.ny * P.nz, stream), "init_t launch");
+
+  SolveParams sp;
+  sp.probs = g_ws.probs.p;
+  sp.nprob = (int)probs.size();
+  sp.ndim = ndim;
+  sp.state = g_ws.state.p;
+  sp.tile_src = g_ws.tile_src.p;
+  sp.slots = g_ws.slots.p;
+  sp.cap_mask = (unsigned)(g_ws.cap - 1);
+  sp.ctl = g_ws.ctl.p;
+  const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
+  sp.timeout_ns = tmo_ms * 1000000ll;
+  sp.counters = opts ? opts->counters : 0;
+  sp.test_stall = opts ? opts->test_stall : 0;
+  const double k_delta = opts && opts->k_delta > 0 ? opts->k_delta : kDefaultKDelta;
+  const double delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
+
+  CK(eik::launch_seed(sp, g_ws.seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
+     "seed launch");
+  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : 0;
+  const int occ = eik::persistent_blocks_per_sm(ndim);
+  if (per_sm <= 0 || per_sm > occ) per_sm = occ;
+  int dev_sms = 0;
+  CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g_ws.device), "SM count");
+  int64_t grid = (int64_t)dev_sms * per_sm;
+  if (grid > total_tiles) grid = total_tiles;
+  if (grid < 1) grid = 1;
+
+  eik_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  unsigned status = 0;
+  for (int attempt = 0;; ++attempt) {
+    CK(eik::launch_persistent(sp, (int)grid, stream), "solve launch");
+    CK(cudaMemcpyAsync(g_ws.ctl_host, g_ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, stream),
+       "read status");
+    CK(cudaStreamSynchronize(stream), "solve");
+    const Ctl &c = *g_ws.ctl_host;
+    status = c.status;
+    acc.evals += (int64_t)c.stats[eik::kStatEvals];
+    acc.decreases += (int64_t)c.stats[eik::kStatDecreases];
+    acc.visits += (int64_t)c.stats[eik::kStatVisits];
+    acc.pushes += (int64_t)c.stats[eik::kStatPushes];
+    acc.stale_pops += (int64_t)c.stats[eik::kStatStale];
+    acc.rounds += (int64_t)c.stats[eik::kStatRounds];
+    if (status != eik::kEcapacity || attempt >= kMaxRetries ||
+        g_ws.cap * 4 * eik::kNumSlots > kMaxCapEntries) break;
+    // grow the frontier, clear the scheduler (keep delta) and resume
+    g_ws.slots_dirty = true;
+    const uint64_t ncap = g_ws.cap * 4;
+    CK(g_ws.slots.ensure((size_t)(ncap * eik::kNumSlots)), "grow frontier");
+    g_ws.cap = ncap;
+    sp.slots = g_ws.slots.p;
+    sp.cap_mask = (unsigned)(ncap - 1);
+    CK(cudaMemsetAsync(g_ws.slots.p, 0xff, g_ws.slots.n * sizeof(unsigned long long), stream),
+       "clear frontier");
+    g_ws.slots_dirty = false;
+    CK(cudaMemsetAsync(g_ws.ctl.p, 0, offsetof(Ctl, rsum), stream), "clear scheduler");
+    CK(cudaMemsetAsync(&g_ws.ctl.p->stats[0], 0, sizeof(Ctl) - offsetof(Ctl, stats), stream),
+       "clear counters");
+    CK(cudaMemsetAsync(g_ws.state.p, 0, (size_t)total_tiles * sizeof(unsigned long long), stream),
+       "clear tile states");
+    CK(eik::launch_reseed(sp, probs.data(), (int)probs.size(), stream), "reseed launch");
+    acc.retries++;
+  }
+  if (status != 0) {
+    g_ws.slots_dirty = true;
+    const Ctl &c = *g_ws.ctl_host;
+    if (status == eik::kEinval) {
+      set_err("invalid input data (cell %llu: speed must be finite and > 0, h/v finite and > 0)",
+              (unsigned long long)c.error_info[0]);
+      return EIK_EINVAL;
+    }
+    if (status == eik::kEtimeout) {
+      set_err("device wait timed out (site %llu)", (unsigned long long)c.error_info[0]);
+      return EIK_ETIMEOUT;
+    }
+    if (status == eik::kEcapacity) {
+      set_err("frontier capacity exhausted");
+      return EIK_ECAPACITY;
+    }
+    set_err("device status %u", status);
+    return EIK_ECUDA;
+  }
+  if (sp.counters) {
+    CK(cudaMemsetAsync(g_ws.count.p, 0, sizeof(unsigned long long), stream), "clear count");
+    CK(eik::launch_count_finite(probs.data(), (int)probs.size(), g_ws.count.p, stream), "count");
+    unsigned long long finite = 0;
+    CK(cudaMemcpyAsync(&finite, g_ws.count.p, sizeof(finite), cudaMemcpyDeviceToHost, stream),
+       "read count");
+    CK(cudaStreamSynchronize(stream), "count");
+    acc.good = (int64_t)finite - total_src;
+  }
+  // host outputs
+  for (size_t i = 0; i < hps.size(); ++i) {
+    if (!hps[i].out_dev) {
+      CK(cudaMemcpyAsync(hps[i].out, probs[i].t, hps[i].n * sizeof(double), cudaMemcpyDeviceToHost,
+                         stream), "download t");
+    }
+  }
+  CK(cudaStreamSynchronize(stream), "download");
+  if (stats) *stats = acc;
+  return EIK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eik_status eik_solve(const double *speed, double h, int ndim, const int64_t *dims,
+                     const int64_t *src_idx, const double *src_t, int64_t nsrc, double *out_t,
+                     const eik_opts *opts, eik_stats *stats, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<HostProblem> hps(1);
+  eik_status st = check_problem(speed, h, ndim, dims, src_idx, src_t, nsrc, out_t, hps[0], s);
+  if (st != EIK_OK) return st;
+  return run(hps, opts, stats, s);
+}
+
+eik_status eik_solve_batched(const eik_problem *probs, int nprob, const eik_opts *opts,
+                             eik_stats *stats, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (nprob <= 0 || !probs) { set_err("empty batch"); return EIK_EINVAL; }
+  std::vector<HostProblem> hps((size_t)nprob);
+  for (int i = 0; i < nprob; ++i) {
+    const eik_problem &q = probs[i];
+    eik_status st = check_problem(q.speed, q.h, q.ndim, q.dims, q.src_idx, q.src_t, q.nsrc,
+                                  q.out_t, hps[(size_t)i], s);
+    if (st != EIK_OK) return st;
+    if (!hps[(size_t)i].speed_dev || !hps[(size_t)i].out_dev) {
+      set_err("batched problems take device pointers only (problem %d)", i);
+      return EIK_EINVAL;
+    }
+  }
+  return run(hps, opts, stats, s);
+}
+
+void eik_release(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_ws.release_all();
+}
+
+const char *eik_status_str(eik_status s) {
+  switch (s) {
+    case EIK_OK: return "EIK_OK";
+    case EIK_EINVAL: return "EIK_EINVAL";
+    case EIK_ENOMEM: return "EIK_ENOMEM";
+    case EIK_ECAPACITY: return "EIK_ECAPACITY";
+    case EIK_ETIMEOUT: return "EIK_ETIMEOUT";
+    case EIK_ECUDA: return "EIK_ECUDA";
+  }
+  return "EIK_UNKNOWN";
+}
+
+const char *eik_last_error(void) { return g_err; }
+
+int eik_abi_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Internal declarations shared by the CUDA translation units of the Eikonal
+// solver (kernels in eik_solver.cu, host API in eik_api.cu).  Not part of the ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace eik {
+
+// Bucket ring: NB slots; bucket b lives in slot b & (NB - 1).  Each slot is a
+// ring of `cap` 64-bit entries (cap a power of two), EMPTY when free.
+constexpr uint32_t kNumSlots = 128;
+constexpr uint64_t kEmpty = ~0ull;
+constexpr uint32_t kMaxBucket = (1u << 30) - 1;
+constexpr int kCounterPad = 16;          // u32 counters padded to 64 bytes
+
+// Tile state word: bits 0..29 bucket, bits 32..38 face mask, bits 40..41 status.
+constexpr uint64_t kStIdle = 0, kStQueued = 1, kStRunning = 2, kStDirty = 3;
+constexpr int kFaceFull = 6;             // face bit 6: evaluate every cell
+
+// Device status codes (match eik_status).
+constexpr unsigned kOk = 0, kEinval = 1, kEcapacity = 3, kEtimeout = 4;
+
+enum StatIdx {
+  kStatEvals = 0, kStatDecreases, kStatVisits, kStatPushes, kStatStale, kStatRounds,
+  kStatCommits, kNumStats
+};
+
+// Control block, zeroed before every solve.
+struct Ctl {
+  int work;                 // frontier entries pushed and not yet finished
+  int pad0[31];
+  unsigned cur;             // hint: lowest bucket that may be non-empty
+  int pad1[31];
+  unsigned status;          // first error (0 = ok)
+  unsigned done;            // termination detected
+  unsigned never_set;       // stays 0: the stall test waits on it
+  int pad2[29];
+  double rsum;              // sum of r = h/v over all cells (auto bucket width)
+  unsigned long long rcount;
+  double delta;             // bucket width used
+  double inv_delta;
+  int pad3[24];
+  unsigned long long stats[kNumStats];
+  unsigned long long error_info[4];   // where a wait gave up / what was invalid
+  unsigned push[kNumSlots * kCounterPad];
+  unsigned pop[kNumSlots * kCounterPad];
+};
+
+// One grid of a (possibly batched) solve, as the kernels see it.
+struct Prob {
+  double *t;                // arrival times (working field and result)
+  const double *r;          // per cell fl(h / v)
+  const int64_t *src_idx;   // sorted unique source indices (device)
+  const double *src_t;      // their times (device), same order
+  int64_t nsrc;
+  int64_t nx, ny, nz;       // extents (nz = 1 in 2D)
+  int64_t ntx, nty, ntz;    // tiles per axis
+  int64_t tile_base;        // first global tile id of this problem
+};
+
+struct SolveParams {
+  const Prob *probs;
+  int nprob;
+  int ndim;
+  unsigned long long *state;      // per global tile
+  unsigned char *tile_src;        // per global tile: 1 if it holds a source
+  unsigned long long *slots;      // kNumSlots * cap
+  unsigned cap_mask;              // cap - 1
+  Ctl *ctl;
+  long long timeout_ns;
+  int counters;
+  int test_stall;
+};
+
+// Tile shapes (cells): one thread per cell, 256 threads per CTA.
+constexpr int kTX2 = 32, kTY2 = 8;                 // 2D
+constexpr int kTX3 = 16, kTY3 = 4, kTZ3 = 4;       // 3D
+
+// Launch wrappers (eik_solver.cu).  All enqueue on `stream`.
+cudaError_t launch_init_r(const double *speed, double h, double *r, int64_t n, Ctl *ctl,
+                          cudaStream_t stream);
+cudaError_t launch_init_t(double *t, int64_t n, cudaStream_t stream);
+// One source of one problem, flattened over the batch for the seed kernel.
+struct SeedItem {
+  int64_t prob;
+  int64_t idx;
+  double t0;
+};
+
+cudaError_t launch_seed(const SolveParams &p, const SeedItem *items, int64_t nitems,
+                        double k_delta, double delta_fixed, cudaStream_t stream);
+cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int nprob,
+                          cudaStream_t stream);
+cudaError_t launch_persistent(const SolveParams &p, int grid, cudaStream_t stream);
+cudaError_t launch_count_finite(const Prob *host_probs, int nprob, unsigned long long *out,
+                                cudaStream_t stream);
+int persistent_blocks_per_sm(int ndim);
+
+}  // namespace eik

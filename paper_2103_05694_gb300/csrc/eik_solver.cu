@@ -1,0 +1,873 @@
+// Kernels of the exactly monotone Eikonal solver for sm_103a.
+//
+// Method (arXiv 2103.05694): the first-order upwind update (Algorithm 1,
+// Eq. finite_difference) evaluated with the exactly monotone rounding d-bar
+// (section "Achieving Exact Monotonicity with Finite Precision Arithmetic"),
+// applied under asynchronous relaxed-priority scheduling with integer buckets
+// floor(t / delta) (Algorithm 6, the "Asynchronous Marching Method").  Because
+// d-bar is monotone and causal, every schedule reaches the same bits
+// (Theorem 1).
+//
+// GB300 design:
+//  * Work item = a tile of cells (2D 32x8, 3D 16x4x4), one CTA (256 threads,
+//    one cell per thread) relaxes it in shared memory: tile plus a one-cell
+//    halo staged with coalesced relaxed loads, x-neighbours by warp shuffles,
+//    y/z neighbours from shared memory, rounds of Jacobi relaxation driven by
+//    per-cell change stamps until the tile is locally converged.
+//  * Commits are 64-bit atomicMin on the bit pattern of the (non-negative)
+//    arrival time; the minimum committed time on each tile face activates the
+//    neighbour tile across that face (one aggregated push per face).
+//  * Scheduler: persistent kernel; kNumSlots bucket slots, each a ring of
+//    64-bit entries (tile | bucket << 32); warp 0 of a CTA scans 32 slots per
+//    step from the lowest-bucket hint, claims an entry with a CAS on the
+//    slot's pop counter and then claims the tile through its state word
+//    (idle / queued(b) / running / dirty(b)); a stale entry is dropped.
+//    Termination: the count of unfinished entries reaches zero.
+//  * FP64 is scarce on this part (about 1.6 DFMA per SM per clock), so every
+//    comparison, min, max and sign test runs on integer bit patterns, and a
+//    cell is evaluated only when a neighbour changed.
+//  * Every wait is bounded by %globaltimer; on expiry the kernel records
+//    EIK_ETIMEOUT in the control block and returns (no trap).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "eik_internal.h"
+
+namespace eik {
+namespace {
+
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWalk = 6;
+constexpr unsigned kMaxRounds = 1u << 20;   // per tile visit; never reached in practice
+
+__device__ __forceinline__ unsigned long long bits_of(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+__device__ __forceinline__ double from_bits(unsigned long long u) {
+  return __longlong_as_double(static_cast<long long>(u));
+}
+__device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) {
+  return a < b ? a : b;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a < b ? b : a;
+}
+
+// Relaxed, GPU-scope accesses (never served from a stale L1 line).
+__device__ __forceinline__ unsigned ld_rlx(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_rlx(const int *p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_rlx(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_time(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rlx(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_rlx(unsigned *p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ long long now_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ void raise_status(Ctl *ctl, unsigned code, unsigned long long info) {
+  if (atomicCAS(&ctl->status, 0u, code) == 0u) {
+    ctl->error_info[0] = info;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// d-bar.  G(tau) = fl(fl(q_x + q_y) + q_z), q_k = fl(m_k * m_k),
+// m_k = max(fl(tau - a_k), +0): every operation an explicit round-to-nearest
+// intrinsic, so nothing is contracted into an FMA.  a_k = +inf gives
+// m_k = -inf -> +0.  Results are compared as bit patterns (all >= +0).
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ unsigned long long G_bits(double tau, const double (&a)[D]) {
+  double m = __dsub_rn(tau, a[0]);
+  m = (__double_as_longlong(m) < 0) ? 0.0 : m;
+  double g = __dmul_rn(m, m);
+#pragma unroll
+  for (int k = 1; k < D; ++k) {
+    double mk = __dsub_rn(tau, a[k]);
+    mk = (__double_as_longlong(mk) < 0) ? 0.0 : mk;
+    g = __dadd_rn(g, __dmul_rn(mk, mk));
+  }
+  return bits_of(g);
+}
+
+// Smallest double tau with G(tau) >= c, given at least one finite a_k.
+// Guess: one-sided update a_0 + r, else the rearranged quadratic root d-hat
+// (Mitigation Strategies), else its three-axis analogue; then the exact
+// answer by a short ulp walk, with bisection over bit patterns as the
+// fallback.  The guess only affects speed, never the result.
+template <int D>
+__device__ double dbar_dev(const double (&a)[D], double r, double c, unsigned long long cb) {
+  unsigned long long s0 = bits_of(a[0]);
+  unsigned long long s1 = D > 1 ? bits_of(a[1]) : kInfBits;
+  unsigned long long s2 = D > 2 ? bits_of(a[2]) : kInfBits;
+  {  // sort ascending as integers
+    unsigned long long lo = umin64(s0, s1), hi = umax64(s0, s1);
+    s0 = lo;
+    s1 = hi;
+    if (D > 2) {
+      unsigned long long l2 = umin64(s1, s2), h2 = umax64(s1, s2);
+      s2 = h2;
+      s1 = umax64(s0, l2);
+      s0 = umin64(s0, l2);
+    }
+  }
+  const double a0 = from_bits(s0);
+  double g = a0 + r;
+  if (s1 != kInfBits) {
+    const double a1 = from_bits(s1);
+    const double d = a1 - a0;
+    if (d < r) {
+      const double disc = 2.0 * c - d * d;
+      g = 0.5 * (a0 + a1 + sqrt(disc > 0.0 ? disc : 0.0));
+      if (D > 2 && s2 != kInfBits) {
+        const double a2 = from_bits(s2);
+        if (g > a2) {
+          const double u2 = a2 - a0, s = d + u2;
+          const double disc3 = s * s - 3.0 * (d * d + u2 * u2 - c);
+          if (disc3 >= 0.0) g = a0 + (s + sqrt(disc3)) * (1.0 / 3.0);
+        }
+      }
+    }
+  }
+  unsigned long long gb = bits_of(g);
+  if (!(gb > s0) || gb >= kInfBits) gb = s0 + 1;
+  unsigned long long lo, hi;
+  if (G_bits<D>(from_bits(gb), a) >= cb) {
+#pragma unroll 1
+    for (int i = 0; i < kWalk; ++i) {
+      if (gb - 1 <= s0) return from_bits(gb);  // G(a_0) = 0 < c
+      if (G_bits<D>(from_bits(gb - 1), a) < cb) return from_bits(gb);
+      --gb;
+    }
+    hi = gb;
+    lo = s0;
+  } else {
+    lo = gb;
+#pragma unroll 1
+    for (int i = 0; i < kWalk; ++i) {
+      ++gb;
+      if (G_bits<D>(from_bits(gb), a) >= cb) return from_bits(gb);
+      lo = gb;
+    }
+    unsigned long long step = 1;
+    hi = lo + 1;
+#pragma unroll 1
+    while (hi < kInfBits && G_bits<D>(from_bits(hi), a) < cb) {
+      lo = hi;
+      step <<= 1;
+      hi = umin64(lo + step, kInfBits);
+    }
+  }
+  // invariant: G(lo) < c <= G(hi)
+#pragma unroll 1
+  while (hi - lo > 1) {
+    const unsigned long long mid = lo + (hi - lo) / 2;
+    if (G_bits<D>(from_bits(mid), a) >= cb) hi = mid; else lo = mid;
+  }
+  return from_bits(hi);
+}
+
+// One application of the update operator at a non-source cell holding tv.
+// Returns true and the new value if the cell decreases.  A decrease needs a
+// finite neighbour below tv (d-bar > min a_k) and G(prev(tv)) >= c (then
+// d-bar <= prev(tv)); both tests are exact.
+template <int D>
+__device__ __forceinline__ bool relax_cell(double tv, const double (&a)[D], double r,
+                                           double &out) {
+  unsigned long long amin = bits_of(a[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) amin = umin64(amin, bits_of(a[k]));
+  const unsigned long long tb = bits_of(tv);
+  if (amin >= kInfBits || tb <= amin) return false;
+  const double c = __dmul_rn(r, r);
+  const unsigned long long cb = bits_of(c);
+  if (tb < kInfBits && G_bits<D>(from_bits(tb - 1), a) < cb) return false;
+  out = dbar_dev<D>(a, r, c, cb);
+  return true;
+}
+
+__device__ __forceinline__ double min_time(double x, double y) {
+  return from_bits(umin64(bits_of(x), bits_of(y)));
+}
+
+// ---------------------------------------------------------------------------
+// Scheduler.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long make_state(unsigned long long st, unsigned bucket,
+                                                         unsigned faces) {
+  return (st << 40) | (static_cast<unsigned long long>(faces) << 32) | bucket;
+}
+__device__ __forceinline__ unsigned long long state_of(unsigned long long s) { return (s >> 40) & 3ull; }
+__device__ __forceinline__ unsigned bucket_of(unsigned long long s) {
+  return static_cast<unsigned>(s & 0x3fffffffull);
+}
+__device__ __forceinline__ unsigned faces_of(unsigned long long s) {
+  return static_cast<unsigned>((s >> 32) & 0x7full);
+}
+
+__device__ __forceinline__ unsigned bucket_of_time(double t, double inv_delta) {
+  const double q = t * inv_delta;
+  if (!(q < static_cast<double>(kMaxBucket))) return kMaxBucket;
+  return static_cast<unsigned>(q);
+}
+
+// Append (tile, b) to bucket b's slot.  The caller already owns the right to
+// push (it moved the tile's state to queued(b)).
+__device__ bool push_entry(const SolveParams &p, unsigned long long tile, unsigned b) {
+  Ctl *ctl = p.ctl;
+  atomicAdd(&ctl->work, 1);
+  const unsigned s = b & (kNumSlots - 1);
+  const unsigned cap = p.cap_mask + 1u;
+  const unsigned idx = atomicAdd(&ctl->push[s * kCounterPad], 1u);
+  if (idx - ld_rlx(&ctl->pop[s * kCounterPad]) >= cap) {
+    raise_status(ctl, kEcapacity, (static_cast<unsigned long long>(s) << 32) | idx);
+    return false;
+  }
+  unsigned long long *slot = p.slots + static_cast<size_t>(s) * cap + (idx & p.cap_mask);
+  const unsigned long long e = (static_cast<unsigned long long>(b) << 32) | tile;
+  long long t0 = 0;
+  while (atomicCAS(slot, kEmpty, e) != kEmpty) {  // previous lap not consumed yet
+    const long long now = now_ns();
+    if (t0 == 0) t0 = now;
+    else if (now - t0 > p.timeout_ns) { raise_status(ctl, kEcapacity, 1ull << 63); return false; }
+    if (ld_rlx(&ctl->status)) return false;
+    __nanosleep(64);
+  }
+  if (p.counters) atomicAdd(&ctl->stats[kStatPushes], 1ull);
+  return true;
+}
+
+// A face of `tile` has new lower halo values (the smallest in bucket
+// `bucket`): make sure the tile is (re)processed after this point.
+__device__ void activate(const SolveParams &p, unsigned long long tile, unsigned face_bits,
+                         unsigned bucket) {
+  Ctl *ctl = p.ctl;
+  const unsigned cur = ld_rlx(&ctl->cur);
+  unsigned b = bucket;
+  if (b < cur) b = cur;
+  else if (b - cur >= kNumSlots) b = cur + kNumSlots - 1;
+  if (b > kMaxBucket) b = kMaxBucket;
+  unsigned long long old = ld_rlx(&p.state[tile]);
+#pragma unroll 1
+  for (int it = 0; it < (1 << 22); ++it) {
+    const unsigned long long st = state_of(old);
+    const unsigned ob = bucket_of(old), of = faces_of(old);
+    unsigned long long nw;
+    bool need_push = false;
+    if (st == kStIdle) {
+      nw = make_state(kStQueued, b, face_bits);
+      need_push = true;
+    } else if (st == kStQueued) {
+      nw = make_state(kStQueued, b < ob ? b : ob, of | face_bits);
+      need_push = b < ob;
+    } else if (st == kStRunning) {
+      nw = make_state(kStDirty, b, face_bits);
+    } else {
+      nw = make_state(kStDirty, b < ob ? b : ob, of | face_bits);
+    }
+    if (nw == old) return;
+    const unsigned long long prev = atomicCAS(&p.state[tile], old, nw);
+    if (prev == old) {
+      if (need_push) push_entry(p, tile, b);
+      return;
+    }
+    old = prev;
+  }
+  raise_status(ctl, kEtimeout, 3);
+}
+
+// Claim a popped entry: queued(b) -> running.  Returns the face mask, or -1
+// if the entry is stale (the tile was re-queued elsewhere or is done).
+__device__ int try_claim(const SolveParams &p, unsigned long long tile, unsigned b) {
+  unsigned long long old = ld_rlx(&p.state[tile]);
+#pragma unroll 1
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (state_of(old) != kStQueued || bucket_of(old) != b) return -1;
+    const unsigned long long prev = atomicCAS(&p.state[tile], old, make_state(kStRunning, 0, 0));
+    if (prev == old) return static_cast<int>(faces_of(old));
+    old = prev;
+  }
+  raise_status(p.ctl, kEtimeout, 4);
+  return -1;
+}
+
+// End of a visit: running -> idle, or dirty(b) -> queued(b) plus a push.
+__device__ void finish_tile(const SolveParams &p, unsigned long long tile) {
+  unsigned long long old = ld_rlx(&p.state[tile]);
+#pragma unroll 1
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned long long nw;
+    const bool dirty = state_of(old) == kStDirty;
+    nw = dirty ? make_state(kStQueued, bucket_of(old), faces_of(old)) : 0ull;
+    const unsigned long long prev = atomicCAS(&p.state[tile], old, nw);
+    if (prev == old) {
+      if (dirty) push_entry(p, tile, bucket_of(old));
+      return;
+    }
+    old = prev;
+  }
+  raise_status(p.ctl, kEtimeout, 5);
+}
+
+// Wait for the entry at ring position q of slot s, take it, free the slot.
+__device__ unsigned long long take_slot(const SolveParams &p, unsigned s, unsigned q) {
+  unsigned long long *slot =
+      p.slots + static_cast<size_t>(s) * (p.cap_mask + 1u) + (q & p.cap_mask);
+  long long t0 = 0;
+#pragma unroll 1
+  for (;;) {
+    const unsigned long long e = ld_rlx(slot);
+    if (e != kEmpty) {
+      st_rlx(slot, kEmpty);
+      return e;
+    }
+    const long long now = now_ns();
+    if (t0 == 0) t0 = now;
+    else if (now - t0 > p.timeout_ns) { raise_status(p.ctl, kEtimeout, 6); return kEmpty; }
+    if (ld_rlx(&p.ctl->status)) return kEmpty;
+    __nanosleep(32);
+  }
+}
+
+// Warp 0: find the lowest non-empty slot from the hint and take one entry.
+// Returns kEmpty when the solve is over (done or error).
+__device__ unsigned long long pop_entry(const SolveParams &p, long long &idle_since) {
+  Ctl *ctl = p.ctl;
+  const unsigned lane = threadIdx.x & 31u;
+#pragma unroll 1
+  for (;;) {
+    unsigned stop = 0, cur = 0;
+    if (lane == 0) {
+      stop = ld_rlx(&ctl->status) | ld_rlx(&ctl->done);
+      cur = ld_rlx(&ctl->cur);
+    }
+    stop = __shfl_sync(kFull, stop, 0);
+    if (stop) return kEmpty;
+    cur = __shfl_sync(kFull, cur, 0);
+#pragma unroll 1
+    for (unsigned base = 0; base < kNumSlots; base += 32) {
+      const unsigned s = (cur + base + lane) & (kNumSlots - 1);
+      unsigned q = ld_rlx(&ctl->pop[s * kCounterPad]);
+      unsigned pp = ld_rlx(&ctl->push[s * kCounterPad]);
+      unsigned nonempty = __ballot_sync(kFull, static_cast<int>(pp - q) > 0);
+#pragma unroll 1
+      while (nonempty) {
+        const int l = __ffs(nonempty) - 1;
+        unsigned long long e = kEmpty;
+        int got = 0;
+        if (lane == static_cast<unsigned>(l)) {
+#pragma unroll 1
+          while (static_cast<int>(pp - q) > 0) {
+            const unsigned prev = atomicCAS(&ctl->pop[s * kCounterPad], q, q + 1u);
+            if (prev == q) { got = 1; break; }
+            q = prev;
+            pp = ld_rlx(&ctl->push[s * kCounterPad]);
+          }
+          if (got) {
+            const unsigned off = base + lane;
+            if (off > 0 && cur + off <= kMaxBucket) atomicCAS(&ctl->cur, cur, cur + off);
+            e = take_slot(p, s, q);
+          }
+        }
+        got = __shfl_sync(kFull, got, l);
+        if (got) {
+          e = __shfl_sync(kFull, e, l);
+          return e;  // kEmpty here means the solve is being aborted
+        }
+        nonempty &= ~(1u << l);
+      }
+    }
+    int w = 0;
+    if (lane == 0) w = ld_rlx(&ctl->work);
+    w = __shfl_sync(kFull, w, 0);
+    if (w == 0) {
+      if (lane == 0) st_rlx(&ctl->done, 1u);
+      return kEmpty;
+    }
+    if (lane == 0) {
+      const long long now = now_ns();
+      if (idle_since == 0) idle_since = now;
+      else if (now - idle_since > p.timeout_ns) raise_status(ctl, kEtimeout, 2);
+    }
+    __nanosleep(200);
+  }
+}
+
+__device__ __forceinline__ int find_prob(const SolveParams &p, unsigned long long tile) {
+  int lo = 0, hi = p.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (static_cast<unsigned long long>(p.probs[mid].tile_base) <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
+  int64_t lo = 0, hi = P.nsrc - 1;
+  while (lo <= hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    const int64_t v = P.src_idx[mid];
+    if (v == idx) return true;
+    if (v < idx) lo = mid + 1; else hi = mid - 1;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent kernel: pop a tile, relax it to local convergence, commit,
+// activate neighbour tiles, repeat until no work is left anywhere.
+// ---------------------------------------------------------------------------
+template <int D, int TX, int TY, int TZ>
+__global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p) {
+  constexpr int NT = TX * TY * TZ;
+  constexpr int HZ = (D == 3) ? 1 : 0;
+  constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2 * HZ;
+  static_assert(32 % TX == 0 || TX == 32, "a tile row must not straddle warps");
+  __shared__ double s_t[SZ][SY][SX];
+  __shared__ unsigned s_stamp[SZ][SY][SX];
+  __shared__ unsigned long long s_facemin[6];
+  __shared__ long long s_tile;
+  __shared__ int s_prob, s_faces, s_hassrc;
+
+  const int tid = threadIdx.x;
+  const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
+  const int xc = lx + 1, yc = ly + 1, zc = lz + HZ;
+  for (int i = tid; i < SZ * SY * SX; i += NT) (&s_stamp[0][0][0])[i] = 0u;
+  const double inv_delta = p.ctl->inv_delta;
+  if (p.test_stall && tid == 0) {   // testing aid: wait on a flag nothing sets
+    const long long t0 = now_ns();
+    while (ld_rlx(&p.ctl->never_set) == 0u) {
+      if (now_ns() - t0 > p.timeout_ns) { raise_status(p.ctl, kEtimeout, 8); break; }
+      __nanosleep(1000);
+    }
+  }
+  unsigned R = 1;
+  unsigned long long n_evals = 0, n_dec = 0, n_commits = 0, n_visits = 0, n_rounds = 0;
+  long long idle_since = 0;
+  __syncthreads();
+
+#pragma unroll 1
+  for (;;) {
+    if (tid < 32) {
+      long long tile = -1;
+      int faces = 0;
+#pragma unroll 1
+      for (;;) {
+        const unsigned long long e = pop_entry(p, idle_since);
+        if (e == kEmpty) break;
+        const unsigned long long tl = e & 0xffffffffull;
+        const unsigned b = static_cast<unsigned>(e >> 32);
+        int f = -1;
+        if (tid == 0) f = try_claim(p, tl, b);
+        f = __shfl_sync(kFull, f, 0);
+        if (f >= 0) { tile = static_cast<long long>(tl); faces = f; break; }
+        if (tid == 0) {
+          atomicAdd(&p.ctl->work, -1);
+          if (p.counters) atomicAdd(&p.ctl->stats[kStatStale], 1ull);
+        }
+      }
+      if (tid == 0) {
+        idle_since = 0;
+        int prob = 0, hs = 0;
+        if (tile >= 0) {
+          __threadfence();  // the claim is ordered before the tile's loads
+          prob = find_prob(p, static_cast<unsigned long long>(tile));
+          hs = p.tile_src[tile];
+        }
+        s_tile = tile;
+        s_faces = faces;
+        s_prob = prob;
+        s_hassrc = hs;
+      }
+    }
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile < 0) break;
+    const int faces = s_faces;
+    const Prob &P = p.probs[s_prob];
+    double *const T = P.t;
+    const int64_t nx = P.nx, ny = P.ny, nz = P.nz;
+    const int64_t lt = tile - P.tile_base;
+    const int64_t tx = lt % P.ntx, rest = lt / P.ntx;
+    const int64_t ty = rest % P.nty, tz = rest / P.nty;
+    const int64_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    const int64_t gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
+    const bool present = gx < nx && gy < ny && gz < nz;
+    const int64_t gidx = (gz * ny + gy) * nx + gx;
+
+    double tv = present ? ld_time(T + gidx) : from_bits(kInfBits);
+    const double rv = present ? __ldg(P.r + gidx) : 1.0;
+    bool active = present;
+    if (s_hassrc && present && is_source(P, gidx)) active = false;
+    s_t[zc][yc][xc] = tv;
+    // halo faces: -x, +x, -y, +y (, -z, +z)
+    {
+      constexpr int FX = TY * TZ, FY = TX * TZ, FZ = (D == 3) ? TX * TY : 0;
+      constexpr int H = 2 * FX + 2 * FY + 2 * FZ;
+#pragma unroll 1
+      for (int i = tid; i < H; i += NT) {
+        int64_t hx, hy, hz;
+        int sx, sy, sz;
+        if (i < 2 * FY) {              // y faces, x fastest: coalesced
+          const int side = i / FY, j = i % FY;
+          const int ix = j % TX, iz = j / TX;
+          hx = x0 + ix; hy = side ? y0 + TY : y0 - 1; hz = z0 + iz;
+          sx = ix + 1; sy = side ? TY + 1 : 0; sz = iz + HZ;
+        } else if (i < 2 * FY + 2 * FZ) {   // z faces
+          const int k = i - 2 * FY;
+          const int side = k / (FZ > 0 ? FZ : 1), j = k % (FZ > 0 ? FZ : 1);
+          const int ix = j % TX, iy = j / TX;
+          hx = x0 + ix; hy = y0 + iy; hz = side ? z0 + TZ : z0 - 1;
+          sx = ix + 1; sy = iy + 1; sz = side ? TZ + 1 : 0;
+        } else {                        // x faces
+          const int k = i - 2 * FY - 2 * FZ;
+          const int side = k / FX, j = k % FX;
+          const int iy = j % TY, iz = j / TY;
+          hx = side ? x0 + TX : x0 - 1; hy = y0 + iy; hz = z0 + iz;
+          sx = side ? TX + 1 : 0; sy = iy + 1; sz = iz + HZ;
+        }
+        const bool in = hx >= 0 && hx < nx && hy >= 0 && hy < ny && hz >= 0 && hz < nz;
+        s_t[sz][sy][sx] = in ? ld_time(T + (hz * ny + hy) * nx + hx) : from_bits(kInfBits);
+      }
+    }
+    if (tid < 6) s_facemin[tid] = kInfBits;
+    __syncthreads();
+
+    const double tv0 = tv;
+    bool need = active;
+    if (need && !(faces & (1 << kFaceFull))) {
+      need = ((faces & 1) && lx == 0) || ((faces & 2) && lx == TX - 1) ||
+             ((faces & 4) && ly == 0) || ((faces & 8) && ly == TY - 1) ||
+             (D == 3 && (((faces & 16) && lz == 0) || ((faces & 32) && lz == TZ - 1)));
+    }
+    unsigned rounds = 0;
+#pragma unroll 1
+    for (;;) {
+      double xl = __shfl_up_sync(kFull, tv, 1, TX);
+      double xr = __shfl_down_sync(kFull, tv, 1, TX);
+      if (lx == 0) xl = s_t[zc][yc][0];
+      if (lx == TX - 1) xr = s_t[zc][yc][TX + 1];
+      double nv = tv;
+      bool chg = false;
+      if (need) {
+        double a[D];
+        a[0] = min_time(xl, xr);
+        a[1] = min_time(s_t[zc][yc - 1][xc], s_t[zc][yc + 1][xc]);
+        if constexpr (D == 3) a[D - 1] = min_time(s_t[zc - 1][yc][xc], s_t[zc + 1][yc][xc]);
+        chg = relax_cell<D>(tv, a, rv, nv);
+        ++n_evals;
+        n_dec += chg ? 1 : 0;
+      }
+      __syncthreads();
+      if (chg) {
+        s_t[zc][yc][xc] = nv;
+        tv = nv;
+        s_stamp[zc][yc][xc] = R;
+      }
+      const int any = __syncthreads_or(chg);
+      ++rounds;
+      if (!any) break;
+      bool nb = s_stamp[zc][yc][xc - 1] == R || s_stamp[zc][yc][xc + 1] == R ||
+                s_stamp[zc][yc - 1][xc] == R || s_stamp[zc][yc + 1][xc] == R;
+      if constexpr (D == 3) nb = nb || s_stamp[zc - 1][yc][xc] == R || s_stamp[zc + 1][yc][xc] == R;
+      need = active && nb;
+      ++R;
+      if (rounds >= kMaxRounds) {   // uniform across the CTA
+        if (tid == 0) raise_status(p.ctl, kEtimeout, 7);
+        break;
+      }
+    }
+    ++R;
+
+    // commit and collect the smallest committed time per tile face
+    if (bits_of(tv) < bits_of(tv0)) {
+      const unsigned long long tb = bits_of(tv);
+      atomicMin(reinterpret_cast<unsigned long long *>(T + gidx), tb);
+      ++n_commits;
+      if (lx == 0) atomicMin(&s_facemin[0], tb);
+      if (lx == TX - 1) atomicMin(&s_facemin[1], tb);
+      if (ly == 0) atomicMin(&s_facemin[2], tb);
+      if (ly == TY - 1) atomicMin(&s_facemin[3], tb);
+      if (D == 3 && lz == 0) atomicMin(&s_facemin[4], tb);
+      if (D == 3 && lz == TZ - 1) atomicMin(&s_facemin[5], tb);
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid < 2 * D) {
+      const unsigned long long fm = s_facemin[tid];
+      if (fm != kInfBits) {
+        const int k = tid >> 1, side = tid & 1;
+        int64_t ntx = tx, nty = ty, ntz = tz;
+        bool exists;
+        if (k == 0) { ntx = side ? tx + 1 : tx - 1; exists = side ? (tx + 1 < P.ntx) : (tx > 0); }
+        else if (k == 1) { nty = side ? ty + 1 : ty - 1; exists = side ? (ty + 1 < P.nty) : (ty > 0); }
+        else { ntz = side ? tz + 1 : tz - 1; exists = side ? (tz + 1 < P.ntz) : (tz > 0); }
+        if (exists) {
+          const unsigned long long nt =
+              static_cast<unsigned long long>(P.tile_base + (ntz * P.nty + nty) * P.ntx + ntx);
+          activate(p, nt, 1u << (tid ^ 1), bucket_of_time(from_bits(fm), inv_delta));
+        }
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      finish_tile(p, static_cast<unsigned long long>(tile));
+      __threadfence();
+      atomicAdd(&p.ctl->work, -1);
+      ++n_visits;
+      n_rounds += rounds;
+    }
+  }
+
+  if (p.counters) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      n_evals += __shfl_xor_sync(kFull, n_evals, o);
+      n_dec += __shfl_xor_sync(kFull, n_dec, o);
+      n_commits += __shfl_xor_sync(kFull, n_commits, o);
+    }
+    if ((tid & 31) == 0) {
+      atomicAdd(&p.ctl->stats[kStatEvals], n_evals);
+      atomicAdd(&p.ctl->stats[kStatDecreases], n_dec);
+      atomicAdd(&p.ctl->stats[kStatCommits], n_commits);
+    }
+    if (tid == 0) {
+      atomicAdd(&p.ctl->stats[kStatVisits], n_visits);
+      atomicAdd(&p.ctl->stats[kStatRounds], n_rounds);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up kernels.
+// ---------------------------------------------------------------------------
+
+// r = fl(h / v) per cell (the constant c = fl(r * r) is formed where used);
+// checks v > 0 finite and r, c finite and positive; sums r for the auto
+// bucket width.
+__global__ void init_r_kernel(const double *__restrict__ speed, double h, double *__restrict__ r,
+                              int64_t n, Ctl *ctl) {
+  double sum = 0.0;
+  unsigned long long cnt = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const double v = speed[i];
+    const double ri = __ddiv_rn(h, v);
+    const double c = __dmul_rn(ri, ri);
+    const bool ok = v > 0.0 && bits_of(v) < kInfBits && ri > 0.0 && bits_of(ri) < kInfBits &&
+                    c > 0.0 && bits_of(c) < kInfBits;
+    if (!ok) raise_status(ctl, kEinval, static_cast<unsigned long long>(i));
+    r[i] = ri;
+    sum += ri;
+    ++cnt;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(kFull, sum, o);
+    cnt += __shfl_xor_sync(kFull, cnt, o);
+  }
+  if ((threadIdx.x & 31) == 0 && cnt) {
+    atomicAdd(&ctl->rsum, sum);
+    atomicAdd(&ctl->rcount, cnt);
+  }
+}
+
+__global__ void init_t_kernel(double *__restrict__ t, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    t[i] = from_bits(kInfBits);
+  }
+}
+
+__device__ __forceinline__ unsigned long long tile_of(const Prob &P, int64_t x, int64_t y, int64_t z,
+                                                      int tx_, int ty_, int tz_) {
+  return static_cast<unsigned long long>(P.tile_base +
+                                         ((z / tz_) * P.nty + (y / ty_)) * P.ntx + (x / tx_));
+}
+
+// Boundary nodes: t := t0 and activate, with every cell to be evaluated, the
+// tile of the source and the tiles of its in-grid neighbours.
+__global__ void seed_kernel(SolveParams p, const SeedItem *__restrict__ items, int64_t n,
+                            double k_delta, double delta_fixed, int tx_, int ty_, int tz_) {
+  Ctl *ctl = p.ctl;
+  double delta = delta_fixed > 0.0 ? delta_fixed
+                                   : k_delta * (ctl->rsum / static_cast<double>(ctl->rcount));
+  if (!(delta > 0.0) || !(bits_of(delta) < kInfBits)) delta = 1.0;
+  const double inv = 1.0 / delta;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->delta = delta;
+    ctl->inv_delta = inv;
+  }
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const SeedItem it = items[i];
+    const Prob &P = p.probs[it.prob];
+    P.t[it.idx] = it.t0;
+    const int64_t x = it.idx % P.nx, yz = it.idx / P.nx;
+    const int64_t y = yz % P.ny, z = yz / P.ny;
+    const unsigned long long own = tile_of(P, x, y, z, tx_, ty_, tz_);
+    p.tile_src[own] = 1;
+    const unsigned b = bucket_of_time(it.t0, inv);
+    activate(p, own, 1u << kFaceFull, b);
+    const int64_t c3[3] = {x, y, z};
+    const int64_t n3[3] = {P.nx, P.ny, P.nz};
+    for (int k = 0; k < 3; ++k) {
+      for (int side = 0; side < 2; ++side) {
+        int64_t q[3] = {c3[0], c3[1], c3[2]};
+        q[k] += side ? 1 : -1;
+        if (q[k] < 0 || q[k] >= n3[k]) continue;
+        const unsigned long long nt = tile_of(P, q[0], q[1], q[2], tx_, ty_, tz_);
+        if (nt != own) activate(p, nt, 1u << kFaceFull, b);
+      }
+    }
+  }
+}
+
+// Capacity retry: every tile holding a finite value is re-queued with a full
+// evaluation (Theorem 1: any state reached by valid updates is a valid start).
+__global__ void reseed_kernel(SolveParams p, int tx_, int ty_, int tz_, int64_t total_tiles) {
+  const double inv = p.ctl->inv_delta;
+  for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total_tiles;
+       g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int pi = find_prob(p, static_cast<unsigned long long>(g));
+    const Prob &P = p.probs[pi];
+    const int64_t lt = g - P.tile_base;
+    const int64_t tx = lt % P.ntx, rest = lt / P.ntx;
+    const int64_t ty = rest % P.nty, tz = rest / P.nty;
+    unsigned long long best = kInfBits;
+    for (int64_t z = tz * tz_; z < (tz + 1) * tz_ && z < P.nz; ++z)
+      for (int64_t y = ty * ty_; y < (ty + 1) * ty_ && y < P.ny; ++y)
+        for (int64_t x = tx * tx_; x < (tx + 1) * tx_ && x < P.nx; ++x)
+          best = umin64(best, bits_of(ld_time(P.t + (z * P.ny + y) * P.nx + x)));
+    if (best < kInfBits) activate(p, static_cast<unsigned long long>(g), 1u << kFaceFull,
+                                  bucket_of_time(from_bits(best), inv));
+  }
+}
+
+__global__ void count_finite_kernel(const double *__restrict__ t, int64_t n,
+                                    unsigned long long *out) {
+  unsigned long long cnt = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    cnt += bits_of(t[i]) < kInfBits ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
+}
+
+int g_num_sms = 0;
+
+int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+int grid_for(int64_t n, int per_sm) {
+  int64_t g = (n + 255) / 256;
+  const int64_t cap = static_cast<int64_t>(num_sms()) * per_sm;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+}  // namespace
+
+cudaError_t launch_init_r(const double *speed, double h, double *r, int64_t n, Ctl *ctl,
+                          cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  init_r_kernel<<<grid_for(n, 8), 256, 0, stream>>>(speed, h, r, n, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_t(double *t, int64_t n, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  init_t_kernel<<<grid_for(n, 8), 256, 0, stream>>>(t, n);
+  return cudaGetLastError();
+}
+
+static void tile_dims(int ndim, int &tx, int &ty, int &tz) {
+  if (ndim == 3) { tx = kTX3; ty = kTY3; tz = kTZ3; }
+  else { tx = kTX2; ty = kTY2; tz = 1; }
+}
+
+cudaError_t launch_seed(const SolveParams &p, const SeedItem *items, int64_t nitems,
+                        double k_delta, double delta_fixed, cudaStream_t stream) {
+  int tx, ty, tz;
+  tile_dims(p.ndim, tx, ty, tz);
+  const int grid = grid_for(nitems > 0 ? nitems : 1, 4);
+  seed_kernel<<<grid, 256, 0, stream>>>(p, items, nitems, k_delta, delta_fixed, tx, ty, tz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int nprob,
+                          cudaStream_t stream) {
+  int tx, ty, tz;
+  tile_dims(p.ndim, tx, ty, tz);
+  const Prob &last = host_probs[nprob - 1];
+  const int64_t total = last.tile_base + last.ntx * last.nty * last.ntz;
+  reseed_kernel<<<grid_for(total, 4), 256, 0, stream>>>(p, tx, ty, tz, total);
+  return cudaGetLastError();
+}
+
+int persistent_blocks_per_sm(int ndim) {
+  int nb = 0;
+  if (ndim == 3) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<3, kTX3, kTY3, kTZ3>,
+                                                  kTX3 * kTY3 * kTZ3, 0);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<2, kTX2, kTY2, 1>,
+                                                  kTX2 * kTY2, 0);
+  }
+  return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_persistent(const SolveParams &p, int grid, cudaStream_t stream) {
+  if (p.ndim == 3) {
+    persistent_kernel<3, kTX3, kTY3, kTZ3><<<grid, kTX3 * kTY3 * kTZ3, 0, stream>>>(p);
+  } else {
+    persistent_kernel<2, kTX2, kTY2, 1><<<grid, kTX2 * kTY2, 0, stream>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_finite(const Prob *host_probs, int nprob, unsigned long long *out,
+                                cudaStream_t stream) {
+  for (int i = 0; i < nprob; ++i) {
+    const Prob &P = host_probs[i];
+    const int64_t n = P.nx * P.ny * P.nz;
+    count_finite_kernel<<<grid_for(n, 8), 256, 0, stream>>>(P.t, n, out);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace eik
