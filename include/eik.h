@@ -89,6 +89,8 @@ typedef struct {
     int64_t stale_pops;    /* frontier entries dropped as stale */
     int64_t rounds;        /* relaxation rounds summed over tile visits */
     int64_t retries;       /* capacity retries performed */
+    double solve_ms;       /* device time of the persistent solve kernel(s), CUDA events
+                              recorded on `stream` around each launch */
 } eik_stats;
 
 /* Solve one grid (Algorithm 6 with d-bar, result identical to Algorithm 2).

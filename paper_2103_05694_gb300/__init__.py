@@ -38,10 +38,10 @@ class EikOpts(ctypes.Structure):
 class EikStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("evals", "decreases", "good", "visits", "pushes", "stale_pops", "rounds",
-                 "retries")]
+                 "retries")] + [("solve_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
-        d = {n: int(getattr(self, n)) for n, _ in self._fields_}
+        d = {n: getattr(self, n) for n, _ in self._fields_}
         d["empty"] = d["evals"] - d["decreases"]
         d["bad"] = d["decreases"] - d["good"]
         return d

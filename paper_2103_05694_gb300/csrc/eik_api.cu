@@ -72,6 +72,7 @@ struct Workspace {
   DevBuf<Ctl> ctl;
   DevBuf<unsigned long long> count;
   Ctl *ctl_host = nullptr;     // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool slots_dirty = true;
   uint64_t cap = 0;            // entries per slot
 
@@ -81,6 +82,9 @@ struct Workspace {
     ctl.release(); count.release();
     if (ctl_host) cudaFreeHost(ctl_host);
     ctl_host = nullptr;
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    ev0 = ev1 = nullptr;
     slots_dirty = true;
     cap = 0;
     device = -1;
@@ -212,6 +216,10 @@ eik_status ensure_device() {
   }
   if (!g_ws.ctl_host) {
     CK(cudaMallocHost(&g_ws.ctl_host, sizeof(Ctl)), "pinned control block");
+  }
+  if (!g_ws.ev0) {
+    CK(cudaEventCreate(&g_ws.ev0), "event");
+    CK(cudaEventCreate(&g_ws.ev1), "event");
   }
   return EIK_OK;
 }
@@ -388,10 +396,15 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   std::memset(&acc, 0, sizeof(acc));
   unsigned status = 0;
   for (int attempt = 0;; ++attempt) {
+    CK(cudaEventRecord(g_ws.ev0, stream), "event record");
     CK(eik::launch_persistent(sp, (int)grid, stream), "solve launch");
+    CK(cudaEventRecord(g_ws.ev1, stream), "event record");
     CK(cudaMemcpyAsync(g_ws.ctl_host, g_ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, stream),
        "read status");
     CK(cudaStreamSynchronize(stream), "solve");
+    float kms = 0.f;
+    CK(cudaEventElapsedTime(&kms, g_ws.ev0, g_ws.ev1), "event time");
+    acc.solve_ms += kms;
     const Ctl &c = *g_ws.ctl_host;
     status = c.status;
     acc.evals += (int64_t)c.stats[eik::kStatEvals];

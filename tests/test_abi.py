@@ -53,7 +53,7 @@ def test_status_strings_without_gpu(lib):
 def test_struct_layouts_match_header():
     # eik_opts: double, double, int64, int64, int, int, int, int -> 48 bytes
     assert ctypes.sizeof(eik.EikOpts) == 48
-    assert ctypes.sizeof(eik.EikStats) == 8 * 8
+    assert ctypes.sizeof(eik.EikStats) == 9 * 8
     # eik_problem: ptr, double, int(+pad), int64[3], ptr, ptr, int64, ptr
     assert ctypes.sizeof(eik.EikProblem) == 8 + 8 + 8 + 24 + 8 + 8 + 8 + 8
 
