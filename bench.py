@@ -45,6 +45,14 @@ def workloads():
     }
 
 
+def scaled_layered(scale: float):
+    """The layered 2D model at a fraction of its extent per axis (profiling cases)."""
+    nx, nz = max(32, round(2301 * scale)), max(8, round(751 * scale))
+    speed = synth.layered_section(nx, nz, 4.0, seed=2)
+    src = np.array([nx // 2], dtype=np.int64)
+    return synth.Problem(f"2d_{nx}x{nz}_layered", speed, 4.0, src, np.zeros(1), {})
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -170,6 +178,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="2", choices=sorted(workloads()))
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="config 2 only: fraction of the extent per axis (profiling)")
     ap.add_argument("--k-delta", type=float, default=0.0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -185,7 +195,11 @@ def main():
         args.gpus = world
 
     wl_name, make = workloads()[args.config]
-    prob = make()
+    if args.config == "2" and args.scale != 1.0:
+        prob = scaled_layered(args.scale)
+        wl_name = prob.name + " (config 2 scaled)"
+    else:
+        prob = make()
     useful = prob.ncells - len(np.unique(prob.sources))   # every cell is reachable
 
     if args.impl == "reference":

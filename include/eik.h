@@ -76,7 +76,10 @@ typedef struct {
     int test_stall;        /* testing aid, keep 0: the solve first waits on a device flag
                               that nothing sets, so the wait reaches timeout_ms and the
                               call returns EIK_ETIMEOUT (exercises the bounded waits) */
-    int reserved;
+    int window;            /* buckets above the lowest active bucket that may be worked on
+                              (look-ahead of the relaxed priority order); 0: default */
+    double band;           /* in-tile acceptance band in units of (smallest h/v of the tile)
+                              / sqrt(ndim), i.e. one cell's travel time; <= 0: default */
 } eik_opts;
 
 /* Work accounting (the paper's good/empty/bad updates, Results section). */
@@ -89,6 +92,10 @@ typedef struct {
     int64_t stale_pops;    /* frontier entries dropped as stale */
     int64_t rounds;        /* relaxation rounds summed over tile visits */
     int64_t retries;       /* capacity retries performed */
+    int64_t max_queue;     /* deepest bucket slot seen at a push (entries) */
+    int64_t visit_ns;      /* tile-visit time summed over CTAs (counters only) */
+    int64_t idle_ns;       /* time CTAs spent looking for work (counters only) */
+    int64_t ctas;          /* persistent CTAs launched */
     double solve_ms;       /* device time of the persistent solve kernel(s), CUDA events
                               recorded on `stream` around each launch */
 } eik_stats;

@@ -32,13 +32,15 @@ class EikOpts(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("k_delta", ctypes.c_double),
                 ("capacity", ctypes.c_int64), ("timeout_ms", ctypes.c_int64),
                 ("ctas_per_sm", ctypes.c_int), ("counters", ctypes.c_int),
-                ("test_stall", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("test_stall", ctypes.c_int), ("window", ctypes.c_int),
+                ("band", ctypes.c_double)]
 
 
 class EikStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("evals", "decreases", "good", "visits", "pushes", "stale_pops", "rounds",
-                 "retries")] + [("solve_ms", ctypes.c_double)]
+                 "retries", "max_queue", "visit_ns", "idle_ns", "ctas")] + \
+        [("solve_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         d = {n: getattr(self, n) for n, _ in self._fields_}

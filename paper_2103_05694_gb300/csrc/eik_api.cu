@@ -33,7 +33,9 @@ void set_err(const char *fmt, ...) {
 
 constexpr int64_t kMaxCells = int64_t(1) << 40;
 constexpr uint64_t kMaxCapEntries = uint64_t(1) << 30;   // whole ring storage limit
-constexpr double kDefaultKDelta = 16.0;
+constexpr double kDefaultKDelta = 8.0;
+constexpr int kDefaultWindow = 4;
+constexpr double kDefaultBand = 4.0;
 constexpr int kMaxRetries = 4;
 
 // Grow-only device buffer.
@@ -64,6 +66,7 @@ struct Workspace {
   DevBuf<double> v_stage;      // host speed staging
   DevBuf<unsigned long long> state;
   DevBuf<unsigned char> tile_src;
+  DevBuf<unsigned> pend;
   DevBuf<unsigned long long> slots;
   DevBuf<int64_t> src_idx;
   DevBuf<double> src_t;
@@ -78,6 +81,7 @@ struct Workspace {
 
   void release_all() {
     r.release(); t_stage.release(); v_stage.release(); state.release(); tile_src.release();
+    pend.release();
     slots.release(); src_idx.release(); src_t.release(); seeds.release(); probs.release();
     ctl.release(); count.release();
     if (ctl_host) cudaFreeHost(ctl_host);
@@ -313,6 +317,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   if (total_tiles >= (int64_t(1) << 32)) { set_err("too many tiles"); return EIK_EINVAL; }
   CK(g_ws.state.ensure((size_t)total_tiles), "alloc tile state");
   CK(g_ws.tile_src.ensure((size_t)total_tiles), "alloc tile flags");
+  CK(g_ws.pend.ensure((size_t)total_tiles * eik::kPendWords), "alloc pending masks");
 
   // frontier capacity per bucket slot
   uint64_t want_cap = opts && opts->capacity > 0 ? (uint64_t)opts->capacity
@@ -342,6 +347,8 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   CK(cudaMemsetAsync(g_ws.state.p, 0, (size_t)total_tiles * sizeof(unsigned long long), stream),
      "clear tile states");
   CK(cudaMemsetAsync(g_ws.tile_src.p, 0, (size_t)total_tiles, stream), "clear tile flags");
+  CK(cudaMemsetAsync(g_ws.pend.p, 0, (size_t)total_tiles * eik::kPendWords * sizeof(unsigned),
+                     stream), "clear pending masks");
   if (g_ws.slots_dirty) {
     CK(cudaMemsetAsync(g_ws.slots.p, 0xff, g_ws.slots.n * sizeof(unsigned long long), stream),
        "clear frontier");
@@ -371,6 +378,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.ndim = ndim;
   sp.state = g_ws.state.p;
   sp.tile_src = g_ws.tile_src.p;
+  sp.pend = g_ws.pend.p;
+  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow);
+  sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand;
   sp.slots = g_ws.slots.p;
   sp.cap_mask = (unsigned)(g_ws.cap - 1);
   sp.ctl = g_ws.ctl.p;
@@ -413,6 +423,10 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     acc.pushes += (int64_t)c.stats[eik::kStatPushes];
     acc.stale_pops += (int64_t)c.stats[eik::kStatStale];
     acc.rounds += (int64_t)c.stats[eik::kStatRounds];
+    acc.max_queue = std::max<int64_t>(acc.max_queue, (int64_t)c.stats[eik::kStatMaxQueue]);
+    acc.visit_ns += (int64_t)c.stats[eik::kStatVisitNs];
+    acc.idle_ns += (int64_t)c.stats[eik::kStatIdleNs];
+    acc.ctas = grid;
     if (status != eik::kEcapacity || attempt >= kMaxRetries ||
         g_ws.cap * 4 * eik::kNumSlots > kMaxCapEntries) break;
     // grow the frontier, clear the scheduler (keep delta) and resume

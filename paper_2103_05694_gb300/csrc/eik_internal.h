@@ -23,7 +23,7 @@ constexpr unsigned kOk = 0, kEinval = 1, kEcapacity = 3, kEtimeout = 4;
 
 enum StatIdx {
   kStatEvals = 0, kStatDecreases, kStatVisits, kStatPushes, kStatStale, kStatRounds,
-  kStatCommits, kNumStats
+  kStatCommits, kStatMaxQueue, kStatVisitNs, kStatIdleNs, kNumStats
 };
 
 // Control block, zeroed before every solve.
@@ -40,11 +40,13 @@ struct Ctl {
   unsigned long long rcount;
   double delta;             // bucket width used
   double inv_delta;
-  int pad3[24];
+  unsigned long long rmin_bits;   // smallest r (bit pattern; all r > 0)
+  int pad3[22];
   unsigned long long stats[kNumStats];
   unsigned long long error_info[4];   // where a wait gave up / what was invalid
   unsigned push[kNumSlots * kCounterPad];
   unsigned pop[kNumSlots * kCounterPad];
+  unsigned run[kNumSlots * kCounterPad];   // tiles claimed from the slot and still running
 };
 
 // One grid of a (possibly batched) solve, as the kernels see it.
@@ -65,13 +67,19 @@ struct SolveParams {
   int ndim;
   unsigned long long *state;      // per global tile
   unsigned char *tile_src;        // per global tile: 1 if it holds a source
+  unsigned *pend;                 // per global tile, kPendWords words: cells deferred by
+                                  // the last visit (to evaluate at the next one)
   unsigned long long *slots;      // kNumSlots * cap
   unsigned cap_mask;              // cap - 1
   Ctl *ctl;
   long long timeout_ns;
   int counters;
   int test_stall;
+  unsigned window;                // buckets above the lowest active one that may be popped
+  double band;                    // in-tile acceptance band, in units of min r / sqrt(D)
 };
+
+constexpr int kPendWords = 8;            // 256 cells per tile / 32
 
 // Tile shapes (cells): one thread per cell, 256 threads per CTA.
 constexpr int kTX2 = 32, kTY2 = 8;                 // 2D

@@ -242,7 +242,9 @@ __device__ bool push_entry(const SolveParams &p, unsigned long long tile, unsign
   const unsigned s = b & (kNumSlots - 1);
   const unsigned cap = p.cap_mask + 1u;
   const unsigned idx = atomicAdd(&ctl->push[s * kCounterPad], 1u);
-  if (idx - ld_rlx(&ctl->pop[s * kCounterPad]) >= cap) {
+  // depth as a signed difference: a popper may already have taken index idx
+  const int depth = static_cast<int>(idx - ld_rlx(&ctl->pop[s * kCounterPad]));
+  if (depth >= static_cast<int>(cap)) {
     raise_status(ctl, kEcapacity, (static_cast<unsigned long long>(s) << 32) | idx);
     return false;
   }
@@ -256,7 +258,14 @@ __device__ bool push_entry(const SolveParams &p, unsigned long long tile, unsign
     if (ld_rlx(&ctl->status)) return false;
     __nanosleep(64);
   }
-  if (p.counters) atomicAdd(&ctl->stats[kStatPushes], 1ull);
+  // A scanner may have moved the lowest-bucket hint past this slot between
+  // the caller's read of the hint and the push: pull the hint back.  A
+  // scanner's forward CAS from a stale value then fails.
+  atomicMin(&ctl->cur, b);
+  if (p.counters) {
+    atomicAdd(&ctl->stats[kStatPushes], 1ull);
+    if (depth > 0) atomicMax(&ctl->stats[kStatMaxQueue], static_cast<unsigned long long>(depth));
+  }
   return true;
 }
 
@@ -352,11 +361,18 @@ __device__ unsigned long long take_slot(const SolveParams &p, unsigned s, unsign
   }
 }
 
-// Warp 0: find the lowest non-empty slot from the hint and take one entry.
+// Warp 0: take one entry from the lowest active bucket slots.  A slot is
+// active while it holds entries or tiles claimed from it are still running;
+// the hint `cur` moves up to the lowest active slot, and only slots within
+// `window` buckets of it are popped (bounded look-ahead, the soft priority of
+// OBIM).  On success the slot's run counter has been incremented for the
+// caller, `slot_out` is the slot and `lo_out` the lowest active bucket.
 // Returns kEmpty when the solve is over (done or error).
-__device__ unsigned long long pop_entry(const SolveParams &p, long long &idle_since) {
+__device__ unsigned long long pop_entry(const SolveParams &p, long long &idle_since,
+                                        unsigned &slot_out, unsigned &lo_out) {
   Ctl *ctl = p.ctl;
   const unsigned lane = threadIdx.x & 31u;
+  const unsigned win = p.window < 31u ? p.window : 31u;
 #pragma unroll 1
   for (;;) {
     unsigned stop = 0, cur = 0;
@@ -367,18 +383,43 @@ __device__ unsigned long long pop_entry(const SolveParams &p, long long &idle_si
     stop = __shfl_sync(kFull, stop, 0);
     if (stop) return kEmpty;
     cur = __shfl_sync(kFull, cur, 0);
+    // find the lowest active slot at or above the hint (whole ring if needed)
+    unsigned first = 0xffffffffu;
+    unsigned q = 0, pp = 0, s = 0;
+    bool pend = false;
 #pragma unroll 1
     for (unsigned base = 0; base < kNumSlots; base += 32) {
-      const unsigned s = (cur + base + lane) & (kNumSlots - 1);
-      unsigned q = ld_rlx(&ctl->pop[s * kCounterPad]);
-      unsigned pp = ld_rlx(&ctl->push[s * kCounterPad]);
-      unsigned nonempty = __ballot_sync(kFull, static_cast<int>(pp - q) > 0);
+      s = (cur + base + lane) & (kNumSlots - 1);
+      q = ld_rlx(&ctl->pop[s * kCounterPad]);
+      pp = ld_rlx(&ctl->push[s * kCounterPad]);
+      const unsigned rn = ld_rlx(&ctl->run[s * kCounterPad]);
+      pend = static_cast<int>(pp - q) > 0;
+      const unsigned act = __ballot_sync(kFull, pend || rn > 0u);
+      if (act) {
+        first = base + static_cast<unsigned>(__ffs(act) - 1);
+        break;
+      }
+    }
+    if (first == 0xffffffffu) {
+      int w = 0;
+      if (lane == 0) w = ld_rlx(&ctl->work);
+      w = __shfl_sync(kFull, w, 0);
+      if (w == 0) {
+        if (lane == 0) st_rlx(&ctl->done, 1u);
+        return kEmpty;
+      }
+    } else {
+      if (first > 0 && lane == 0 && cur + first <= kMaxBucket) atomicCAS(&ctl->cur, cur, cur + first);
+      if (first >= 32) continue;   // re-read the 32 slots from the new hint
+      const unsigned lo = cur + first;
+      unsigned cand = __ballot_sync(kFull, pend && lane >= first && lane <= first + win);
 #pragma unroll 1
-      while (nonempty) {
-        const int l = __ffs(nonempty) - 1;
+      while (cand) {
+        const int l = __ffs(cand) - 1;
         unsigned long long e = kEmpty;
         int got = 0;
         if (lane == static_cast<unsigned>(l)) {
+          atomicAdd(&ctl->run[s * kCounterPad], 1u);   // keep the slot active meanwhile
 #pragma unroll 1
           while (static_cast<int>(pp - q) > 0) {
             const unsigned prev = atomicCAS(&ctl->pop[s * kCounterPad], q, q + 1u);
@@ -386,33 +427,25 @@ __device__ unsigned long long pop_entry(const SolveParams &p, long long &idle_si
             q = prev;
             pp = ld_rlx(&ctl->push[s * kCounterPad]);
           }
-          if (got) {
-            const unsigned off = base + lane;
-            if (off > 0 && cur + off <= kMaxBucket) atomicCAS(&ctl->cur, cur, cur + off);
-            e = take_slot(p, s, q);
-          }
+          if (got) e = take_slot(p, s, q);
+          else atomicAdd(&ctl->run[s * kCounterPad], 0xffffffffu);
         }
         got = __shfl_sync(kFull, got, l);
         if (got) {
           e = __shfl_sync(kFull, e, l);
+          slot_out = __shfl_sync(kFull, s, l);
+          lo_out = lo;
           return e;  // kEmpty here means the solve is being aborted
         }
-        nonempty &= ~(1u << l);
+        cand &= ~(1u << l);
       }
-    }
-    int w = 0;
-    if (lane == 0) w = ld_rlx(&ctl->work);
-    w = __shfl_sync(kFull, w, 0);
-    if (w == 0) {
-      if (lane == 0) st_rlx(&ctl->done, 1u);
-      return kEmpty;
     }
     if (lane == 0) {
       const long long now = now_ns();
       if (idle_since == 0) idle_since = now;
       else if (now - idle_since > p.timeout_ns) raise_status(ctl, kEtimeout, 2);
     }
-    __nanosleep(200);
+    __nanosleep(128);
   }
 }
 
@@ -437,26 +470,52 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 }
 
 // ---------------------------------------------------------------------------
-// Persistent kernel: pop a tile, relax it to local convergence, commit,
-// activate neighbour tiles, repeat until no work is left anywhere.
+// Persistent kernel: pop a tile, relax it in shared memory, commit, activate
+// neighbour tiles, repeat until no work is left anywhere.
+//
+// A visit finalises cells in increasing order of time (delta-stepping inside
+// the tile): every round evaluates the cells whose neighbours changed, takes
+// the CTA-wide minimum m of the pending candidates and accepts the candidates
+// within `band` of m (one cell's travel time: those cannot improve each other).
+// Candidates at or above the visit limit V = (lowest active bucket + window
+// + 1) * delta are deferred: recorded in the tile's pending mask and the tile
+// re-queued at their bucket.  Only accepted values are written to memory.
 // ---------------------------------------------------------------------------
 template <int D, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p) {
+__global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams p) {
   constexpr int NT = TX * TY * TZ;
+  static_assert(NT == 32 * kPendWords, "one pending bit per cell");
   constexpr int HZ = (D == 3) ? 1 : 0;
   constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2 * HZ;
   static_assert(32 % TX == 0 || TX == 32, "a tile row must not straddle warps");
   __shared__ double s_t[SZ][SY][SX];
   __shared__ unsigned s_stamp[SZ][SY][SX];
+  __shared__ double s_a[D][NT];            // axis minima of the cells on the list
+  __shared__ double s_r[NT];               // r of each cell of the tile
+  __shared__ unsigned long long s_best[NT];  // value a candidate must beat
+  __shared__ unsigned long long s_cand[NT];  // candidate produced this round
+  __shared__ unsigned short s_list[NT];    // cells whose update needs FP64 this round
+  __shared__ int s_cnt[2];
   __shared__ unsigned long long s_facemin[6];
+  __shared__ unsigned long long s_min[2];
+  __shared__ unsigned long long s_rmin;
+  __shared__ unsigned long long s_vlim;
+  __shared__ double s_band;
   __shared__ long long s_tile;
   __shared__ int s_prob, s_faces, s_hassrc;
+  __shared__ unsigned s_slot, s_lo;
 
   const int tid = threadIdx.x;
+  const unsigned lane = tid & 31;
+  const int warp = tid >> 5;
   const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
   const int xc = lx + 1, yc = ly + 1, zc = lz + HZ;
   for (int i = tid; i < SZ * SY * SX; i += NT) (&s_stamp[0][0][0])[i] = 0u;
+  s_cand[tid] = kInfBits;
+  if (tid == 0) { s_rmin = kInfBits; s_min[0] = s_min[1] = kInfBits; s_cnt[0] = s_cnt[1] = 0; }
+  const double delta = p.ctl->delta;
   const double inv_delta = p.ctl->inv_delta;
+  const double band_scale = p.band / sqrt(static_cast<double>(D));
   if (p.test_stall && tid == 0) {   // testing aid: wait on a flag nothing sets
     const long long t0 = now_ns();
     while (ld_rlx(&p.ctl->never_set) == 0u) {
@@ -466,7 +525,8 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
   }
   unsigned R = 1;
   unsigned long long n_evals = 0, n_dec = 0, n_commits = 0, n_visits = 0, n_rounds = 0;
-  long long idle_since = 0;
+  unsigned long long visit_ns = 0, idle_ns = 0;
+  long long idle_since = 0, t_claim = 0;
   __syncthreads();
 
 #pragma unroll 1
@@ -474,9 +534,11 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
     if (tid < 32) {
       long long tile = -1;
       int faces = 0;
+      unsigned slot = 0, lo = 0;
+      const long long t_pop = p.counters ? now_ns() : 0;
 #pragma unroll 1
       for (;;) {
-        const unsigned long long e = pop_entry(p, idle_since);
+        const unsigned long long e = pop_entry(p, idle_since, slot, lo);
         if (e == kEmpty) break;
         const unsigned long long tl = e & 0xffffffffull;
         const unsigned b = static_cast<unsigned>(e >> 32);
@@ -485,22 +547,31 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
         f = __shfl_sync(kFull, f, 0);
         if (f >= 0) { tile = static_cast<long long>(tl); faces = f; break; }
         if (tid == 0) {
+          atomicAdd(&p.ctl->run[slot * kCounterPad], 0xffffffffu);
           atomicAdd(&p.ctl->work, -1);
           if (p.counters) atomicAdd(&p.ctl->stats[kStatStale], 1ull);
         }
       }
       if (tid == 0) {
         idle_since = 0;
+        if (p.counters) {
+          t_claim = now_ns();
+          idle_ns += static_cast<unsigned long long>(t_claim - t_pop);
+        }
         int prob = 0, hs = 0;
         if (tile >= 0) {
           __threadfence();  // the claim is ordered before the tile's loads
           prob = find_prob(p, static_cast<unsigned long long>(tile));
           hs = p.tile_src[tile];
+          const double vlim = static_cast<double>(lo + p.window + 1u) * delta;
+          s_vlim = bits_of(vlim);
         }
         s_tile = tile;
         s_faces = faces;
         s_prob = prob;
         s_hassrc = hs;
+        s_slot = slot;
+        s_lo = lo;
       }
     }
     __syncthreads();
@@ -523,6 +594,16 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
     bool active = present;
     if (s_hassrc && present && is_source(P, gidx)) active = false;
     s_t[zc][yc][xc] = tv;
+    s_r[tid] = rv;
+    unsigned pword = 0;
+    if (lane == 0) pword = ld_rlx(p.pend + static_cast<size_t>(tile) * kPendWords + warp);
+    pword = __shfl_sync(kFull, pword, 0);
+    {  // smallest r of the tile's active cells -> acceptance band
+      unsigned long long rb = active ? bits_of(rv) : kInfBits;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rb = umin64(rb, __shfl_xor_sync(kFull, rb, o));
+      if (lane == 0 && rb < kInfBits) atomicMin(&s_rmin, rb);
+    }
     // halo faces: -x, +x, -y, +y (, -z, +z)
     {
       constexpr int FX = TY * TZ, FY = TX * TZ, FZ = (D == 3) ? TX * TY : 0;
@@ -554,42 +635,101 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
       }
     }
     if (tid < 6) s_facemin[tid] = kInfBits;
+    if (tid == 0) { s_min[0] = kInfBits; s_min[1] = kInfBits; s_cnt[0] = 0; s_cnt[1] = 0; }
     __syncthreads();
+    if (tid == 0) {
+      s_band = from_bits(s_rmin) * band_scale;
+      s_rmin = kInfBits;
+    }
+    const unsigned long long vlim = s_vlim;
 
     const double tv0 = tv;
     bool need = active;
     if (need && !(faces & (1 << kFaceFull))) {
       need = ((faces & 1) && lx == 0) || ((faces & 2) && lx == TX - 1) ||
              ((faces & 4) && ly == 0) || ((faces & 8) && ly == TY - 1) ||
-             (D == 3 && (((faces & 16) && lz == 0) || ((faces & 32) && lz == TZ - 1)));
+             (D == 3 && (((faces & 16) && lz == 0) || ((faces & 32) && lz == TZ - 1))) ||
+             ((pword >> lane) & 1u);
     }
+    unsigned long long pv = kInfBits;   // pending candidate (bit pattern)
+    unsigned long long m = kInfBits;
     unsigned rounds = 0;
 #pragma unroll 1
     for (;;) {
+      // (A) neighbour minima (x by shuffles) and the exact integer filters; the
+      //     cells that may decrease go on a dense list for the FP64 phase
       double xl = __shfl_up_sync(kFull, tv, 1, TX);
       double xr = __shfl_down_sync(kFull, tv, 1, TX);
       if (lx == 0) xl = s_t[zc][yc][0];
       if (lx == TX - 1) xr = s_t[zc][yc][TX + 1];
-      double nv = tv;
-      bool chg = false;
+      bool go = false;
       if (need) {
         double a[D];
         a[0] = min_time(xl, xr);
         a[1] = min_time(s_t[zc][yc - 1][xc], s_t[zc][yc + 1][xc]);
         if constexpr (D == 3) a[D - 1] = min_time(s_t[zc - 1][yc][xc], s_t[zc + 1][yc][xc]);
-        chg = relax_cell<D>(tv, a, rv, nv);
+        unsigned long long amin = bits_of(a[0]);
+#pragma unroll
+        for (int k = 1; k < D; ++k) amin = umin64(amin, bits_of(a[k]));
+        const unsigned long long best = umin64(bits_of(tv), pv);
+        go = amin < kInfBits && best > amin;
+        if (go) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) s_a[k][tid] = a[k];
+          s_best[tid] = best;
+        }
         ++n_evals;
-        n_dec += chg ? 1 : 0;
+      }
+      {
+        const unsigned bal = __ballot_sync(kFull, go);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&s_cnt[R & 1u], __popc(bal));
+        base = __shfl_sync(kFull, base, 0);
+        if (go) s_list[base + __popc(bal & ((1u << lane) - 1u))] = static_cast<unsigned short>(tid);
       }
       __syncthreads();
-      if (chg) {
-        s_t[zc][yc][xc] = nv;
-        tv = nv;
-        s_stamp[zc][yc][xc] = R;
+      // (B) dense FP64 phase: the first ceil(cnt/32) warps evaluate d-bar
+      {
+        const int cnt = s_cnt[R & 1u];
+        if (tid < cnt) {
+          const int c = s_list[tid];
+          double a[D];
+#pragma unroll
+          for (int k = 0; k < D; ++k) a[k] = s_a[k][c];
+          double nv;
+          if (relax_cell<D>(from_bits(s_best[c]), a, s_r[c], nv)) s_cand[c] = bits_of(nv);
+        }
       }
-      const int any = __syncthreads_or(chg);
+      __syncthreads();
+      if (tid == 0) s_cnt[(R + 1u) & 1u] = 0;
+      if (go) {
+        const unsigned long long cv = s_cand[tid];
+        if (cv < pv) pv = cv;
+        s_cand[tid] = kInfBits;
+      }
+      {  // CTA-wide minimum of the pending candidates
+        unsigned long long w = pv;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w = umin64(w, __shfl_xor_sync(kFull, w, o));
+        if (lane == 0 && w < kInfBits) atomicMin(&s_min[R & 1u], w);
+      }
+      __syncthreads();
+      m = s_min[R & 1u];
+      if (tid == 0) s_min[(R + 1u) & 1u] = kInfBits;
       ++rounds;
-      if (!any) break;
+      if (m >= vlim) break;   // nothing pending below the visit limit (uniform)
+      double lim_d = 0.0;
+      if (lane == 0) lim_d = __dadd_rn(from_bits(m), s_band);
+      const unsigned long long lim = umin64(bits_of(__shfl_sync(kFull, lim_d, 0)), vlim - 1);
+      const bool acc = pv <= lim;
+      if (acc) {
+        tv = from_bits(pv);
+        pv = kInfBits;
+        s_t[zc][yc][xc] = tv;
+        s_stamp[zc][yc][xc] = R;
+        ++n_dec;
+      }
+      __syncthreads();
       bool nb = s_stamp[zc][yc][xc - 1] == R || s_stamp[zc][yc][xc + 1] == R ||
                 s_stamp[zc][yc - 1][xc] == R || s_stamp[zc][yc + 1][xc] == R;
       if constexpr (D == 3) nb = nb || s_stamp[zc - 1][yc][xc] == R || s_stamp[zc + 1][yc][xc] == R;
@@ -602,6 +742,14 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
     }
     ++R;
 
+    // cells still pending are deferred to a later visit
+    {
+      const unsigned pend_bits = __ballot_sync(kFull, pv < kInfBits);
+      if (lane == 0) {
+        unsigned *pw = p.pend + static_cast<size_t>(tile) * kPendWords + warp;
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(pw), "r"(pend_bits) : "memory");
+      }
+    }
     // commit and collect the smallest committed time per tile face
     if (bits_of(tv) < bits_of(tv0)) {
       const unsigned long long tb = bits_of(tv);
@@ -635,11 +783,19 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
     }
     __syncthreads();
     if (tid == 0) {
+      if (m < kInfBits) {   // deferred cells: come back at their bucket, beyond this window
+        unsigned b = bucket_of_time(from_bits(m), inv_delta);
+        const unsigned bmin = s_lo + p.window + 1u;
+        if (b < bmin) b = bmin;
+        activate(p, static_cast<unsigned long long>(tile), 0u, b);
+      }
       finish_tile(p, static_cast<unsigned long long>(tile));
       __threadfence();
+      atomicAdd(&p.ctl->run[s_slot * kCounterPad], 0xffffffffu);
       atomicAdd(&p.ctl->work, -1);
       ++n_visits;
       n_rounds += rounds;
+      if (p.counters) visit_ns += static_cast<unsigned long long>(now_ns() - t_claim);
     }
   }
 
@@ -650,7 +806,7 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
       n_dec += __shfl_xor_sync(kFull, n_dec, o);
       n_commits += __shfl_xor_sync(kFull, n_commits, o);
     }
-    if ((tid & 31) == 0) {
+    if (lane == 0) {
       atomicAdd(&p.ctl->stats[kStatEvals], n_evals);
       atomicAdd(&p.ctl->stats[kStatDecreases], n_dec);
       atomicAdd(&p.ctl->stats[kStatCommits], n_commits);
@@ -658,6 +814,8 @@ __global__ void __launch_bounds__(TX * TY * TZ) persistent_kernel(SolveParams p)
     if (tid == 0) {
       atomicAdd(&p.ctl->stats[kStatVisits], n_visits);
       atomicAdd(&p.ctl->stats[kStatRounds], n_rounds);
+      atomicAdd(&p.ctl->stats[kStatVisitNs], visit_ns);
+      atomicAdd(&p.ctl->stats[kStatIdleNs], idle_ns);
     }
   }
 }
