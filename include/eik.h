@@ -80,6 +80,14 @@ typedef struct {
                               (look-ahead of the relaxed priority order); 0: default */
     double band;           /* in-tile acceptance band in units of (smallest h/v of the tile)
                               / sqrt(ndim), i.e. one cell's travel time; <= 0: default */
+    int arith;             /* arithmetic of d-bar: 1 = FP64 unit, 2 = exact emulation on the
+                              integer pipes (same results bit for bit); 0: default */
+    int sched_flags;       /* bit 0: the look-ahead window follows the lowest bucket holding
+                              queued entries only (tiles still running do not hold it) */
+    void *trace;           /* optional device buffer of trace_cap 32-byte visit records
+                              {int64 t_claim_ns, t_end_ns; uint32 tile, lowest bucket,
+                              rounds, flags}; NULL: no trace */
+    int64_t trace_cap;
 } eik_opts;
 
 /* Work accounting (the paper's good/empty/bad updates, Results section). */
@@ -96,6 +104,11 @@ typedef struct {
     int64_t visit_ns;      /* tile-visit time summed over CTAs (counters only) */
     int64_t idle_ns;       /* time CTAs spent looking for work (counters only) */
     int64_t ctas;          /* persistent CTAs launched */
+    int64_t trace_n;       /* visit records produced (only the first trace_cap are stored) */
+    int64_t detail[9];     /* counters >= 2 only: SM cycles of one thread per CTA spent in
+                              [0] tile load, [1] round phase A, [2] phase B, [3] phase C,
+                              [4] commit and activation; [5] Newton steps, [6] ulp-walk
+                              steps, [7] bisection fallbacks, [8] d-bar evaluations */
     double solve_ms;       /* device time of the persistent solve kernel(s), CUDA events
                               recorded on `stream` around each launch */
 } eik_stats;
@@ -132,6 +145,17 @@ typedef struct {
  * stats (optional) accumulates over the batch. */
 eik_status eik_solve_batched(const eik_problem *probs, int nprob, const eik_opts *opts,
                              eik_stats *stats, void *stream);
+
+/* Self-test of the exact arithmetic.  The solver evaluates d-bar with exact
+ * round-to-nearest binary64 operations emulated on the integer pipes (FP64 is
+ * scarce on GB300); this runs n random and tie-heavy trials on the current
+ * device, comparing each emulated result with the hardware FP64 unit (and
+ * d-bar with a plain bisection over G built from the hardware operations), bit
+ * for bit.  mismatches[16] receives: [0] x-y, [1] m*m, [2] x+y, [3] G 2D,
+ * [4] G 3D, [5] d-bar 2D, [6] d-bar 3D mismatch counts, [7] trials run,
+ * [8..14] the first failing trial index per check (-1 if none).  Allocates
+ * and frees a small device buffer; synchronises `stream`. */
+eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches, void *stream);
 
 /* Release the library's device workspace on the current device. */
 void eik_release(void);

@@ -33,17 +33,22 @@ class EikOpts(ctypes.Structure):
                 ("capacity", ctypes.c_int64), ("timeout_ms", ctypes.c_int64),
                 ("ctas_per_sm", ctypes.c_int), ("counters", ctypes.c_int),
                 ("test_stall", ctypes.c_int), ("window", ctypes.c_int),
-                ("band", ctypes.c_double)]
+                ("band", ctypes.c_double), ("arith", ctypes.c_int), ("sched_flags", ctypes.c_int),
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64)]
 
 
 class EikStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in
                 ("evals", "decreases", "good", "visits", "pushes", "stale_pops", "rounds",
-                 "retries", "max_queue", "visit_ns", "idle_ns", "ctas")] + \
-        [("solve_ms", ctypes.c_double)]
+                 "retries", "max_queue", "visit_ns", "idle_ns", "ctas", "trace_n")] + \
+        [("detail", ctypes.c_int64 * 9), ("solve_ms", ctypes.c_double)]
+
+    DETAIL = ["cyc_load", "cyc_a", "cyc_b", "cyc_c", "cyc_commit", "newton", "walk", "bisect",
+              "dbar_calls"]
 
     def as_dict(self) -> dict:
-        d = {n: getattr(self, n) for n, _ in self._fields_}
+        d = {n: getattr(self, n) for n, _ in self._fields_ if n != "detail"}
+        d.update({k: int(self.detail[i]) for i, k in enumerate(self.DETAIL)})
         d["empty"] = d["evals"] - d["decreases"]
         d["bad"] = d["decreases"] - d["good"]
         return d
@@ -90,12 +95,29 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     L.eik_last_error.restype = ctypes.c_char_p
     L.eik_abi_version.argtypes = []
     L.eik_abi_version.restype = ctypes.c_int
+    L.eik_selftest.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64), vp]
+    L.eik_selftest.restype = ctypes.c_int
     _lib = L
     return L
 
 
 EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
-            "eik_abi_version"]
+            "eik_abi_version", "eik_selftest"]
+
+SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3"]
+
+
+def eik_selftest(n: int = 1 << 20, seed: int = 1, stream=None) -> dict:
+    """Bit-exact check of the integer-pipe arithmetic against the FP64 unit."""
+    L = load_library()
+    out = (ctypes.c_int64 * 16)()
+    rc = L.eik_selftest(int(n), int(seed) & ((1 << 64) - 1), out, _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, "selftest failed to run")
+    res = {k: int(out[i]) for i, k in enumerate(SELFTEST_CHECKS)}
+    res["trials"] = int(out[7])
+    res["first"] = {k: int(out[8 + i]) for i, k in enumerate(SELFTEST_CHECKS)}
+    return res
 
 
 def eik_status_str(status: int) -> str:

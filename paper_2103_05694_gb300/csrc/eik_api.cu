@@ -61,7 +61,7 @@ struct DevBuf {
 
 struct Workspace {
   int device = -1;
-  DevBuf<double> r;            // fl(h/v) per cell, all problems
+  DevBuf<double> r;            // c = fl(fl(h/v)^2) per cell, all problems
   DevBuf<double> t_stage;      // host out_t staging
   DevBuf<double> v_stage;      // host speed staging
   DevBuf<unsigned long long> state;
@@ -298,7 +298,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     P.ntz = (P.nz + tz - 1) / tz;
     P.tile_base = total_tiles;
     total_tiles += P.ntx * P.nty * P.ntz;
-    P.r = g_ws.r.p + speed_off[prob_speed[i]];
+    P.c = g_ws.r.p + speed_off[prob_speed[i]];
     if (hp.out_dev) {
       P.t = hp.out;
     } else {
@@ -367,8 +367,8 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
       vsrc = g_ws.v_stage.p + v_off;
       v_off += speed_n[j];
     }
-    CK(eik::launch_init_r(vsrc, speed_h[j], g_ws.r.p + speed_off[j], speed_n[j], g_ws.ctl.p, stream),
-       "init_r launch");
+    CK(eik::launch_init_c(vsrc, speed_h[j], g_ws.r.p + speed_off[j], speed_n[j], g_ws.ctl.p, stream),
+       "init_c launch");
   }
   for (auto &P : probs) CK(eik::launch_init_t(P.t, P.nx * P.ny * P.nz, stream), "init_t launch");
 
@@ -381,6 +381,11 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.pend = g_ws.pend.p;
   sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow);
   sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand;
+  sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
+  sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
+  sp.trace = opts && opts->trace && opts->trace_cap > 0 ? static_cast<eik::TraceRec *>(opts->trace)
+                                                        : nullptr;
+  sp.trace_cap = sp.trace ? (unsigned long long)opts->trace_cap : 0ull;
   sp.slots = g_ws.slots.p;
   sp.cap_mask = (unsigned)(g_ws.cap - 1);
   sp.ctl = g_ws.ctl.p;
@@ -394,7 +399,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   CK(eik::launch_seed(sp, g_ws.seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
      "seed launch");
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : 0;
-  const int occ = eik::persistent_blocks_per_sm(ndim);
+  const int occ = eik::persistent_blocks_per_sm(ndim, sp.arith);
   if (per_sm <= 0 || per_sm > occ) per_sm = occ;
   int dev_sms = 0;
   CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g_ws.device), "SM count");
@@ -427,6 +432,8 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     acc.visit_ns += (int64_t)c.stats[eik::kStatVisitNs];
     acc.idle_ns += (int64_t)c.stats[eik::kStatIdleNs];
     acc.ctas = grid;
+    acc.trace_n = (int64_t)c.trace_n;
+    for (int k = 0; k < 9; ++k) acc.detail[k] += (int64_t)c.stats[eik::kStatCycLoad + k];
     if (status != eik::kEcapacity || attempt >= kMaxRetries ||
         g_ws.cap * 4 * eik::kNumSlots > kMaxCapEntries) break;
     // grow the frontier, clear the scheduler (keep delta) and resume

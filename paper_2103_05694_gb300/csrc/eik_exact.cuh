@@ -1,0 +1,461 @@
+// Exact binary64 round-to-nearest-even arithmetic on the integer pipes, for the
+// operations the exactly monotone update d-bar needs (section "Achieving Exact
+// Monotonicity with Finite Precision Arithmetic"): x - y for x > y >= 0, m * m
+// for m >= 0, x + y for x, y >= 0, and comparisons of non-negative values as
+// bit patterns.
+//
+// Why: on GB300 an FP64 warp instruction occupies its sub-partition's FP64
+// pipe for ~80 cycles (1.6 FP64 lanes per clock per SM) with 64-cycle latency,
+// while 32-bit integer instructions issue every 1-2 cycles.  The operations
+// below use 15-25 integer instructions each.
+//
+// Each function is the IEEE-754 definition written out: align the significands
+// with guard bits and a sticky bit, add or subtract (or multiply to 128 bits),
+// normalise, round to nearest with ties to even.  Operands outside a safe
+// exponent window (subnormals, results near overflow or underflow) are passed
+// to the hardware intrinsics instead, so every result is the correctly rounded
+// IEEE result for every input.  A self-test kernel (eik_selftest) compares
+// these functions with the hardware FP64 unit on random and tie-heavy inputs.
+#pragma once
+
+#include <cstdint>
+
+namespace eik {
+namespace xf {
+
+constexpr unsigned long long kFrac = (1ull << 52) - 1;
+constexpr unsigned long long kHidden = 1ull << 52;
+constexpr unsigned long long kInf = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ double as_d(unsigned long long u) {
+  return __longlong_as_double(static_cast<long long>(u));
+}
+__device__ __forceinline__ unsigned long long as_u(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x));
+}
+
+// Round to nearest, ties to even, and pack.  The exact value is z + f with
+// 0 <= f < 1 in units of z's last bit (f > 0 exactly when `sticky`), its
+// leading 1 at bit `top` (63 or 62).  The significand is bits top..top-52;
+// the bits below decide the rounding: above half rounds up, exactly half
+// (rest == half and f == 0) rounds to even.  e is the biased exponent that
+// goes with a significand whose leading 1 sits at bit 52.
+__device__ __forceinline__ unsigned long long round_pack(unsigned long long z, int top, bool sticky,
+                                                         int e) {
+  const int sh = top - 52;                       // 11 or 10
+  unsigned long long m = z >> sh;
+  const unsigned long long rest = z & ((1ull << sh) - 1ull);
+  const unsigned long long half = 1ull << (sh - 1);
+  if (rest > half || (rest == half && (sticky || (m & 1ull)))) m += 1ull;
+  if (m >> 53) {
+    m >>= 1;
+    ++e;
+  }
+  if (e >= 2047) return kInf;
+  return (static_cast<unsigned long long>(e) << 52) | (m & kFrac);
+}
+
+// fl(x - y) for bit patterns with x > y >= 0, x finite.
+__device__ __forceinline__ unsigned long long sub_pos(unsigned long long x, unsigned long long y) {
+  if (y == 0ull) return x;
+  const int ex = static_cast<int>(x >> 52), ey = static_cast<int>(y >> 52);
+  if (ex < 64 || ey == 0 || ex > 2045) return as_u(__dsub_rn(as_d(x), as_d(y)));
+  const unsigned long long X = ((x & kFrac) | kHidden) << 10;
+  const unsigned long long Ys = ((y & kFrac) | kHidden) << 10;
+  const int d = ex - ey;
+  unsigned long long Y;
+  bool sticky;
+  if (d >= 63) {
+    Y = 0ull;
+    sticky = true;
+  } else {
+    Y = Ys >> d;
+    sticky = (Y << d) != Ys;
+  }
+  // exact difference = (X - Y) - f with 0 < f < 1 when sticky: Z + (1 - f)
+  const unsigned long long Z = X - Y - (sticky ? 1ull : 0ull);
+  const int lz = __clzll(static_cast<long long>(Z));
+  return round_pack(Z << lz, 63, sticky, ex + 1 - lz);
+}
+
+// fl(m * m) for a bit pattern m >= 0.
+__device__ __forceinline__ unsigned long long sq(unsigned long long m) {
+  if (m == 0ull) return 0ull;
+  const int e = static_cast<int>(m >> 52);
+  if (e < 600 || e > 1500) return as_u(__dmul_rn(as_d(m), as_d(m)));
+  const unsigned long long P = ((m & kFrac) | kHidden) << 11;   // bit 63 set
+  const unsigned long long hi = __umul64hi(P, P);
+  const unsigned long long lo = P * P;
+  const int top = static_cast<int>(hi >> 63);
+  const unsigned long long H = top ? hi : ((hi << 1) | (lo >> 63));
+  const unsigned long long L = top ? lo : (lo << 1);
+  return round_pack(H, 63, L != 0ull, 2 * e - 1023 + top);
+}
+
+// fl(x + y) for bit patterns x, y >= 0.
+__device__ __forceinline__ unsigned long long add_pos(unsigned long long x, unsigned long long y) {
+  if (y > x) {
+    const unsigned long long t = x;
+    x = y;
+    y = t;
+  }
+  if (y == 0ull) return x;
+  const int ex = static_cast<int>(x >> 52), ey = static_cast<int>(y >> 52);
+  if (ey == 0 || ex > 2045) return as_u(__dadd_rn(as_d(x), as_d(y)));
+  const unsigned long long X = ((x & kFrac) | kHidden) << 10;
+  const unsigned long long Ys = ((y & kFrac) | kHidden) << 10;
+  const int d = ex - ey;
+  unsigned long long Y;
+  bool sticky;
+  if (d >= 63) {
+    Y = 0ull;
+    sticky = true;
+  } else {
+    Y = Ys >> d;
+    sticky = (Y << d) != Ys;
+  }
+  const unsigned long long Z = X + Y;            // exact value: Z + f, 0 <= f < 1
+  if (Z >> 63) return round_pack(Z, 63, sticky, ex + 1);
+  return round_pack(Z, 62, sticky, ex);
+}
+
+// m = max(fl(tau - a), +0) for tau, a >= 0 (a may be +inf).
+__device__ __forceinline__ unsigned long long upwind_diff(unsigned long long tau, unsigned long long a) {
+  return tau > a ? sub_pos(tau, a) : 0ull;
+}
+
+// Approximate conversions by bit manipulation (no FP64-pipe conversion
+// instructions).  Used only for the starting guess and Newton steps, whose
+// accuracy does not affect the result.  to_f: truncates to fp32 (flushes
+// values below the fp32 normal range to 0, saturates above it to +inf).
+__device__ __forceinline__ float to_f(unsigned long long u) {
+  const int e = static_cast<int>((u >> 52) & 0x7ffu) - 1023 + 127;
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __int_as_float(0x7f800000);
+  return __int_as_float((e << 23) | static_cast<int>((u >> 29) & 0x7fffffu));
+}
+// fp32 (>= 0, finite) to the bit pattern of the equal double (exact).
+__device__ __forceinline__ unsigned long long from_f(float f) {
+  const unsigned b = __float_as_uint(f) & 0x7fffffffu;
+  const unsigned e = b >> 23;
+  if (e == 0u) return 0ull;                       // zero or fp32 subnormal: 0 is fine here
+  return (static_cast<unsigned long long>(e - 127u + 1023u) << 52) |
+         (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
+}
+
+__device__ __forceinline__ unsigned long long umin(unsigned long long a, unsigned long long b) {
+  return a < b ? a : b;
+}
+__device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigned long long b) {
+  return a < b ? b : a;
+}
+
+// G(tau) = fl(fl(q_x + q_y) + q_z), q_k = fl(m_k * m_k), m_k = max(fl(tau - a_k), 0),
+// terms in axis order; all arguments and the result are bit patterns (>= 0).
+template <int D>
+__device__ __forceinline__ unsigned long long G(unsigned long long tau, const unsigned long long (&a)[D]) {
+  unsigned long long g = sq(upwind_diff(tau, a[0]));
+#pragma unroll
+  for (int k = 1; k < D; ++k) g = add_pos(g, sq(upwind_diff(tau, a[k])));
+  return g;
+}
+
+// G(tau) and, in fp32, the sum of the upwind differences (G' / 2) for Newton.
+template <int D>
+__device__ __forceinline__ unsigned long long G_slope(unsigned long long tau,
+                                                      const unsigned long long (&a)[D], float &msum) {
+  unsigned long long m = upwind_diff(tau, a[0]);
+  msum = to_f(m);
+  unsigned long long g = sq(m);
+#pragma unroll
+  for (int k = 1; k < D; ++k) {
+    m = upwind_diff(tau, a[k]);
+    msum += to_f(m);
+    g = add_pos(g, sq(m));
+  }
+  return g;
+}
+
+// ulp of a positive normal double, as fp32 (0 when below the fp32 range).
+__device__ __forceinline__ float ulp_f(unsigned long long tau) {
+  const int e = static_cast<int>(tau >> 52) - 1075 + 127;
+  return e > 0 && e < 255 ? __int_as_float(e << 23) : 0.0f;
+}
+
+// d-bar: the smallest double tau with G(tau) >= c, for axis minima a (bit
+// patterns, at least one finite) and c = fl(r*r) > 0.  Starting point: the
+// one-sided root a_0 + r, else the quadratic root of the two (three) smallest
+// minima, in fp32; refined by Newton steps on G(tau) - c with the exact G (G
+// is convex and continuously differentiable above a_0); finished by the exact
+// test G(tau) >= c > G(prev(tau)) with at most a few ulp steps; bisection over
+// bit patterns if the walk does not end there.  Only the finish decides the
+// result, so the guess and the Newton steps only affect speed.
+template <int D>
+__device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned long long cb) {
+  unsigned long long s0 = a[0];
+  unsigned long long s1 = D > 1 ? a[1] : kInf;
+  unsigned long long s2 = D > 2 ? a[2] : kInf;
+  {
+    const unsigned long long lo = umin(s0, s1), hi = umax(s0, s1);
+    s0 = lo;
+    s1 = hi;
+    if (D > 2) {
+      const unsigned long long l2 = umin(s1, s2), h2 = umax(s1, s2);
+      s2 = h2;
+      s1 = umax(s0, l2);
+      s0 = umin(s0, l2);
+    }
+  }
+  const float cf = to_f(cb);
+  const float rf = sqrtf(cf);
+  float w = rf;
+  if (s1 != kInf) {
+    const float u1 = to_f(upwind_diff(s1, s0));
+    if (u1 < rf) {
+      w = 0.5f * (u1 + sqrtf(fmaxf(2.0f * cf - u1 * u1, 0.0f)));
+      if (D > 2 && s2 != kInf) {
+        const float u2 = to_f(upwind_diff(s2, s0));
+        if (w > u2) {
+          const float s = u1 + u2;
+          const float disc = s * s - 3.0f * (u1 * u1 + u2 * u2 - cf);
+          if (disc >= 0.0f) w = (s + sqrtf(disc)) * (1.0f / 3.0f);
+        }
+      }
+    }
+  }
+  unsigned long long tau = add_pos(s0, from_f(w));
+  if (tau <= s0) tau = s0 + 1ull;
+  unsigned long long g = kInf;
+  bool have_g = false;
+#pragma unroll 1
+  for (int it = 0; it < 3; ++it) {
+    float msum;
+    g = G_slope<D>(tau, a, msum);
+    have_g = true;
+    if (!(msum > 0.0f) || g >= kInf) break;
+    const float alpha = g >= cb ? to_f(upwind_diff(g, cb)) : -to_f(sub_pos(cb, g));
+    const float step = __fdividef(alpha, 2.0f * msum);
+    if (fabsf(step) <= 0.25f * ulp_f(tau)) break;   // the root is within this ulp
+    const unsigned long long sb = from_f(fabsf(step));
+    unsigned long long nt = step > 0.0f ? (tau > sb ? sub_pos(tau, sb) : s0 + 1ull) : add_pos(tau, sb);
+    if (nt <= s0) nt = s0 + 1ull;
+    if (nt == tau) break;
+    tau = nt;
+    have_g = false;
+  }
+  if (!have_g) g = G<D>(tau, a);
+  unsigned long long lo, hi;
+  if (g >= cb) {
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+      if (tau - 1ull <= s0) return tau;                  // G(a_0) = 0 < c
+      if (G<D>(tau - 1ull, a) < cb) return tau;
+      --tau;
+    }
+    hi = tau;
+    lo = s0;
+  } else {
+    lo = tau;
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+      ++tau;
+      if (G<D>(tau, a) >= cb) return tau;
+      lo = tau;
+    }
+    unsigned long long step = 1ull;
+    hi = lo + 1ull;
+#pragma unroll 1
+    while (hi < kInf && G<D>(hi, a) < cb) {
+      lo = hi;
+      step <<= 1;
+      hi = umin(lo + step, kInf);
+    }
+  }
+#pragma unroll 1
+  while (hi - lo > 1ull) {       // G(lo) < c <= G(hi)
+    const unsigned long long mid = lo + (hi - lo) / 2ull;
+    if (G<D>(mid, a) >= cb) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// One application of the update operator to a non-source cell whose best
+// known value is `best`: true and the new value if it decreases.  A decrease
+// needs a finite neighbour below best (d-bar > min a_k) and G(prev(best)) >= c
+// (then d-bar <= prev(best)).
+template <int D>
+__device__ __forceinline__ bool relax(unsigned long long best, const unsigned long long (&a)[D],
+                                      unsigned long long cb, unsigned long long &out) {
+  unsigned long long amin = a[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) amin = umin(amin, a[k]);
+  if (amin >= kInf || best <= amin) return false;
+  if (best < kInf && G<D>(best - 1ull, a) < cb) return false;
+  out = dbar<D>(a, cb);
+  return true;
+}
+
+}  // namespace xf
+}  // namespace eik
+
+namespace eik {
+namespace hw {
+
+// The same update on the hardware FP64 unit: every operation of G an explicit
+// round-to-nearest intrinsic (never contracted into an FMA); the guess uses
+// the d-hat form of the quadratic root with a hardware sqrt; the finish is the
+// exact ulp test.  Same interface as xf::relax (bit patterns in and out).
+using xf::as_d;
+using xf::as_u;
+using xf::kInf;
+
+template <int D>
+__device__ __forceinline__ unsigned long long G(unsigned long long tau, const unsigned long long (&a)[D]) {
+  double m = __dsub_rn(as_d(tau), as_d(a[0]));
+  m = (__double_as_longlong(m) < 0) ? 0.0 : m;
+  double g = __dmul_rn(m, m);
+#pragma unroll
+  for (int k = 1; k < D; ++k) {
+    double mk = __dsub_rn(as_d(tau), as_d(a[k]));
+    mk = (__double_as_longlong(mk) < 0) ? 0.0 : mk;
+    g = __dadd_rn(g, __dmul_rn(mk, mk));
+  }
+  return as_u(g);
+}
+
+// G(tau) on the FP64 unit and, in fp32 (bit conversions, no FP64 pipe), the
+// sum of the upwind differences.
+template <int D>
+__device__ __forceinline__ unsigned long long G_slope(unsigned long long tau,
+                                                      const unsigned long long (&a)[D], float &msum) {
+  double m = __dsub_rn(as_d(tau), as_d(a[0]));
+  m = (__double_as_longlong(m) < 0) ? 0.0 : m;
+  msum = xf::to_f(as_u(m));
+  double g = __dmul_rn(m, m);
+#pragma unroll
+  for (int k = 1; k < D; ++k) {
+    double mk = __dsub_rn(as_d(tau), as_d(a[k]));
+    mk = (__double_as_longlong(mk) < 0) ? 0.0 : mk;
+    msum += xf::to_f(as_u(mk));
+    g = __dadd_rn(g, __dmul_rn(mk, mk));
+  }
+  return as_u(g);
+}
+
+// d-bar with the exact G on the FP64 unit: fp32 starting guess (one-sided
+// root, else the quadratic root of the smallest two (three) minima), Newton
+// steps on G(tau) - c, then the exact test G(tau) >= c > G(prev(tau)) with a
+// few ulp steps and bisection as the last resort.  About 20 FP64
+// instructions in the common case.
+template <int D>
+__device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned long long cb,
+                                   unsigned *path = nullptr) {
+  unsigned long long s0 = a[0];
+  unsigned long long s1 = D > 1 ? a[1] : kInf;
+  unsigned long long s2 = D > 2 ? a[2] : kInf;
+  {
+    const unsigned long long lo = xf::umin(s0, s1), hi = xf::umax(s0, s1);
+    s0 = lo;
+    s1 = hi;
+    if (D > 2) {
+      const unsigned long long l2 = xf::umin(s1, s2), h2 = xf::umax(s1, s2);
+      s2 = h2;
+      s1 = xf::umax(s0, l2);
+      s0 = xf::umin(s0, l2);
+    }
+  }
+  const float cf = xf::to_f(cb);
+  const float rf = sqrtf(cf);
+  float w = rf;
+  if (s1 != kInf) {
+    const float u1 = xf::to_f(as_u(__dsub_rn(as_d(s1), as_d(s0))));
+    if (u1 < rf) {
+      w = 0.5f * (u1 + sqrtf(fmaxf(2.0f * cf - u1 * u1, 0.0f)));
+      if (D > 2 && s2 != kInf) {
+        const float u2 = xf::to_f(as_u(__dsub_rn(as_d(s2), as_d(s0))));
+        if (w > u2) {
+          const float s = u1 + u2;
+          const float disc = s * s - 3.0f * (u1 * u1 + u2 * u2 - cf);
+          if (disc >= 0.0f) w = (s + sqrtf(disc)) * (1.0f / 3.0f);
+        }
+      }
+    }
+  }
+  unsigned long long tau = as_u(__dadd_rn(as_d(s0), as_d(xf::from_f(w))));
+  if (tau <= s0 || tau >= kInf) tau = s0 + 1ull;
+  unsigned long long g = kInf;
+  bool have_g = false;
+#pragma unroll 1
+  for (int it = 0; it < 3; ++it) {
+    float msum;
+    g = G_slope<D>(tau, a, msum);
+    have_g = true;
+    if (path) path[0] += 1u;
+    if (!(msum > 0.0f) || g >= kInf) break;
+    const float alpha = g >= cb ? xf::to_f(as_u(__dsub_rn(as_d(g), as_d(cb))))
+                                : -xf::to_f(as_u(__dsub_rn(as_d(cb), as_d(g))));
+    const float step = __fdividef(alpha, 2.0f * msum);
+    if (fabsf(step) <= 0.25f * xf::ulp_f(tau)) break;   // the root is within this ulp
+    unsigned long long sb = xf::from_f(fabsf(step));
+    if (step < 0.0f) sb |= 1ull << 63;                 // tau - step, sign set on the bits
+    unsigned long long nt = as_u(__dsub_rn(as_d(tau), as_d(sb)));
+    if (nt <= s0 || nt >= kInf) nt = s0 + 1ull;
+    if (nt == tau) break;
+    tau = nt;
+    have_g = false;
+  }
+  if (!have_g) g = G<D>(tau, a);
+  unsigned long long lo, hi;
+  if (g >= cb) {
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+      if (path) path[1] += 1u;
+      if (tau - 1ull <= s0) return tau;
+      if (G<D>(tau - 1ull, a) < cb) return tau;
+      --tau;
+    }
+    hi = tau;
+    lo = s0;
+  } else {
+    lo = tau;
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+      if (path) path[1] += 1u;
+      ++tau;
+      if (G<D>(tau, a) >= cb) return tau;
+      lo = tau;
+    }
+    unsigned long long step = 1ull;
+    hi = lo + 1ull;
+#pragma unroll 1
+    while (hi < kInf && G<D>(hi, a) < cb) {
+      lo = hi;
+      step <<= 1;
+      hi = xf::umin(lo + step, kInf);
+    }
+  }
+  if (path) path[2] += 1u;
+#pragma unroll 1
+  while (hi - lo > 1ull) {
+    const unsigned long long mid = lo + (hi - lo) / 2ull;
+    if (G<D>(mid, a) >= cb) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+template <int D>
+__device__ __forceinline__ bool relax(unsigned long long best, const unsigned long long (&a)[D],
+                                      unsigned long long cb, unsigned long long &out,
+                                      unsigned *path = nullptr) {
+  unsigned long long amin = a[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) amin = xf::umin(amin, a[k]);
+  if (amin >= kInf || best <= amin) return false;
+  if (best < kInf && G<D>(best - 1ull, a) < cb) return false;
+  if (path) path[3] += 1u;
+  out = dbar<D>(a, cb, path);
+  return true;
+}
+
+}  // namespace hw
+}  // namespace eik

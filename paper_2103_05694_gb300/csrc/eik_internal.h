@@ -23,7 +23,10 @@ constexpr unsigned kOk = 0, kEinval = 1, kEcapacity = 3, kEtimeout = 4;
 
 enum StatIdx {
   kStatEvals = 0, kStatDecreases, kStatVisits, kStatPushes, kStatStale, kStatRounds,
-  kStatCommits, kStatMaxQueue, kStatVisitNs, kStatIdleNs, kNumStats
+  kStatCommits, kStatMaxQueue, kStatVisitNs, kStatIdleNs,
+  // detailed timing (counters >= 2): cycles of thread 0 per phase, d-bar paths
+  kStatCycLoad, kStatCycA, kStatCycB, kStatCycC, kStatCycCommit,
+  kStatNewton, kStatWalk, kStatBisect, kStatDbarCalls, kNumStats
 };
 
 // Control block, zeroed before every solve.
@@ -44,6 +47,7 @@ struct Ctl {
   int pad3[22];
   unsigned long long stats[kNumStats];
   unsigned long long error_info[4];   // where a wait gave up / what was invalid
+  unsigned long long trace_n;         // trace records written (may exceed the capacity)
   unsigned push[kNumSlots * kCounterPad];
   unsigned pop[kNumSlots * kCounterPad];
   unsigned run[kNumSlots * kCounterPad];   // tiles claimed from the slot and still running
@@ -52,7 +56,7 @@ struct Ctl {
 // One grid of a (possibly batched) solve, as the kernels see it.
 struct Prob {
   double *t;                // arrival times (working field and result)
-  const double *r;          // per cell fl(h / v)
+  const double *c;          // per cell c = fl(fl(h / v)^2)
   const int64_t *src_idx;   // sorted unique source indices (device)
   const double *src_t;      // their times (device), same order
   int64_t nsrc;
@@ -77,16 +81,27 @@ struct SolveParams {
   int test_stall;
   unsigned window;                // buckets above the lowest active one that may be popped
   double band;                    // in-tile acceptance band, in units of min r / sqrt(D)
+  int arith;                      // kArithFp64 or kArithInt
+  int gate_pending_only;          // window follows pending entries only, not running tiles
+  struct TraceRec *trace;         // optional visit trace (device), NULL when off
+  unsigned long long trace_cap;
+};
+
+// One tile visit, for timeline analysis (opts.trace).
+struct TraceRec {
+  long long t_claim, t_end;       // %globaltimer ns
+  unsigned tile, lo, rounds, flags;   // flags: bit 0 deferred cells, bits 8.. CTA index
 };
 
 constexpr int kPendWords = 8;            // 256 cells per tile / 32
+constexpr int kArithFp64 = 1, kArithInt = 2;   // d-bar on the FP64 unit / on the integer pipes
 
 // Tile shapes (cells): one thread per cell, 256 threads per CTA.
 constexpr int kTX2 = 32, kTY2 = 8;                 // 2D
 constexpr int kTX3 = 16, kTY3 = 4, kTZ3 = 4;       // 3D
 
 // Launch wrappers (eik_solver.cu).  All enqueue on `stream`.
-cudaError_t launch_init_r(const double *speed, double h, double *r, int64_t n, Ctl *ctl,
+cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
                           cudaStream_t stream);
 cudaError_t launch_init_t(double *t, int64_t n, cudaStream_t stream);
 // One source of one problem, flattened over the batch for the seed kernel.
@@ -103,6 +118,6 @@ cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int npro
 cudaError_t launch_persistent(const SolveParams &p, int grid, cudaStream_t stream);
 cudaError_t launch_count_finite(const Prob *host_probs, int nprob, unsigned long long *out,
                                 cudaStream_t stream);
-int persistent_blocks_per_sm(int ndim);
+int persistent_blocks_per_sm(int ndim, int arith);
 
 }  // namespace eik

@@ -31,6 +31,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "eik_exact.cuh"
 #include "eik_internal.h"
 
 namespace eik {
@@ -38,7 +39,6 @@ namespace {
 
 constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
 constexpr unsigned kFull = 0xffffffffu;
-constexpr int kWalk = 6;
 constexpr unsigned kMaxRounds = 1u << 20;   // per tile visit; never reached in practice
 
 __device__ __forceinline__ unsigned long long bits_of(double x) {
@@ -49,9 +49,6 @@ __device__ __forceinline__ double from_bits(unsigned long long u) {
 }
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) {
   return a < b ? a : b;
-}
-__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
-  return a < b ? b : a;
 }
 
 // Relaxed, GPU-scope accesses (never served from a stale L1 line).
@@ -94,126 +91,6 @@ __device__ void raise_status(Ctl *ctl, unsigned code, unsigned long long info) {
 }
 
 // ---------------------------------------------------------------------------
-// d-bar.  G(tau) = fl(fl(q_x + q_y) + q_z), q_k = fl(m_k * m_k),
-// m_k = max(fl(tau - a_k), +0): every operation an explicit round-to-nearest
-// intrinsic, so nothing is contracted into an FMA.  a_k = +inf gives
-// m_k = -inf -> +0.  Results are compared as bit patterns (all >= +0).
-// ---------------------------------------------------------------------------
-template <int D>
-__device__ __forceinline__ unsigned long long G_bits(double tau, const double (&a)[D]) {
-  double m = __dsub_rn(tau, a[0]);
-  m = (__double_as_longlong(m) < 0) ? 0.0 : m;
-  double g = __dmul_rn(m, m);
-#pragma unroll
-  for (int k = 1; k < D; ++k) {
-    double mk = __dsub_rn(tau, a[k]);
-    mk = (__double_as_longlong(mk) < 0) ? 0.0 : mk;
-    g = __dadd_rn(g, __dmul_rn(mk, mk));
-  }
-  return bits_of(g);
-}
-
-// Smallest double tau with G(tau) >= c, given at least one finite a_k.
-// Guess: one-sided update a_0 + r, else the rearranged quadratic root d-hat
-// (Mitigation Strategies), else its three-axis analogue; then the exact
-// answer by a short ulp walk, with bisection over bit patterns as the
-// fallback.  The guess only affects speed, never the result.
-template <int D>
-__device__ double dbar_dev(const double (&a)[D], double r, double c, unsigned long long cb) {
-  unsigned long long s0 = bits_of(a[0]);
-  unsigned long long s1 = D > 1 ? bits_of(a[1]) : kInfBits;
-  unsigned long long s2 = D > 2 ? bits_of(a[2]) : kInfBits;
-  {  // sort ascending as integers
-    unsigned long long lo = umin64(s0, s1), hi = umax64(s0, s1);
-    s0 = lo;
-    s1 = hi;
-    if (D > 2) {
-      unsigned long long l2 = umin64(s1, s2), h2 = umax64(s1, s2);
-      s2 = h2;
-      s1 = umax64(s0, l2);
-      s0 = umin64(s0, l2);
-    }
-  }
-  const double a0 = from_bits(s0);
-  double g = a0 + r;
-  if (s1 != kInfBits) {
-    const double a1 = from_bits(s1);
-    const double d = a1 - a0;
-    if (d < r) {
-      const double disc = 2.0 * c - d * d;
-      g = 0.5 * (a0 + a1 + sqrt(disc > 0.0 ? disc : 0.0));
-      if (D > 2 && s2 != kInfBits) {
-        const double a2 = from_bits(s2);
-        if (g > a2) {
-          const double u2 = a2 - a0, s = d + u2;
-          const double disc3 = s * s - 3.0 * (d * d + u2 * u2 - c);
-          if (disc3 >= 0.0) g = a0 + (s + sqrt(disc3)) * (1.0 / 3.0);
-        }
-      }
-    }
-  }
-  unsigned long long gb = bits_of(g);
-  if (!(gb > s0) || gb >= kInfBits) gb = s0 + 1;
-  unsigned long long lo, hi;
-  if (G_bits<D>(from_bits(gb), a) >= cb) {
-#pragma unroll 1
-    for (int i = 0; i < kWalk; ++i) {
-      if (gb - 1 <= s0) return from_bits(gb);  // G(a_0) = 0 < c
-      if (G_bits<D>(from_bits(gb - 1), a) < cb) return from_bits(gb);
-      --gb;
-    }
-    hi = gb;
-    lo = s0;
-  } else {
-    lo = gb;
-#pragma unroll 1
-    for (int i = 0; i < kWalk; ++i) {
-      ++gb;
-      if (G_bits<D>(from_bits(gb), a) >= cb) return from_bits(gb);
-      lo = gb;
-    }
-    unsigned long long step = 1;
-    hi = lo + 1;
-#pragma unroll 1
-    while (hi < kInfBits && G_bits<D>(from_bits(hi), a) < cb) {
-      lo = hi;
-      step <<= 1;
-      hi = umin64(lo + step, kInfBits);
-    }
-  }
-  // invariant: G(lo) < c <= G(hi)
-#pragma unroll 1
-  while (hi - lo > 1) {
-    const unsigned long long mid = lo + (hi - lo) / 2;
-    if (G_bits<D>(from_bits(mid), a) >= cb) hi = mid; else lo = mid;
-  }
-  return from_bits(hi);
-}
-
-// One application of the update operator at a non-source cell holding tv.
-// Returns true and the new value if the cell decreases.  A decrease needs a
-// finite neighbour below tv (d-bar > min a_k) and G(prev(tv)) >= c (then
-// d-bar <= prev(tv)); both tests are exact.
-template <int D>
-__device__ __forceinline__ bool relax_cell(double tv, const double (&a)[D], double r,
-                                           double &out) {
-  unsigned long long amin = bits_of(a[0]);
-#pragma unroll
-  for (int k = 1; k < D; ++k) amin = umin64(amin, bits_of(a[k]));
-  const unsigned long long tb = bits_of(tv);
-  if (amin >= kInfBits || tb <= amin) return false;
-  const double c = __dmul_rn(r, r);
-  const unsigned long long cb = bits_of(c);
-  if (tb < kInfBits && G_bits<D>(from_bits(tb - 1), a) < cb) return false;
-  out = dbar_dev<D>(a, r, c, cb);
-  return true;
-}
-
-__device__ __forceinline__ double min_time(double x, double y) {
-  return from_bits(umin64(bits_of(x), bits_of(y)));
-}
-
-// ---------------------------------------------------------------------------
 // Scheduler.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned long long make_state(unsigned long long st, unsigned bucket,
@@ -228,9 +105,9 @@ __device__ __forceinline__ unsigned faces_of(unsigned long long s) {
   return static_cast<unsigned>((s >> 32) & 0x7full);
 }
 
-__device__ __forceinline__ unsigned bucket_of_time(double t, double inv_delta) {
-  const double q = t * inv_delta;
-  if (!(q < static_cast<double>(kMaxBucket))) return kMaxBucket;
+__device__ __forceinline__ unsigned bucket_of_time(unsigned long long tb, float inv_delta) {
+  const float q = __double2float_rn(from_bits(tb)) * inv_delta;
+  if (!(q < static_cast<float>(kMaxBucket))) return kMaxBucket;
   return static_cast<unsigned>(q);
 }
 
@@ -392,7 +269,7 @@ __device__ unsigned long long pop_entry(const SolveParams &p, long long &idle_si
       s = (cur + base + lane) & (kNumSlots - 1);
       q = ld_rlx(&ctl->pop[s * kCounterPad]);
       pp = ld_rlx(&ctl->push[s * kCounterPad]);
-      const unsigned rn = ld_rlx(&ctl->run[s * kCounterPad]);
+      const unsigned rn = p.gate_pending_only ? 0u : ld_rlx(&ctl->run[s * kCounterPad]);
       pend = static_cast<int>(pp - q) > 0;
       const unsigned act = __ballot_sync(kFull, pend || rn > 0u);
       if (act) {
@@ -481,7 +358,7 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 // + 1) * delta are deferred: recorded in the tile's pending mask and the tile
 // re-queued at their bucket.  Only accepted values are written to memory.
 // ---------------------------------------------------------------------------
-template <int D, int TX, int TY, int TZ>
+template <int D, int TX, int TY, int TZ, int ARITH>
 __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams p) {
   constexpr int NT = TX * TY * TZ;
   static_assert(NT == 32 * kPendWords, "one pending bit per cell");
@@ -490,19 +367,19 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
   static_assert(32 % TX == 0 || TX == 32, "a tile row must not straddle warps");
   __shared__ double s_t[SZ][SY][SX];
   __shared__ unsigned s_stamp[SZ][SY][SX];
-  __shared__ double s_a[D][NT];            // axis minima of the cells on the list
-  __shared__ double s_r[NT];               // r of each cell of the tile
+  __shared__ unsigned long long s_a[D][NT];  // axis minima of the cells on the list
+  __shared__ unsigned long long s_c[NT];     // c = fl(fl(h/v)^2) of each cell of the tile
   __shared__ unsigned long long s_best[NT];  // value a candidate must beat
-  __shared__ unsigned long long s_cand[NT];  // candidate produced this round
+  __shared__ unsigned long long s_pv[NT];    // pending candidate of each cell (owner-indexed)
   __shared__ unsigned short s_list[NT];    // cells whose update needs FP64 this round
   __shared__ int s_cnt[2];
   __shared__ unsigned long long s_facemin[6];
-  __shared__ unsigned long long s_min[2];
-  __shared__ unsigned long long s_rmin;
+  __shared__ unsigned long long s_min[3];
+  __shared__ unsigned long long s_cmin;
   __shared__ unsigned long long s_vlim;
-  __shared__ double s_band;
+  __shared__ unsigned long long s_band;
   __shared__ long long s_tile;
-  __shared__ int s_prob, s_faces, s_hassrc;
+  __shared__ int s_prob, s_faces;
   __shared__ unsigned s_slot, s_lo;
 
   const int tid = threadIdx.x;
@@ -511,11 +388,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
   const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
   const int xc = lx + 1, yc = ly + 1, zc = lz + HZ;
   for (int i = tid; i < SZ * SY * SX; i += NT) (&s_stamp[0][0][0])[i] = 0u;
-  s_cand[tid] = kInfBits;
-  if (tid == 0) { s_rmin = kInfBits; s_min[0] = s_min[1] = kInfBits; s_cnt[0] = s_cnt[1] = 0; }
+  s_pv[tid] = kInfBits;
+  if (tid == 0) { s_cmin = kInfBits; s_min[0] = s_min[1] = s_min[2] = kInfBits; s_cnt[0] = s_cnt[1] = 0; }
   const double delta = p.ctl->delta;
-  const double inv_delta = p.ctl->inv_delta;
-  const double band_scale = p.band / sqrt(static_cast<double>(D));
+  const float inv_delta = static_cast<float>(p.ctl->inv_delta);
+  const float band_scale = static_cast<float>(p.band) * rsqrtf(static_cast<float>(D));
   if (p.test_stall && tid == 0) {   // testing aid: wait on a flag nothing sets
     const long long t0 = now_ns();
     while (ld_rlx(&p.ctl->never_set) == 0u) {
@@ -526,6 +403,9 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
   unsigned R = 1;
   unsigned long long n_evals = 0, n_dec = 0, n_commits = 0, n_visits = 0, n_rounds = 0;
   unsigned long long visit_ns = 0, idle_ns = 0;
+  unsigned path[4] = {0u, 0u, 0u, 0u};          // newton, walk, bisect, dbar calls
+  unsigned long long cyc[5] = {0ull, 0ull, 0ull, 0ull, 0ull};   // load, A, B, C, commit
+  long long c0 = 0;
   long long idle_since = 0, t_claim = 0;
   __syncthreads();
 
@@ -535,7 +415,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       long long tile = -1;
       int faces = 0;
       unsigned slot = 0, lo = 0;
-      const long long t_pop = p.counters ? now_ns() : 0;
+      const long long t_pop = (p.counters || p.trace) ? now_ns() : 0;
 #pragma unroll 1
       for (;;) {
         const unsigned long long e = pop_entry(p, idle_since, slot, lo);
@@ -554,22 +434,20 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       }
       if (tid == 0) {
         idle_since = 0;
-        if (p.counters) {
+        if (p.counters || p.trace) {
           t_claim = now_ns();
           idle_ns += static_cast<unsigned long long>(t_claim - t_pop);
         }
-        int prob = 0, hs = 0;
+        int prob = 0;
         if (tile >= 0) {
           __threadfence();  // the claim is ordered before the tile's loads
           prob = find_prob(p, static_cast<unsigned long long>(tile));
-          hs = p.tile_src[tile];
           const double vlim = static_cast<double>(lo + p.window + 1u) * delta;
           s_vlim = bits_of(vlim);
         }
         s_tile = tile;
         s_faces = faces;
         s_prob = prob;
-        s_hassrc = hs;
         s_slot = slot;
         s_lo = lo;
       }
@@ -577,6 +455,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
     __syncthreads();
     const long long tile = s_tile;
     if (tile < 0) break;
+    const bool timing = p.counters >= 2 && tid == 0;
+    if (timing) c0 = clock64();
     const int faces = s_faces;
     const Prob &P = p.probs[s_prob];
     double *const T = P.t;
@@ -590,19 +470,21 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
     const int64_t gidx = (gz * ny + gy) * nx + gx;
 
     double tv = present ? ld_time(T + gidx) : from_bits(kInfBits);
-    const double rv = present ? __ldg(P.r + gidx) : 1.0;
+    const unsigned long long cv =
+        present ? static_cast<unsigned long long>(__ldg(reinterpret_cast<const long long *>(P.c) + gidx))
+                : kInfBits;
     bool active = present;
-    if (s_hassrc && present && is_source(P, gidx)) active = false;
+    if (p.tile_src[tile] && present && is_source(P, gidx)) active = false;
     s_t[zc][yc][xc] = tv;
-    s_r[tid] = rv;
+    s_c[tid] = cv;
     unsigned pword = 0;
     if (lane == 0) pword = ld_rlx(p.pend + static_cast<size_t>(tile) * kPendWords + warp);
     pword = __shfl_sync(kFull, pword, 0);
-    {  // smallest r of the tile's active cells -> acceptance band
-      unsigned long long rb = active ? bits_of(rv) : kInfBits;
+    {  // smallest c of the tile's active cells -> acceptance band
+      unsigned long long cb = active ? cv : kInfBits;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) rb = umin64(rb, __shfl_xor_sync(kFull, rb, o));
-      if (lane == 0 && rb < kInfBits) atomicMin(&s_rmin, rb);
+      for (int o = 16; o > 0; o >>= 1) cb = umin64(cb, __shfl_xor_sync(kFull, cb, o));
+      if (lane == 0 && cb < kInfBits) atomicMin(&s_cmin, cb);
     }
     // halo faces: -x, +x, -y, +y (, -z, +z)
     {
@@ -635,11 +517,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       }
     }
     if (tid < 6) s_facemin[tid] = kInfBits;
-    if (tid == 0) { s_min[0] = kInfBits; s_min[1] = kInfBits; s_cnt[0] = 0; s_cnt[1] = 0; }
+    if (tid == 0) { s_min[0] = s_min[1] = s_min[2] = kInfBits; s_cnt[0] = 0; s_cnt[1] = 0; }
     __syncthreads();
-    if (tid == 0) {
-      s_band = from_bits(s_rmin) * band_scale;
-      s_rmin = kInfBits;
+    if (timing) { const long long c1 = clock64(); cyc[0] += c1 - c0; c0 = c1; }
+    if (tid == 0) {   // band = k * sqrt(c_min) / sqrt(D): one cell's travel time
+      const float cm = s_cmin < kInfBits ? __double2float_rn(from_bits(s_cmin)) : 0.0f;
+      s_band = bits_of(static_cast<double>(sqrtf(cm) * band_scale));
+      s_cmin = kInfBits;
     }
     const unsigned long long vlim = s_vlim;
 
@@ -651,9 +535,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
              (D == 3 && (((faces & 16) && lz == 0) || ((faces & 32) && lz == TZ - 1))) ||
              ((pword >> lane) & 1u);
     }
-    unsigned long long pv = kInfBits;   // pending candidate (bit pattern)
+    // Pending candidates live in s_pv (owner-indexed).  The minimum over all
+    // pending candidates of round R accumulates in s_min[R % 3]: the accept
+    // phase of round R-1 adds what stayed pending, the evaluation phase of
+    // round R adds the new candidates.  Three barriers per round.
     unsigned long long m = kInfBits;
     unsigned rounds = 0;
+    unsigned ri = R % 3u;
 #pragma unroll 1
     for (;;) {
       // (A) neighbour minima (x by shuffles) and the exact integer filters; the
@@ -664,14 +552,15 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       if (lx == TX - 1) xr = s_t[zc][yc][TX + 1];
       bool go = false;
       if (need) {
-        double a[D];
-        a[0] = min_time(xl, xr);
-        a[1] = min_time(s_t[zc][yc - 1][xc], s_t[zc][yc + 1][xc]);
-        if constexpr (D == 3) a[D - 1] = min_time(s_t[zc - 1][yc][xc], s_t[zc + 1][yc][xc]);
-        unsigned long long amin = bits_of(a[0]);
+        unsigned long long a[D];
+        a[0] = umin64(bits_of(xl), bits_of(xr));
+        a[1] = umin64(bits_of(s_t[zc][yc - 1][xc]), bits_of(s_t[zc][yc + 1][xc]));
+        if constexpr (D == 3)
+          a[D - 1] = umin64(bits_of(s_t[zc - 1][yc][xc]), bits_of(s_t[zc + 1][yc][xc]));
+        unsigned long long amin = a[0];
 #pragma unroll
-        for (int k = 1; k < D; ++k) amin = umin64(amin, bits_of(a[k]));
-        const unsigned long long best = umin64(bits_of(tv), pv);
+        for (int k = 1; k < D; ++k) amin = umin64(amin, a[k]);
+        const unsigned long long best = umin64(bits_of(tv), s_pv[tid]);
         go = amin < kInfBits && best > amin;
         if (go) {
 #pragma unroll
@@ -687,54 +576,67 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
         base = __shfl_sync(kFull, base, 0);
         if (go) s_list[base + __popc(bal & ((1u << lane) - 1u))] = static_cast<unsigned short>(tid);
       }
-      __syncthreads();
-      // (B) dense FP64 phase: the first ceil(cnt/32) warps evaluate d-bar
+      __syncthreads();                                              // barrier 1
+      if (timing) { const long long c1 = clock64(); cyc[1] += c1 - c0; c0 = c1; }
+      // (B) dense arithmetic phase: the first ceil(cnt/32) warps evaluate d-bar
       {
         const int cnt = s_cnt[R & 1u];
+        unsigned long long nv = kInfBits;
         if (tid < cnt) {
           const int c = s_list[tid];
-          double a[D];
+          unsigned long long a[D];
 #pragma unroll
           for (int k = 0; k < D; ++k) a[k] = s_a[k][c];
-          double nv;
-          if (relax_cell<D>(from_bits(s_best[c]), a, s_r[c], nv)) s_cand[c] = bits_of(nv);
+          const bool dec = ARITH == kArithInt
+                               ? xf::relax<D>(s_best[c], a, s_c[c], nv)
+                               : hw::relax<D>(s_best[c], a, s_c[c], nv,
+                                              p.counters >= 2 ? path : nullptr);
+          if (dec) s_pv[c] = nv; else nv = kInfBits;
+        }
+        if (tid < ((cnt + 31) & ~31)) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) nv = umin64(nv, __shfl_xor_sync(kFull, nv, o));
+          if (lane == 0 && nv < kInfBits) atomicMin(&s_min[ri], nv);
         }
       }
-      __syncthreads();
-      if (tid == 0) s_cnt[(R + 1u) & 1u] = 0;
-      if (go) {
-        const unsigned long long cv = s_cand[tid];
-        if (cv < pv) pv = cv;
-        s_cand[tid] = kInfBits;
+      __syncthreads();                                              // barrier 2
+      if (timing) { const long long c1 = clock64(); cyc[2] += c1 - c0; c0 = c1; }
+      // (C) accept the pending candidates within the band above the minimum
+      m = s_min[ri];
+      const unsigned rn = ri == 2u ? 0u : ri + 1u;
+      if (tid == 0) {
+        s_cnt[(R + 1u) & 1u] = 0;
+        s_min[rn == 2u ? 0u : rn + 1u] = kInfBits;   // the buffer of round R+2
       }
-      {  // CTA-wide minimum of the pending candidates
-        unsigned long long w = pv;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w = umin64(w, __shfl_xor_sync(kFull, w, o));
-        if (lane == 0 && w < kInfBits) atomicMin(&s_min[R & 1u], w);
-      }
-      __syncthreads();
-      m = s_min[R & 1u];
-      if (tid == 0) s_min[(R + 1u) & 1u] = kInfBits;
       ++rounds;
       if (m >= vlim) break;   // nothing pending below the visit limit (uniform)
-      double lim_d = 0.0;
-      if (lane == 0) lim_d = __dadd_rn(from_bits(m), s_band);
-      const unsigned long long lim = umin64(bits_of(__shfl_sync(kFull, lim_d, 0)), vlim - 1);
-      const bool acc = pv <= lim;
-      if (acc) {
-        tv = from_bits(pv);
-        pv = kInfBits;
-        s_t[zc][yc][xc] = tv;
-        s_stamp[zc][yc][xc] = R;
-        ++n_dec;
+      unsigned long long lim = 0;
+      if (lane == 0) lim = xf::add_pos(m, s_band);
+      lim = umin64(__shfl_sync(kFull, lim, 0), vlim - 1);
+      {
+        const unsigned long long pv = s_pv[tid];
+        unsigned long long keep = kInfBits;
+        if (pv <= lim) {
+          tv = from_bits(pv);
+          s_pv[tid] = kInfBits;
+          s_t[zc][yc][xc] = tv;
+          s_stamp[zc][yc][xc] = R;
+          ++n_dec;
+        } else {
+          keep = pv;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) keep = umin64(keep, __shfl_xor_sync(kFull, keep, o));
+        if (lane == 0 && keep < kInfBits) atomicMin(&s_min[rn], keep);
       }
-      __syncthreads();
+      __syncthreads();                                              // barrier 3
+      if (timing) { const long long c1 = clock64(); cyc[3] += c1 - c0; c0 = c1; }
       bool nb = s_stamp[zc][yc][xc - 1] == R || s_stamp[zc][yc][xc + 1] == R ||
                 s_stamp[zc][yc - 1][xc] == R || s_stamp[zc][yc + 1][xc] == R;
       if constexpr (D == 3) nb = nb || s_stamp[zc - 1][yc][xc] == R || s_stamp[zc + 1][yc][xc] == R;
       need = active && nb;
       ++R;
+      ri = rn;
       if (rounds >= kMaxRounds) {   // uniform across the CTA
         if (tid == 0) raise_status(p.ctl, kEtimeout, 7);
         break;
@@ -744,7 +646,9 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
 
     // cells still pending are deferred to a later visit
     {
-      const unsigned pend_bits = __ballot_sync(kFull, pv < kInfBits);
+      const bool deferred = s_pv[tid] < kInfBits;
+      s_pv[tid] = kInfBits;
+      const unsigned pend_bits = __ballot_sync(kFull, deferred);
       if (lane == 0) {
         unsigned *pw = p.pend + static_cast<size_t>(tile) * kPendWords + warp;
         asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(pw), "r"(pend_bits) : "memory");
@@ -755,12 +659,16 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       const unsigned long long tb = bits_of(tv);
       atomicMin(reinterpret_cast<unsigned long long *>(T + gidx), tb);
       ++n_commits;
-      if (lx == 0) atomicMin(&s_facemin[0], tb);
-      if (lx == TX - 1) atomicMin(&s_facemin[1], tb);
-      if (ly == 0) atomicMin(&s_facemin[2], tb);
-      if (ly == TY - 1) atomicMin(&s_facemin[3], tb);
-      if (D == 3 && lz == 0) atomicMin(&s_facemin[4], tb);
-      if (D == 3 && lz == TZ - 1) atomicMin(&s_facemin[5], tb);
+      // a face value can change the cell across the face only if it is below
+      // that cell's value (causality; the loaded halo value is an upper bound)
+      if (lx == 0 && tb < bits_of(s_t[zc][yc][xc - 1])) atomicMin(&s_facemin[0], tb);
+      if (lx == TX - 1 && tb < bits_of(s_t[zc][yc][xc + 1])) atomicMin(&s_facemin[1], tb);
+      if (ly == 0 && tb < bits_of(s_t[zc][yc - 1][xc])) atomicMin(&s_facemin[2], tb);
+      if (ly == TY - 1 && tb < bits_of(s_t[zc][yc + 1][xc])) atomicMin(&s_facemin[3], tb);
+      if constexpr (D == 3) {
+        if (lz == 0 && tb < bits_of(s_t[zc - 1][yc][xc])) atomicMin(&s_facemin[4], tb);
+        if (lz == TZ - 1 && tb < bits_of(s_t[zc + 1][yc][xc])) atomicMin(&s_facemin[5], tb);
+      }
     }
     __threadfence();
     __syncthreads();
@@ -776,15 +684,16 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
         if (exists) {
           const unsigned long long nt =
               static_cast<unsigned long long>(P.tile_base + (ntz * P.nty + nty) * P.ntx + ntx);
-          activate(p, nt, 1u << (tid ^ 1), bucket_of_time(from_bits(fm), inv_delta));
+          activate(p, nt, 1u << (tid ^ 1), bucket_of_time(fm, inv_delta));
         }
       }
       __threadfence();
     }
     __syncthreads();
     if (tid == 0) {
+      if (timing) { const long long c1 = clock64(); cyc[4] += c1 - c0; c0 = c1; }
       if (m < kInfBits) {   // deferred cells: come back at their bucket, beyond this window
-        unsigned b = bucket_of_time(from_bits(m), inv_delta);
+        unsigned b = bucket_of_time(m, inv_delta);
         const unsigned bmin = s_lo + p.window + 1u;
         if (b < bmin) b = bmin;
         activate(p, static_cast<unsigned long long>(tile), 0u, b);
@@ -796,6 +705,19 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       ++n_visits;
       n_rounds += rounds;
       if (p.counters) visit_ns += static_cast<unsigned long long>(now_ns() - t_claim);
+      if (p.trace) {
+        const unsigned long long k = atomicAdd(&p.ctl->trace_n, 1ull);
+        if (k < p.trace_cap) {
+          TraceRec rec;
+          rec.t_claim = t_claim;
+          rec.t_end = now_ns();
+          rec.tile = static_cast<unsigned>(tile);
+          rec.lo = s_lo;
+          rec.rounds = rounds;
+          rec.flags = (m < kInfBits ? 1u : 0u) | (static_cast<unsigned>(blockIdx.x) << 8);
+          p.trace[k] = rec;
+        }
+      }
     }
   }
 
@@ -805,6 +727,19 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       n_evals += __shfl_xor_sync(kFull, n_evals, o);
       n_dec += __shfl_xor_sync(kFull, n_dec, o);
       n_commits += __shfl_xor_sync(kFull, n_commits, o);
+    }
+    if (p.counters >= 2) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        unsigned v = path[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0 && v) atomicAdd(&p.ctl->stats[kStatNewton + k], static_cast<unsigned long long>(v));
+      }
+      if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) atomicAdd(&p.ctl->stats[kStatCycLoad + k], cyc[k]);
+      }
     }
     if (lane == 0) {
       atomicAdd(&p.ctl->stats[kStatEvals], n_evals);
@@ -824,10 +759,10 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
 // Set-up kernels.
 // ---------------------------------------------------------------------------
 
-// r = fl(h / v) per cell (the constant c = fl(r * r) is formed where used);
-// checks v > 0 finite and r, c finite and positive; sums r for the auto
-// bucket width.
-__global__ void init_r_kernel(const double *__restrict__ speed, double h, double *__restrict__ r,
+// Per-cell constant of the update, c = fl(fl(h / v)^2) (the right-hand side
+// (h/v)^2 of Eq. difference_as_root); checks v > 0 finite and r, c finite and
+// positive; sums r = fl(h / v) for the auto bucket width.
+__global__ void init_c_kernel(const double *__restrict__ speed, double h, double *__restrict__ c_out,
                               int64_t n, Ctl *ctl) {
   double sum = 0.0;
   unsigned long long cnt = 0;
@@ -839,7 +774,7 @@ __global__ void init_r_kernel(const double *__restrict__ speed, double h, double
     const bool ok = v > 0.0 && bits_of(v) < kInfBits && ri > 0.0 && bits_of(ri) < kInfBits &&
                     c > 0.0 && bits_of(c) < kInfBits;
     if (!ok) raise_status(ctl, kEinval, static_cast<unsigned long long>(i));
-    r[i] = ri;
+    c_out[i] = c;
     sum += ri;
     ++cnt;
   }
@@ -889,7 +824,7 @@ __global__ void seed_kernel(SolveParams p, const SeedItem *__restrict__ items, i
     const int64_t y = yz % P.ny, z = yz / P.ny;
     const unsigned long long own = tile_of(P, x, y, z, tx_, ty_, tz_);
     p.tile_src[own] = 1;
-    const unsigned b = bucket_of_time(it.t0, inv);
+    const unsigned b = bucket_of_time(bits_of(it.t0), static_cast<float>(inv));
     activate(p, own, 1u << kFaceFull, b);
     const int64_t c3[3] = {x, y, z};
     const int64_t n3[3] = {P.nx, P.ny, P.nz};
@@ -908,7 +843,7 @@ __global__ void seed_kernel(SolveParams p, const SeedItem *__restrict__ items, i
 // Capacity retry: every tile holding a finite value is re-queued with a full
 // evaluation (Theorem 1: any state reached by valid updates is a valid start).
 __global__ void reseed_kernel(SolveParams p, int tx_, int ty_, int tz_, int64_t total_tiles) {
-  const double inv = p.ctl->inv_delta;
+  const float inv = static_cast<float>(p.ctl->inv_delta);
   for (int64_t g = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; g < total_tiles;
        g += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int pi = find_prob(p, static_cast<unsigned long long>(g));
@@ -922,7 +857,7 @@ __global__ void reseed_kernel(SolveParams p, int tx_, int ty_, int tz_, int64_t 
         for (int64_t x = tx * tx_; x < (tx + 1) * tx_ && x < P.nx; ++x)
           best = umin64(best, bits_of(ld_time(P.t + (z * P.ny + y) * P.nx + x)));
     if (best < kInfBits) activate(p, static_cast<unsigned long long>(g), 1u << kFaceFull,
-                                  bucket_of_time(from_bits(best), inv));
+                                  bucket_of_time(best, inv));
   }
 }
 
@@ -960,10 +895,10 @@ int grid_for(int64_t n, int per_sm) {
 
 }  // namespace
 
-cudaError_t launch_init_r(const double *speed, double h, double *r, int64_t n, Ctl *ctl,
+cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
                           cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
-  init_r_kernel<<<grid_for(n, 8), 256, 0, stream>>>(speed, h, r, n, ctl);
+  init_c_kernel<<<grid_for(n, 8), 256, 0, stream>>>(speed, h, c, n, ctl);
   return cudaGetLastError();
 }
 
@@ -997,23 +932,37 @@ cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int npro
   return cudaGetLastError();
 }
 
-int persistent_blocks_per_sm(int ndim) {
+int persistent_blocks_per_sm(int ndim, int arith) {
   int nb = 0;
   if (ndim == 3) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<3, kTX3, kTY3, kTZ3>,
-                                                  kTX3 * kTY3 * kTZ3, 0);
+    if (arith == kArithInt)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, persistent_kernel<3, kTX3, kTY3, kTZ3, kArithInt>, kTX3 * kTY3 * kTZ3, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, persistent_kernel<3, kTX3, kTY3, kTZ3, kArithFp64>, kTX3 * kTY3 * kTZ3, 0);
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<2, kTX2, kTY2, 1>,
-                                                  kTX2 * kTY2, 0);
+    if (arith == kArithInt)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, persistent_kernel<2, kTX2, kTY2, 1, kArithInt>, kTX2 * kTY2, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &nb, persistent_kernel<2, kTX2, kTY2, 1, kArithFp64>, kTX2 * kTY2, 0);
   }
   return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_persistent(const SolveParams &p, int grid, cudaStream_t stream) {
   if (p.ndim == 3) {
-    persistent_kernel<3, kTX3, kTY3, kTZ3><<<grid, kTX3 * kTY3 * kTZ3, 0, stream>>>(p);
+    if (p.arith == kArithInt)
+      persistent_kernel<3, kTX3, kTY3, kTZ3, kArithInt><<<grid, kTX3 * kTY3 * kTZ3, 0, stream>>>(p);
+    else
+      persistent_kernel<3, kTX3, kTY3, kTZ3, kArithFp64><<<grid, kTX3 * kTY3 * kTZ3, 0, stream>>>(p);
   } else {
-    persistent_kernel<2, kTX2, kTY2, 1><<<grid, kTX2 * kTY2, 0, stream>>>(p);
+    if (p.arith == kArithInt)
+      persistent_kernel<2, kTX2, kTY2, 1, kArithInt><<<grid, kTX2 * kTY2, 0, stream>>>(p);
+    else
+      persistent_kernel<2, kTX2, kTY2, 1, kArithFp64><<<grid, kTX2 * kTY2, 0, stream>>>(p);
   }
   return cudaGetLastError();
 }

@@ -51,9 +51,9 @@ def test_status_strings_without_gpu(lib):
 
 
 def test_struct_layouts_match_header():
-    # eik_opts: double, double, int64, int64, int, int, int, int, double -> 56 bytes
-    assert ctypes.sizeof(eik.EikOpts) == 56
-    assert ctypes.sizeof(eik.EikStats) == 13 * 8
+    # eik_opts: double, double, int64, int64, 4 x int, double, 2 x int, ptr, int64 -> 80 bytes
+    assert ctypes.sizeof(eik.EikOpts) == 80
+    assert ctypes.sizeof(eik.EikStats) == 23 * 8
     # eik_problem: ptr, double, int(+pad), int64[3], ptr, ptr, int64, ptr
     assert ctypes.sizeof(eik.EikProblem) == 8 + 8 + 8 + 24 + 8 + 8 + 8 + 8
 

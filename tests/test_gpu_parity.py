@@ -59,14 +59,18 @@ SHAPES = [(1, 1), (1, 40), (40, 1), (8, 32), (9, 33), (17, 65), (100, 37), (64, 
           (1, 1, 1), (4, 4, 16), (5, 5, 5), (17, 5, 9), (9, 33, 5), (20, 21, 22), (2, 40, 3)]
 
 
+ARITHS = [1, 2]    # d-bar on the FP64 unit / exact emulation on the integer pipes
+
+
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("seed", [0, 1])
-def test_random_grids_bit_exact(shape, seed):
+def test_random_grids_bit_exact(shape, seed, arith):
     p = synth.random_problem(1000 + seed, shape, n_src=1 + 2 * seed, contrast=10.0,
                              src_t_max=0.3 * seed, h=0.5)
     ref = oracle.fmm(p.speed, p.h, p.sources, p.src_t).t
-    got, _ = gpu_solve(p)
-    assert_bits_equal(got, ref, f"{shape} seed {seed}")
+    got, _ = gpu_solve(p, opts={"arith": arith})
+    assert_bits_equal(got, ref, f"{shape} seed {seed} arith {arith}")
 
 
 @pytest.mark.parametrize("shape", [(200, 300), (40, 50, 60)])
@@ -89,19 +93,31 @@ def test_config1_bit_exact_and_closed_form():
         assert got[m, m + k] == abs(k) * p.h and got[m + k, m] == abs(k) * p.h
 
 
-def test_config2_bit_exact():
+@pytest.mark.parametrize("arith", ARITHS)
+def test_config2_bit_exact(arith):
     p = synth.config2()
     ref = oracle.fmm(p.speed, p.h, p.sources).t
-    got, st = gpu_solve(p, opts={"counters": 1})
+    got, st = gpu_solve(p, opts={"counters": 1, "arith": arith})
     assert_bits_equal(got, ref, "config2")
     assert st["good"] == p.ncells - 1
 
 
+_C3 = {}
+
+
+def _config3_ref():
+    if not _C3:
+        p = synth.config3()
+        _C3["p"] = p
+        _C3["ref"] = oracle.fmm(p.speed, p.h, p.sources).t
+    return _C3["p"], _C3["ref"]
+
+
 @pytest.mark.slow
-def test_config3_bit_exact():
-    p = synth.config3()
-    ref = oracle.fmm(p.speed, p.h, p.sources).t
-    got, st = gpu_solve(p, opts={"counters": 1})
+@pytest.mark.parametrize("arith", ARITHS)
+def test_config3_bit_exact(arith):
+    p, ref = _config3_ref()
+    got, st = gpu_solve(p, opts={"counters": 1, "arith": arith})
     assert_bits_equal(got, ref, "config3")
     assert st["good"] == p.ncells - 1
 
