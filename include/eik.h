@@ -157,6 +157,30 @@ eik_status eik_solve_batched(const eik_problem *probs, int nprob, const eik_opts
  * and frees a small device buffer; synchronises `stream`. */
 eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches, void *stream);
 
+/* The single-grid solve of eik_solve without allocating any memory.  (The
+ * paper has no counterpart: this serves callers that cannot allocate device
+ * memory, e.g. code whose device memory belongs to an arena allocator that
+ * forbids outside cudaMalloc calls, or latency-sensitive loops where
+ * cudaMalloc / cudaFree would synchronise the device.)
+ *   Arguments and results as eik_solve, with these limits:
+ *   - speed, src_idx, src_t (if not NULL) and out_t must be device pointers;
+ *   - at most 2^20 cells, 2^15 tiles (2D tiles 32x8, 3D tiles 16x4x4) and
+ *     2048 sources; larger inputs return EIK_EINVAL before anything runs;
+ *   - no capacity retry: a frontier overflow returns EIK_ECAPACITY;
+ *   - stats->solve_ms, max_queue and the timing details stay 0;
+ *     opts->trace and opts->test_stall are ignored.
+ * Scratch memory is one fixed file-scope device array of about 17 MB, present
+ * on every GPU that loads the library until the process exits.  The first
+ * call on a device looks up that array's device address (once per device);
+ * make that first call before any stream capture.  Every call shares the
+ * array and clears what must start at zero; calls whose GPU work overlaps
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller.  Synchronises `stream` to read the status. */
+eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int64_t *dims,
+                             const int64_t *src_idx, const double *src_t, int64_t nsrc,
+                             double *out_t, const eik_opts *opts, eik_stats *stats,
+                             void *stream);
+
 /* Release the library's device workspace on the current device. */
 void eik_release(void);
 

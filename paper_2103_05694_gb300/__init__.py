@@ -97,12 +97,14 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     L.eik_abi_version.restype = ctypes.c_int
     L.eik_selftest.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int64), vp]
     L.eik_selftest.restype = ctypes.c_int
+    L.eik_solve_noalloc.argtypes = L.eik_solve.argtypes
+    L.eik_solve_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
 
 EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
-            "eik_abi_version", "eik_selftest"]
+            "eik_abi_version", "eik_selftest", "eik_solve_noalloc"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3"]
 
@@ -171,6 +173,24 @@ def eik_solve(speed_ptr: int, h: float, ndim: int, dims, src_ptr: int | None,
                      ctypes.byref(o) if o is not None else None, ctypes.byref(st), stream)
     if rc != EIK_OK:
         raise EikError(rc, eik_last_error())
+    return st.as_dict()
+
+
+def eik_solve_noalloc(speed_ptr: int, h: float, ndim: int, dims, src_ptr: int | None,
+                      src_t_ptr: int | None, nsrc: int, out_ptr: int, opts: dict | None = None,
+                      stream: int | None = None) -> dict:
+    """Raw call of the allocation-free solve (device pointers only; at most
+    2^20 cells, 2^15 tiles, 2048 sources).  For callers that may not allocate
+    device memory."""
+    L = load_library()
+    d = (ctypes.c_int64 * ndim)(*[int(x) for x in dims])
+    st = EikStats()
+    o = _make_opts(opts)
+    rc = L.eik_solve_noalloc(speed_ptr, float(h), int(ndim), d, src_ptr, src_t_ptr, int(nsrc),
+                             out_ptr, ctypes.byref(o) if o is not None else None, ctypes.byref(st),
+                             stream)
+    if rc != EIK_OK:
+        raise EikError(rc, "eik_solve_noalloc")
     return st.as_dict()
 
 
