@@ -33,9 +33,13 @@ void set_err(const char *fmt, ...) {
 
 constexpr int64_t kMaxCells = int64_t(1) << 40;
 constexpr uint64_t kMaxCapEntries = uint64_t(1) << 30;   // whole ring storage limit
-constexpr double kDefaultKDelta = 8.0;
+// Defaults per dimension (from parameter sweeps on the 2D layered and 3D
+// checkerboard workloads): bucket width in cell travel times, look-ahead
+// window in buckets, in-tile acceptance band, persistent CTAs per SM.
+constexpr double kDefaultKDelta[2] = {8.0, 4.0};
 constexpr int kDefaultWindow = 4;
-constexpr double kDefaultBand = 4.0;
+constexpr double kDefaultBand[2] = {8.0, 4.0};
+constexpr int kDefaultCtasPerSm[2] = {1, 2};
 constexpr int kMaxRetries = 4;
 
 // Grow-only device buffer.
@@ -380,7 +384,8 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.tile_src = g_ws.tile_src.p;
   sp.pend = g_ws.pend.p;
   sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow);
-  sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand;
+  const int di = ndim == 3 ? 1 : 0;
+  sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand[di];
   sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
   sp.trace = opts && opts->trace && opts->trace_cap > 0 ? static_cast<eik::TraceRec *>(opts->trace)
@@ -393,14 +398,14 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.timeout_ns = tmo_ms * 1000000ll;
   sp.counters = opts ? opts->counters : 0;
   sp.test_stall = opts ? opts->test_stall : 0;
-  const double k_delta = opts && opts->k_delta > 0 ? opts->k_delta : kDefaultKDelta;
+  const double k_delta = opts && opts->k_delta > 0 ? opts->k_delta : kDefaultKDelta[di];
   const double delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
 
   CK(eik::launch_seed(sp, g_ws.seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
      "seed launch");
-  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : 0;
+  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : kDefaultCtasPerSm[di];
   const int occ = eik::persistent_blocks_per_sm(ndim, sp.arith);
-  if (per_sm <= 0 || per_sm > occ) per_sm = occ;
+  if (per_sm > occ) per_sm = occ;
   int dev_sms = 0;
   CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g_ws.device), "SM count");
   int64_t grid = (int64_t)dev_sms * per_sm;

@@ -459,3 +459,131 @@ __device__ __forceinline__ bool relax(unsigned long long best, const unsigned lo
 
 }  // namespace hw
 }  // namespace eik
+
+namespace eik {
+namespace hw {
+
+// Starting point for d-bar in about 9 (2D) / 15 (3D) FP64 instructions and
+// no branches on the data: the root of the active-set quadratic
+//   A w^2 - 2 B w + C = 0,  A = |S|,  B = sum_S u_k,  C = sum_S u_k^2 - c,
+// with u_k = a_k - a_0 over the sorted minima; the active set S is picked
+// in fp32 (one-sided, two axes, three axes: Algorithm 1's case split and the
+// rearranged root d-hat of the Mitigation Strategies section).  The square
+// root is an fp32 reciprocal-square-root seed refined by two DFMA Newton
+// steps.  tau = a_0 + w lands within about an ulp of d-bar; only speed
+// depends on this.  a are the minima in axis order, s0 their minimum.
+template <int D>
+__device__ __forceinline__ unsigned long long guess(const unsigned long long (&a)[D],
+                                                    unsigned long long cb) {
+  unsigned long long s0 = a[0], s1 = D > 1 ? a[1] : kInf, s2 = D > 2 ? a[2] : kInf;
+  {
+    const unsigned long long lo = xf::umin(s0, s1), hi = xf::umax(s0, s1);
+    s0 = lo;
+    s1 = hi;
+    if (D > 2) {
+      const unsigned long long l2 = xf::umin(s1, s2), h2 = xf::umax(s1, s2);
+      s2 = h2;
+      s1 = xf::umax(s0, l2);
+      s0 = xf::umin(s0, l2);
+    }
+  }
+  const double c = as_d(cb);
+  const double a0 = as_d(s0);
+  double u1 = s1 < kInf ? __dsub_rn(as_d(s1), a0) : 0.0;
+  double u2 = 0.0;
+  if (D > 2) u2 = s2 < kInf ? __dsub_rn(as_d(s2), a0) : 0.0;
+  // active set in fp32
+  const float cf = xf::to_f(cb);
+  const float rf = sqrtf(cf);
+  const float u1f = xf::to_f(as_u(u1)), u2f = xf::to_f(as_u(u2));
+  int A = 1;
+  float wf = rf;
+  if (s1 < kInf && u1f < rf) {
+    A = 2;
+    wf = 0.5f * (u1f + sqrtf(fmaxf(2.0f * cf - u1f * u1f, 0.0f)));
+    if (D > 2 && s2 < kInf && u2f < wf) A = 3;
+  }
+  if (A < 2) u1 = 0.0;
+  if (A < 3) u2 = 0.0;
+  double w;
+  if (D == 2) {
+    // 2D: w = (u1 + sqrt(X - u1^2)) / 2 with X = 2c (two axes) or X = 4c, u1 = 0 (one axis)
+    const double X = as_d(cb + (static_cast<unsigned long long>(A == 2 ? 1 : 2) << 52));  // exact 2c / 4c
+    const double x = fma(-u1, u1, X);
+    const float xf32 = fmaxf(xf::to_f(as_u(x)), 1e-30f);
+    const float y0 = rsqrtf(xf32);
+    const double hy = as_d(xf::from_f(0.5f * y0));
+    double sq = x * as_d(xf::from_f(y0));
+    sq = fma(fma(-sq, sq, x), hy, sq);
+    sq = fma(fma(-sq, sq, x), hy, sq);
+    w = as_d(as_u(u1 + sq) - (1ull << 52));                                  // halve exactly
+  } else {
+    const double B = u1 + u2;
+    const double C = fma(u1, u1, fma(u2, u2, -c));
+    const double x = fma(B, B, -static_cast<double>(A) * C);
+    const float xf32 = fmaxf(xf::to_f(as_u(x)), 1e-30f);
+    const float y0 = rsqrtf(xf32);
+    const double hy = as_d(xf::from_f(0.5f * y0));
+    double sq = x * as_d(xf::from_f(y0));
+    sq = fma(fma(-sq, sq, x), hy, sq);
+    sq = fma(fma(-sq, sq, x), hy, sq);
+    w = (B + sq) * (A == 1 ? 1.0 : (A == 2 ? 0.5 : (1.0 / 3.0)));
+  }
+  unsigned long long t = as_u(a0 + w);
+  if (!(t > s0) || t >= kInf) t = s0 + 1ull;
+  return t;
+}
+
+// The update for one cell, evaluated by a group of L lanes (L = 4 or 8,
+// aligned within the warp).  Every lane computes the same starting point;
+// lane 0 of the group evaluates G(prev(best)) (is a decrease possible?), the
+// other lanes G at the L-1 consecutive doubles centred on the guess, in one
+// G pass.  d-bar is the first of those points with G >= c whose predecessor
+// fails; if the window does not contain it, lane 0 runs the full search.
+// Returns (in every lane of the group) true and the new value if the cell
+// decreases.  All lanes of the warp must call this together.
+template <int D, int L>
+__device__ __forceinline__ bool relax_group(unsigned long long best, const unsigned long long (&a)[D],
+                                            unsigned long long cb, bool valid,
+                                            unsigned long long &out) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned j = lane & (L - 1u);
+  const unsigned long long tg = valid ? guess<D>(a, cb) : 1ull;
+  unsigned long long amin = a[0];
+#pragma unroll
+  for (int k = 1; k < D; ++k) amin = xf::umin(amin, a[k]);
+  unsigned long long pt;
+  if (j == 0) {
+    pt = best < kInf ? best - 1ull : tg;
+  } else {
+    const long long off = static_cast<long long>(j) - static_cast<long long>(L / 2);
+    pt = static_cast<unsigned long long>(static_cast<long long>(tg) + off);
+    if (pt < amin) pt = amin;                          // G(a_min) = 0 < c
+  }
+  const bool ge = valid && G<D>(pt, a) >= cb;
+  const unsigned bal = __ballot_sync(0xffffffffu, ge);
+  const unsigned bits = (bal >> (lane & ~(L - 1u))) & ((1u << L) - 1u);
+  bool dec = false;
+  unsigned long long res = kInf;
+  if (valid) {
+    const bool possible = best >= kInf || (bits & 1u);
+    if (possible) {
+      const unsigned w = bits >> 1;                    // points 1..L-1
+      const int first = w ? __ffs(static_cast<int>(w)) : 0;   // 1-based index within the window
+      if (first >= 2) {
+        res = static_cast<unsigned long long>(static_cast<long long>(tg) + (first - static_cast<int>(L / 2)));
+      } else if (j == 0) {
+        res = dbar<D>(a, cb);                          // window missed: full exact search
+      }
+      dec = true;
+    }
+  }
+  // lane 0 of the group may have run the fallback: share its result
+  const unsigned long long r0 = __shfl_sync(0xffffffffu, res, lane & ~(L - 1u));
+  if (dec && res >= kInf) res = r0;
+  out = res;
+  return dec && res < best;
+}
+
+}  // namespace hw
+}  // namespace eik

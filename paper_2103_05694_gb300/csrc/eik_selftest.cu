@@ -68,14 +68,44 @@ __device__ unsigned long long rand_double(unsigned long long h, int emin, int er
   return (e << 52) | m;
 }
 
-// counters: 0 sub, 1 sq, 2 add, 3 G2, 4 G3, 5 dbar2, 6 dbar3, 7 trials
+// The lane-group update of one cell (all L lanes take the cell of the group's
+// first lane) against the reference: decrease iff d-bar < best, value d-bar.
+template <int D, int L>
+__device__ bool group_ok(const unsigned long long (&a_in)[D], unsigned long long cb_in,
+                         unsigned long long h) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned lead = lane & ~(L - 1u);
+  unsigned long long a[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) a[k] = __shfl_sync(0xffffffffu, a_in[k], lead);
+  const unsigned long long cb = __shfl_sync(0xffffffffu, cb_in, lead);
+  const unsigned long long ref = dbar_ref<D>(a, cb);
+  const unsigned long long hh = __shfl_sync(0xffffffffu, h, lead);
+  unsigned long long best;
+  switch (hh & 3u) {
+    case 0: best = kInf; break;
+    case 1: best = ref; break;
+    case 2: best = ref + 1ull + ((hh >> 8) % 100u); break;
+    default: best = ref > 2ull ? ref - 1ull - ((hh >> 8) % 2u) : ref; break;
+  }
+  unsigned long long out = 0;
+  const bool dec = hw::relax_group<D, L>(best, a, cb, true, out);
+  const bool want = ref < best;
+  return dec == want && (!dec || out == ref);
+}
+
+// counters: 0 sub, 1 sq, 2 add, 3 G2, 4 G3, 5 dbar2, 6 dbar3, 7 group 2D x8,
+// 8 group 3D x8, 9 group 2D x4; [10] trials; [16 + k] first failing trial of check k
 __global__ void selftest_kernel(int64_t n, unsigned long long seed, unsigned long long *bad,
                                 unsigned long long *first) {
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  // whole warps iterate together (the lane-group checks use warp collectives)
+  const int64_t span = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t base = blockIdx.x * static_cast<int64_t>(blockDim.x); base < n; base += span) {
+    const int64_t i = base + threadIdx.x;
+    const bool live = i < n;
     const unsigned long long h0 = mix(seed ^ mix(static_cast<unsigned long long>(i)));
     const unsigned long long h1 = mix(h0), h2 = mix(h1), h3 = mix(h2), h4 = mix(h3), h5 = mix(h4);
-    unsigned long long nb[7] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned long long nb[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // sub and add: x >= y > 0 with exponent gaps 0..70
     {
       unsigned long long x = rand_double(h1, 900, 250);
@@ -116,15 +146,19 @@ __global__ void selftest_kernel(int64_t n, unsigned long long seed, unsigned lon
       if (xf::G<3>(tau, a3) != G_hw<3>(tau, a3)) nb[4] = 1;
       if (xf::dbar<2>(a2, cb) != dbar_ref<2>(a2, cb)) nb[5] = 1;
       if (xf::dbar<3>(a3, cb) != dbar_ref<3>(a3, cb)) nb[6] = 1;
+      const unsigned long long hg = mix(h5 ^ 3);
+      if (!group_ok<2, 8>(a2, cb, hg)) nb[7] = 1;
+      if (!group_ok<3, 8>(a3, cb, hg)) nb[8] = 1;
+      if (!group_ok<2, 4>(a2, cb, hg ^ 1)) nb[9] = 1;
     }
-    for (int k = 0; k < 7; ++k) {
-      if (nb[k]) {
+    for (int k = 0; k < 10; ++k) {
+      if (live && nb[k]) {
         atomicAdd(&bad[k], 1ull);
         atomicCAS(&first[k], ~0ull, static_cast<unsigned long long>(i));
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&bad[7], static_cast<unsigned long long>(n));
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&bad[10], static_cast<unsigned long long>(n));
 }
 
 }  // namespace
@@ -134,24 +168,24 @@ extern "C" eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches
   if (n < 0 || !mismatches) return EIK_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   unsigned long long *d = nullptr;
-  if (cudaMalloc(&d, 16 * sizeof(unsigned long long)) != cudaSuccess) {
+  if (cudaMalloc(&d, 32 * sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     return EIK_ENOMEM;
   }
-  cudaMemsetAsync(d, 0, 8 * sizeof(unsigned long long), s);
-  cudaMemsetAsync(d + 8, 0xff, 8 * sizeof(unsigned long long), s);
+  cudaMemsetAsync(d, 0, 16 * sizeof(unsigned long long), s);
+  cudaMemsetAsync(d + 16, 0xff, 16 * sizeof(unsigned long long), s);
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   int64_t grid = (n + 255) / 256;
   if (grid > 8 * sms) grid = 8 * sms;
   if (grid < 1) grid = 1;
-  eik::selftest_kernel<<<static_cast<int>(grid), 256, 0, s>>>(n, seed, d, d + 8);
-  unsigned long long h[16];
+  eik::selftest_kernel<<<static_cast<int>(grid), 256, 0, s>>>(n, seed, d, d + 16);
+  unsigned long long h[32];
   cudaError_t e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(d);
   if (e != cudaSuccess) return EIK_ECUDA;
-  for (int k = 0; k < 16; ++k) mismatches[k] = static_cast<int64_t>(h[k]);
+  for (int k = 0; k < 32; ++k) mismatches[k] = static_cast<int64_t>(h[k]);
   return EIK_OK;
 }

@@ -51,6 +51,16 @@ __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsig
   return a < b ? a : b;
 }
 
+// Minimum of a 64-bit value over the full warp with two warp-reduce
+// instructions (high words first, then the low words of the lanes that hold
+// the smallest high word).
+__device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
+  const unsigned hi = __reduce_min_sync(0xffffffffu, static_cast<unsigned>(v >> 32));
+  const unsigned lo = __reduce_min_sync(
+      0xffffffffu, static_cast<unsigned>(v >> 32) == hi ? static_cast<unsigned>(v) : 0xffffffffu);
+  return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+
 // Relaxed, GPU-scope accesses (never served from a stale L1 line).
 __device__ __forceinline__ unsigned ld_rlx(const unsigned *p) {
   unsigned v;
@@ -381,6 +391,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
   __shared__ long long s_tile;
   __shared__ int s_prob, s_faces;
   __shared__ unsigned s_slot, s_lo;
+  __shared__ int s_cont;
 
   const int tid = threadIdx.x;
   const unsigned lane = tid & 31;
@@ -481,11 +492,20 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
     if (lane == 0) pword = ld_rlx(p.pend + static_cast<size_t>(tile) * kPendWords + warp);
     pword = __shfl_sync(kFull, pword, 0);
     {  // smallest c of the tile's active cells -> acceptance band
-      unsigned long long cb = active ? cv : kInfBits;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) cb = umin64(cb, __shfl_xor_sync(kFull, cb, o));
+      const unsigned long long cb = warp_min64(active ? cv : kInfBits);
       if (lane == 0 && cb < kInfBits) atomicMin(&s_cmin, cb);
     }
+    // A claimed tile is worked on until it has nothing left inside the window:
+    // after each commit, a tile that neighbours re-activated meanwhile (dirty)
+    // or whose deferred cells came inside the moved window continues here
+    // with a fresh halo instead of going back through the queue.
+    int faces_now = faces;
+    bool first = true;
+    unsigned long long m = kInfBits;
+    unsigned rounds = 0;
+    unsigned long long vlim = 0;
+#pragma unroll 1
+    for (;;) {
     // halo faces: -x, +x, -y, +y (, -z, +z)
     {
       constexpr int FX = TY * TZ, FY = TX * TZ, FZ = (D == 3) ? TX * TY : 0;
@@ -520,28 +540,29 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
     if (tid == 0) { s_min[0] = s_min[1] = s_min[2] = kInfBits; s_cnt[0] = 0; s_cnt[1] = 0; }
     __syncthreads();
     if (timing) { const long long c1 = clock64(); cyc[0] += c1 - c0; c0 = c1; }
-    if (tid == 0) {   // band = k * sqrt(c_min) / sqrt(D): one cell's travel time
+    if (first && tid == 0) {   // band = k * sqrt(c_min) / sqrt(D): one cell's travel time
       const float cm = s_cmin < kInfBits ? __double2float_rn(from_bits(s_cmin)) : 0.0f;
       s_band = bits_of(static_cast<double>(sqrtf(cm) * band_scale));
       s_cmin = kInfBits;
     }
-    const unsigned long long vlim = s_vlim;
+    vlim = s_vlim;
 
     const double tv0 = tv;
     bool need = active;
-    if (need && !(faces & (1 << kFaceFull))) {
-      need = ((faces & 1) && lx == 0) || ((faces & 2) && lx == TX - 1) ||
-             ((faces & 4) && ly == 0) || ((faces & 8) && ly == TY - 1) ||
-             (D == 3 && (((faces & 16) && lz == 0) || ((faces & 32) && lz == TZ - 1))) ||
-             ((pword >> lane) & 1u);
+    if (need && !(faces_now & (1 << kFaceFull))) {
+      const bool pend_cell = first ? ((pword >> lane) & 1u) != 0u : s_pv[tid] < kInfBits;
+      need = ((faces_now & 1) && lx == 0) || ((faces_now & 2) && lx == TX - 1) ||
+             ((faces_now & 4) && ly == 0) || ((faces_now & 8) && ly == TY - 1) ||
+             (D == 3 && (((faces_now & 16) && lz == 0) || ((faces_now & 32) && lz == TZ - 1))) ||
+             pend_cell;
     }
     // Pending candidates live in s_pv (owner-indexed).  The minimum over all
     // pending candidates of round R accumulates in s_min[R % 3]: the accept
     // phase of round R-1 adds what stayed pending, the evaluation phase of
     // round R adds the new candidates.  Three barriers per round.
-    unsigned long long m = kInfBits;
-    unsigned rounds = 0;
+    m = kInfBits;
     unsigned ri = R % 3u;
+    unsigned pass_round = 0;
 #pragma unroll 1
     for (;;) {
       // (A) neighbour minima (x by shuffles) and the exact integer filters; the
@@ -569,6 +590,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
         }
         ++n_evals;
       }
+      if (pass_round == 0 && !first) {
+        // candidates still pending from the previous pass of this visit take
+        // part in this round's minimum (the buffers were reset for the pass)
+        const unsigned long long keep = warp_min64(s_pv[tid]);
+        if (lane == 0 && keep < kInfBits) atomicMin(&s_min[ri], keep);
+      }
+      ++pass_round;
       {
         const unsigned bal = __ballot_sync(kFull, go);
         int base = 0;
@@ -578,24 +606,49 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       }
       __syncthreads();                                              // barrier 1
       if (timing) { const long long c1 = clock64(); cyc[1] += c1 - c0; c0 = c1; }
-      // (B) dense arithmetic phase: the first ceil(cnt/32) warps evaluate d-bar
+      // (B) dense arithmetic phase.  Few cells: a group of 8 (or 4) lanes per
+      //     cell evaluates d-bar (guess + one G pass over a window of points);
+      //     many cells: one lane per cell.  Only warps holding work take part.
       {
         const int cnt = s_cnt[R & 1u];
         unsigned long long nv = kInfBits;
-        if (tid < cnt) {
-          const int c = s_list[tid];
-          unsigned long long a[D];
+        bool part = false;
+        if (ARITH == kArithFp64 && cnt <= 64) {
+          const int L = cnt <= 32 ? 8 : 4;
+          if (warp < (cnt * L + 31) / 32) {
+            part = true;
+            const int g = tid / L;
+            const bool valid = g < cnt;
+            const int c = valid ? s_list[g] : 0;
+            unsigned long long a[D];
 #pragma unroll
-          for (int k = 0; k < D; ++k) a[k] = s_a[k][c];
-          const bool dec = ARITH == kArithInt
-                               ? xf::relax<D>(s_best[c], a, s_c[c], nv)
-                               : hw::relax<D>(s_best[c], a, s_c[c], nv,
-                                              p.counters >= 2 ? path : nullptr);
-          if (dec) s_pv[c] = nv; else nv = kInfBits;
+            for (int k = 0; k < D; ++k) a[k] = valid ? s_a[k][c] : kInfBits;
+            const unsigned long long best = valid ? s_best[c] : kInfBits;
+            const unsigned long long cb = valid ? s_c[c] : 0ull;
+            unsigned long long out;
+            const bool dec = L == 8 ? hw::relax_group<D, 8>(best, a, cb, valid, out)
+                                    : hw::relax_group<D, 4>(best, a, cb, valid, out);
+            if (dec) {
+              nv = out;
+              if ((tid & (L - 1)) == 0) s_pv[c] = out;
+            }
+          }
+        } else if (tid < ((cnt + 31) & ~31)) {
+          part = true;
+          if (tid < cnt) {
+            const int c = s_list[tid];
+            unsigned long long a[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) a[k] = s_a[k][c];
+            const bool dec = ARITH == kArithInt
+                                 ? xf::relax<D>(s_best[c], a, s_c[c], nv)
+                                 : hw::relax<D>(s_best[c], a, s_c[c], nv,
+                                                p.counters >= 2 ? path : nullptr);
+            if (dec) s_pv[c] = nv; else nv = kInfBits;
+          }
         }
-        if (tid < ((cnt + 31) & ~31)) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) nv = umin64(nv, __shfl_xor_sync(kFull, nv, o));
+        if (part) {   // warp-uniform
+          nv = warp_min64(nv);
           if (lane == 0 && nv < kInfBits) atomicMin(&s_min[ri], nv);
         }
       }
@@ -610,9 +663,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
       }
       ++rounds;
       if (m >= vlim) break;   // nothing pending below the visit limit (uniform)
-      unsigned long long lim = 0;
-      if (lane == 0) lim = xf::add_pos(m, s_band);
-      lim = umin64(__shfl_sync(kFull, lim, 0), vlim - 1);
+      const unsigned long long lim =
+          umin64(bits_of(__dadd_rn(from_bits(m), from_bits(s_band))), vlim - 1);
       {
         const unsigned long long pv = s_pv[tid];
         unsigned long long keep = kInfBits;
@@ -625,8 +677,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
         } else {
           keep = pv;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) keep = umin64(keep, __shfl_xor_sync(kFull, keep, o));
+        keep = warp_min64(keep);
         if (lane == 0 && keep < kInfBits) atomicMin(&s_min[rn], keep);
       }
       __syncthreads();                                              // barrier 3
@@ -644,16 +695,6 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
     }
     ++R;
 
-    // cells still pending are deferred to a later visit
-    {
-      const bool deferred = s_pv[tid] < kInfBits;
-      s_pv[tid] = kInfBits;
-      const unsigned pend_bits = __ballot_sync(kFull, deferred);
-      if (lane == 0) {
-        unsigned *pw = p.pend + static_cast<size_t>(tile) * kPendWords + warp;
-        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(pw), "r"(pend_bits) : "memory");
-      }
-    }
     // commit and collect the smallest committed time per tile face
     if (bits_of(tv) < bits_of(tv0)) {
       const unsigned long long tb = bits_of(tv);
@@ -686,6 +727,49 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
               static_cast<unsigned long long>(P.tile_base + (ntz * P.nty + nty) * P.ntx + ntx);
           activate(p, nt, 1u << (tid ^ 1), bucket_of_time(fm, inv_delta));
         }
+      }
+      __threadfence();
+    }
+    // continue on this tile?  (dirty: take the new faces; deferred cells now
+    // inside the moved window: take no faces)
+    if (tid == 0) {
+      int cont = 0;
+      unsigned long long old = ld_rlx(&p.state[tile]);
+      if (state_of(old) == kStDirty) {
+        const unsigned long long prev = atomicCAS(&p.state[tile], old, make_state(kStRunning, 0, 0));
+        if (prev == old) {
+          cont = 1;
+          s_faces = static_cast<int>(faces_of(old));
+        }
+      }
+      if (!cont && m < kInfBits) {
+        const unsigned lo2 = ld_rlx(&p.ctl->cur);
+        const unsigned long long v2 = bits_of(static_cast<double>(lo2 + p.window + 1u) * delta);
+        if (m < v2) {
+          cont = 2;
+          s_faces = 0;
+          s_vlim = v2;
+          s_lo = lo2;
+        }
+      }
+      if (cont) __threadfence();   // the claim of the new work is ordered before the halo loads
+      s_cont = cont;
+    }
+    __syncthreads();
+    if (!s_cont) break;
+    faces_now = s_faces;
+    first = false;
+    if (tid < 6) s_facemin[tid] = kInfBits;
+    }   // continuation loop
+
+    // cells still pending are deferred to a later visit
+    {
+      const bool deferred = s_pv[tid] < kInfBits;
+      s_pv[tid] = kInfBits;
+      const unsigned pend_bits = __ballot_sync(kFull, deferred);
+      if (lane == 0) {
+        unsigned *pw = p.pend + static_cast<size_t>(tile) * kPendWords + warp;
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(pw), "r"(pend_bits) : "memory");
       }
       __threadfence();
     }
