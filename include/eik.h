@@ -183,6 +183,26 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
                              double *out_t, const eik_opts *opts, eik_stats *stats,
                              void *stream);
 
+/* Plans: a batch prepared once and solved many times.
+ * eik_plan_create checks the problems (device pointers only; all of one ndim),
+ * copies and de-duplicates their sources, and allocates the plan's own device
+ * workspace (synchronous).  eik_plan_enqueue enqueues one complete solve of
+ * every problem on `stream` -- constants, initial field, seeds and ONE
+ * persistent launch over the tiles of all problems -- without allocating and
+ * without waiting for the device, so a CUDA graph can capture it and replay it.
+ * The speed arrays are read and out_t written by each solve; keep them alive
+ * while the plan is used.  eik_plan_status synchronises `stream` and returns
+ * the status of the last completed solve (and its counters when the plan was
+ * created with opts->counters); a frontier overflow is reported as
+ * EIK_ECAPACITY (no retry inside a plan: create it with a larger capacity).
+ * eik_plan_destroy frees the plan (after its work has completed). */
+typedef struct eik_plan eik_plan;
+eik_status eik_plan_create(const eik_problem *probs, int nprob, const eik_opts *opts,
+                           eik_plan **plan);
+eik_status eik_plan_enqueue(eik_plan *plan, void *stream);
+eik_status eik_plan_status(eik_plan *plan, eik_stats *stats, void *stream);
+void eik_plan_destroy(eik_plan *plan);
+
 /* Release the library's device workspace on the current device. */
 void eik_release(void);
 

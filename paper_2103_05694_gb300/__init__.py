@@ -99,12 +99,22 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     L.eik_selftest.restype = ctypes.c_int
     L.eik_solve_noalloc.argtypes = L.eik_solve.argtypes
     L.eik_solve_noalloc.restype = ctypes.c_int
+    L.eik_plan_create.argtypes = [ctypes.POINTER(EikProblem), ctypes.c_int,
+                                  ctypes.POINTER(EikOpts), ctypes.POINTER(vp)]
+    L.eik_plan_create.restype = ctypes.c_int
+    L.eik_plan_enqueue.argtypes = [vp, vp]
+    L.eik_plan_enqueue.restype = ctypes.c_int
+    L.eik_plan_status.argtypes = [vp, ctypes.POINTER(EikStats), vp]
+    L.eik_plan_status.restype = ctypes.c_int
+    L.eik_plan_destroy.argtypes = [vp]
+    L.eik_plan_destroy.restype = None
     _lib = L
     return L
 
 
 EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
-            "eik_abi_version", "eik_selftest", "eik_solve_noalloc"]
+            "eik_abi_version", "eik_selftest", "eik_solve_noalloc", "eik_plan_create",
+            "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3", "group2x8", "group3x8",
                    "group2x4"]
@@ -282,3 +292,86 @@ def solve_batched(problems: list[dict], opts: dict | None = None, stream=None) -
         if p.get("src_t") is not None and not isinstance(p["src_t"], torch.Tensor):
             p["src_t"] = torch.as_tensor(np.asarray(p["src_t"], np.float64)).to(p["speed"].device)
     return eik_solve_batched(problems, opts, stream)
+
+
+def _problem_array(problems: list[dict]):
+    arr = (EikProblem * len(problems))()
+    for i, p in enumerate(problems):
+        sp = p["speed"]
+        arr[i].speed = _ptr(sp)
+        arr[i].h = float(p["h"])
+        arr[i].ndim = sp.ndim
+        for k in range(3):
+            arr[i].dims[k] = int(sp.shape[k]) if k < sp.ndim else 1
+        arr[i].src_idx = _ptr(p["sources"])
+        arr[i].src_t = _ptr(p.get("src_t"))
+        arr[i].nsrc = int(p["sources"].numel())
+        arr[i].out_t = _ptr(p["out"])
+    return arr
+
+
+def eik_plan_create(problems: list[dict], opts: dict | None = None) -> int:
+    """Prepare a batch (torch CUDA tensors: speed, sources, optional src_t, out;
+    and h).  Returns the plan handle."""
+    L = load_library()
+    arr = _problem_array(problems)
+    o = _make_opts(opts)
+    h = ctypes.c_void_p()
+    rc = L.eik_plan_create(arr, len(problems), ctypes.byref(o) if o is not None else None,
+                           ctypes.byref(h))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    return h.value
+
+
+def eik_plan_enqueue(plan: int, stream=None) -> None:
+    rc = load_library().eik_plan_enqueue(plan, _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+
+
+def eik_plan_status(plan: int, stream=None) -> dict:
+    st = EikStats()
+    rc = load_library().eik_plan_status(plan, ctypes.byref(st), _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    return st.as_dict()
+
+
+def eik_plan_destroy(plan: int) -> None:
+    load_library().eik_plan_destroy(plan)
+
+
+class Plan:
+    """A batch of problems solved together in one persistent launch per solve.
+    ``enqueue`` only enqueues device work (no allocation, no host wait), so it
+    can be captured in a torch.cuda.CUDAGraph and replayed."""
+
+    def __init__(self, problems: list[dict], opts: dict | None = None):
+        import torch
+        for p in problems:
+            if p.get("out") is None:
+                p["out"] = torch.empty_like(p["speed"])
+            src = p["sources"]
+            if not isinstance(src, torch.Tensor):
+                src = torch.as_tensor(np.asarray(src, dtype=np.int64))
+            p["sources"] = src.to(device=p["speed"].device, dtype=torch.int64).contiguous()
+        self.problems = problems          # keeps the tensors alive
+        self.handle = eik_plan_create(problems, opts)
+
+    def enqueue(self, stream=None) -> None:
+        eik_plan_enqueue(self.handle, stream)
+
+    def status(self, stream=None) -> dict:
+        return eik_plan_status(self.handle, stream)
+
+    def close(self) -> None:
+        if self.handle:
+            eik_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

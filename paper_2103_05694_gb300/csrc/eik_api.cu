@@ -555,3 +555,250 @@ const char *eik_last_error(void) { return g_err; }
 int eik_abi_version(void) { return 100; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Plans: a batch of problems prepared once (validation, sources, workspace),
+// then solved any number of times by eik_plan_enqueue, which only enqueues
+// device work on the stream (no allocation, no host synchronisation), so a
+// CUDA graph can capture it.
+// ---------------------------------------------------------------------------
+struct eik_plan {
+  int device = -1;
+  int ndim = 2;
+  std::vector<Prob> probs;                   // host copies of the device records
+  std::vector<const double *> speeds;        // distinct speed arrays
+  std::vector<int64_t> speed_off, speed_n;
+  std::vector<double> speed_h;
+  int64_t total_tiles = 0, nseeds = 0, total_src = 0;
+  DevBuf<double> c;
+  DevBuf<unsigned long long> state;
+  DevBuf<unsigned char> tile_src;
+  DevBuf<unsigned> pend;
+  DevBuf<unsigned long long> slots;
+  DevBuf<int64_t> src_idx;
+  DevBuf<double> src_t;
+  DevBuf<SeedItem> seeds;
+  DevBuf<Prob> probs_d;
+  DevBuf<Ctl> ctl;
+  DevBuf<unsigned long long> count;
+  Ctl *ctl_host = nullptr;
+  SolveParams sp;
+  int grid = 1;
+  double k_delta = 0.0, delta_fixed = 0.0;
+  uint64_t cap = 0;
+
+  ~eik_plan() {
+    c.release(); state.release(); tile_src.release(); pend.release(); slots.release();
+    src_idx.release(); src_t.release(); seeds.release(); probs_d.release(); ctl.release();
+    count.release();
+    if (ctl_host) cudaFreeHost(ctl_host);
+  }
+};
+
+namespace {
+
+eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opts *opts,
+                      cudaStream_t stream) {
+  CK(cudaGetDevice(&pl.device), "cudaGetDevice");
+  pl.ndim = hps[0].ndim;
+  for (auto &hp : hps) {
+    if (hp.ndim != pl.ndim) { set_err("all problems of a plan must have the same ndim"); return EIK_EINVAL; }
+    if (!hp.speed_dev || !hp.out_dev) { set_err("plans take device pointers only"); return EIK_EINVAL; }
+  }
+  int64_t tx, ty, tz;
+  tile_shape(pl.ndim, tx, ty, tz);
+  std::vector<int> prob_speed(hps.size());
+  int64_t c_total = 0;
+  for (size_t i = 0; i < hps.size(); ++i) {
+    int found = -1;
+    for (size_t j = 0; j < pl.speeds.size(); ++j)
+      if (pl.speeds[j] == hps[i].speed && pl.speed_n[j] == hps[i].n && pl.speed_h[j] == hps[i].h)
+        found = (int)j;
+    if (found < 0) {
+      found = (int)pl.speeds.size();
+      pl.speeds.push_back(hps[i].speed);
+      pl.speed_off.push_back(c_total);
+      pl.speed_n.push_back(hps[i].n);
+      pl.speed_h.push_back(hps[i].h);
+      c_total += hps[i].n;
+    }
+    prob_speed[i] = found;
+  }
+  for (auto &hp : hps) pl.total_src += (int64_t)hp.src.size();
+  CK(pl.c.ensure((size_t)c_total), "plan: alloc c");
+  CK(pl.src_idx.ensure((size_t)std::max<int64_t>(pl.total_src, 1)), "plan: alloc src_idx");
+  CK(pl.src_t.ensure((size_t)std::max<int64_t>(pl.total_src, 1)), "plan: alloc src_t");
+  CK(pl.seeds.ensure((size_t)std::max<int64_t>(pl.total_src, 1)), "plan: alloc seeds");
+  CK(pl.probs_d.ensure(hps.size()), "plan: alloc problems");
+  CK(pl.ctl.ensure(1), "plan: alloc control block");
+  CK(pl.count.ensure(1), "plan: alloc count");
+  CK(cudaMallocHost(&pl.ctl_host, sizeof(Ctl)), "plan: pinned control block");
+  std::vector<SeedItem> seeds;
+  std::vector<int64_t> all_src;
+  std::vector<double> all_t0;
+  pl.probs.resize(hps.size());
+  for (size_t i = 0; i < hps.size(); ++i) {
+    HostProblem &hp = hps[i];
+    Prob &P = pl.probs[i];
+    std::memset(&P, 0, sizeof(P));
+    P.nx = hp.dims[2];
+    P.ny = hp.dims[1];
+    P.nz = hp.dims[0];
+    P.ntx = (P.nx + tx - 1) / tx;
+    P.nty = (P.ny + ty - 1) / ty;
+    P.ntz = (P.nz + tz - 1) / tz;
+    P.tile_base = pl.total_tiles;
+    pl.total_tiles += P.ntx * P.nty * P.ntz;
+    P.c = pl.c.p + pl.speed_off[prob_speed[i]];
+    P.t = hp.out;
+    P.src_idx = pl.src_idx.p + all_src.size();
+    P.src_t = pl.src_t.p + all_src.size();
+    P.nsrc = (int64_t)hp.src.size();
+    for (size_t k = 0; k < hp.src.size(); ++k) {
+      seeds.push_back(SeedItem{(int64_t)i, hp.src[k], hp.t0[k]});
+      all_src.push_back(hp.src[k]);
+      all_t0.push_back(hp.t0[k]);
+    }
+  }
+  pl.nseeds = (int64_t)seeds.size();
+  if (pl.total_tiles >= (int64_t(1) << 32)) { set_err("too many tiles"); return EIK_EINVAL; }
+  CK(pl.state.ensure((size_t)pl.total_tiles), "plan: alloc tile state");
+  CK(pl.tile_src.ensure((size_t)pl.total_tiles), "plan: alloc tile flags");
+  CK(pl.pend.ensure((size_t)pl.total_tiles * eik::kPendWords), "plan: alloc pending masks");
+  uint64_t want_cap = opts && opts->capacity > 0 ? (uint64_t)opts->capacity
+                                                 : (uint64_t)pl.total_tiles / 2 + 4096;
+  want_cap = next_pow2(std::max<uint64_t>(want_cap, 16));
+  while (want_cap * eik::kNumSlots > kMaxCapEntries && want_cap > 1024) want_cap >>= 1;
+  pl.cap = want_cap;
+  CK(pl.slots.ensure((size_t)(want_cap * eik::kNumSlots)), "plan: alloc frontier");
+  if (!all_src.empty()) {
+    CK(cudaMemcpyAsync(pl.src_idx.p, all_src.data(), all_src.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, stream), "plan: upload sources");
+    CK(cudaMemcpyAsync(pl.src_t.p, all_t0.data(), all_t0.size() * sizeof(double),
+                       cudaMemcpyHostToDevice, stream), "plan: upload source times");
+    CK(cudaMemcpyAsync(pl.seeds.p, seeds.data(), seeds.size() * sizeof(SeedItem),
+                       cudaMemcpyHostToDevice, stream), "plan: upload seeds");
+  }
+  CK(cudaMemcpyAsync(pl.probs_d.p, pl.probs.data(), pl.probs.size() * sizeof(Prob),
+                     cudaMemcpyHostToDevice, stream), "plan: upload problems");
+  CK(cudaStreamSynchronize(stream), "plan: uploads");
+
+  SolveParams &sp = pl.sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.probs = pl.probs_d.p;
+  sp.nprob = (int)pl.probs.size();
+  sp.ndim = pl.ndim;
+  sp.state = pl.state.p;
+  sp.tile_src = pl.tile_src.p;
+  sp.pend = pl.pend.p;
+  sp.slots = pl.slots.p;
+  sp.cap_mask = (unsigned)(pl.cap - 1);
+  sp.ctl = pl.ctl.p;
+  const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
+  sp.timeout_ns = tmo_ms * 1000000ll;
+  sp.counters = opts ? opts->counters : 0;
+  sp.test_stall = 0;
+  const int di = pl.ndim == 3 ? 1 : 0;
+  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow);
+  sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand[di];
+  sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
+  sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
+  sp.trace = nullptr;
+  sp.trace_cap = 0;
+  pl.k_delta = opts && opts->k_delta > 0 ? opts->k_delta : kDefaultKDelta[di];
+  pl.delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
+  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : kDefaultCtasPerSm[di];
+  const int occ = eik::persistent_blocks_per_sm(pl.ndim, sp.arith);
+  if (per_sm > occ) per_sm = occ;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl.device), "SM count");
+  int64_t grid = (int64_t)sms * per_sm;
+  if (grid > pl.total_tiles) grid = pl.total_tiles;
+  pl.grid = (int)std::max<int64_t>(grid, 1);
+  return EIK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eik_status eik_plan_create(const eik_problem *probs, int nprob, const eik_opts *opts,
+                           eik_plan **out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!out || nprob <= 0 || !probs) { set_err("bad plan arguments"); return EIK_EINVAL; }
+  *out = nullptr;
+  std::vector<HostProblem> hps((size_t)nprob);
+  for (int i = 0; i < nprob; ++i) {
+    const eik_problem &q = probs[i];
+    eik_status st = check_problem(q.speed, q.h, q.ndim, q.dims, q.src_idx, q.src_t, q.nsrc,
+                                  q.out_t, hps[(size_t)i], nullptr);
+    if (st != EIK_OK) return st;
+  }
+  eik_plan *pl = new (std::nothrow) eik_plan();
+  if (!pl) return EIK_ENOMEM;
+  eik_status st = plan_build(*pl, hps, opts, nullptr);
+  if (st != EIK_OK) {
+    delete pl;
+    return st;
+  }
+  *out = pl;
+  return EIK_OK;
+}
+
+eik_status eik_plan_enqueue(eik_plan *pl, void *stream) {
+  if (!pl) return EIK_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(pl->ctl.p, 0, sizeof(Ctl), s), "clear control block");
+  CK(cudaMemsetAsync(pl->state.p, 0, (size_t)pl->total_tiles * sizeof(unsigned long long), s),
+     "clear tile states");
+  CK(cudaMemsetAsync(pl->tile_src.p, 0, (size_t)pl->total_tiles, s), "clear tile flags");
+  CK(cudaMemsetAsync(pl->pend.p, 0, (size_t)pl->total_tiles * eik::kPendWords * sizeof(unsigned), s),
+     "clear pending masks");
+  CK(cudaMemsetAsync(pl->slots.p, 0xff, pl->slots.n * sizeof(unsigned long long), s), "clear frontier");
+  for (size_t j = 0; j < pl->speeds.size(); ++j) {
+    CK(eik::launch_init_c(pl->speeds[j], pl->speed_h[j], pl->c.p + pl->speed_off[j], pl->speed_n[j],
+                          pl->ctl.p, s), "init_c launch");
+  }
+  for (auto &P : pl->probs) CK(eik::launch_init_t(P.t, P.nx * P.ny * P.nz, s), "init_t launch");
+  CK(eik::launch_seed(pl->sp, pl->seeds.p, pl->nseeds, pl->k_delta, pl->delta_fixed, s), "seed launch");
+  CK(eik::launch_persistent(pl->sp, pl->grid, s), "solve launch");
+  return EIK_OK;
+}
+
+eik_status eik_plan_status(eik_plan *pl, eik_stats *stats, void *stream) {
+  if (!pl) return EIK_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(pl->ctl_host, pl->ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, s), "read status");
+  unsigned long long finite = 0;
+  if (stats && pl->sp.counters) {
+    CK(cudaMemsetAsync(pl->count.p, 0, sizeof(unsigned long long), s), "clear count");
+    CK(eik::launch_count_finite(pl->probs.data(), (int)pl->probs.size(), pl->count.p, s), "count");
+    CK(cudaMemcpyAsync(&finite, pl->count.p, sizeof(finite), cudaMemcpyDeviceToHost, s), "read count");
+  }
+  CK(cudaStreamSynchronize(s), "plan status");
+  const Ctl &c = *pl->ctl_host;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->evals = (int64_t)c.stats[eik::kStatEvals];
+    stats->decreases = (int64_t)c.stats[eik::kStatDecreases];
+    stats->visits = (int64_t)c.stats[eik::kStatVisits];
+    stats->pushes = (int64_t)c.stats[eik::kStatPushes];
+    stats->stale_pops = (int64_t)c.stats[eik::kStatStale];
+    stats->rounds = (int64_t)c.stats[eik::kStatRounds];
+    stats->max_queue = (int64_t)c.stats[eik::kStatMaxQueue];
+    stats->ctas = pl->grid;
+    if (pl->sp.counters) stats->good = (int64_t)finite - pl->total_src;
+  }
+  switch (c.status) {
+    case 0: return EIK_OK;
+    case eik::kEinval: set_err("invalid input data"); return EIK_EINVAL;
+    case eik::kEtimeout: set_err("device wait timed out"); return EIK_ETIMEOUT;
+    case eik::kEcapacity: set_err("frontier capacity exhausted (create the plan with a larger capacity)");
+      return EIK_ECAPACITY;
+    default: return EIK_ECUDA;
+  }
+}
+
+void eik_plan_destroy(eik_plan *pl) { delete pl; }
+
+}  // extern "C"
