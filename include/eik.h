@@ -183,6 +183,24 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
                              double *out_t, const eik_opts *opts, eik_stats *stats,
                              void *stream);
 
+/* Adjoint for traveltime tomography (not in the paper: implicit
+ * differentiation of the real-arithmetic local equations at the computed
+ * fixed point).  For each problem i, probs[i].out_t must hold the arrival
+ * times solved for exactly that problem (speed, h, sources); dL_dt[i] (NULL,
+ * or dL_dt == NULL: zero) is d(loss)/d(t) per cell; dL_dslowness[i] receives
+ * d(loss)/d(s) with slowness s = 1/v per cell (written, not accumulated; 0 at
+ * sources and unreachable cells).  For a reached non-source cell n with axis
+ * minima a_k and active axes A = {k : a_k < t_n}, S_n = sum_A (t_n - a_k):
+ *   lambda_n = dL_dt_n + sum_{downwind m} lambda_m (t_m - t_n) / S_m
+ *   (halved where m's two neighbours on that axis tie), downwind neighbours in
+ *   the order x-, x+, y-, y+, z-, z+;  dL/ds_n = lambda_n (h^2 s_n) / S_n.
+ * Every operation is separately rounded in that order, so results are
+ * reproducible bit for bit.  Device pointers only.  stats (optional): good =
+ * cells processed, visits = reached cells. */
+eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
+                       double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,
+                       void *stream);
+
 /* Plans: a batch prepared once and solved many times.
  * eik_plan_create checks the problems (device pointers only; all of one ndim),
  * copies and de-duplicates their sources, and allocates the plan's own device

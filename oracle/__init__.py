@@ -17,6 +17,8 @@ Functions and the passages they follow:
   method, Algorithm 5 (mode 1).
 * ``relax_order`` -- relaxation in a caller-given order (Theorem 1).
 * ``residual`` -- the fixed-point residual of Table 3.
+* ``adjoint`` -- d(loss)/d(slowness) through the fixed point (not in the paper:
+  implicit differentiation of the real-arithmetic local equations).
 """
 from __future__ import annotations
 
@@ -78,6 +80,8 @@ def lib():
         L.orc_residual.argtypes = [ctypes.c_int, _p, _p, _d, _p, _p, _i64, _p,
                                    ctypes.POINTER(_d)]
         L.orc_residual.restype = _i64
+        L.orc_adjoint.argtypes = [ctypes.c_int, _p, _p, _d, _p, _i64, _p, _p, _p, _p]
+        L.orc_adjoint.restype = ctypes.c_int
     return _lib
 
 
@@ -177,3 +181,17 @@ def residual(speed: np.ndarray, h: float, sources, t: np.ndarray, src_t=None):
     if bad < 0:
         raise RuntimeError("orc_residual failed")
     return int(bad), float(mr.value)
+
+
+def adjoint(speed: np.ndarray, h: float, sources, t: np.ndarray, dL_dt: np.ndarray):
+    """(lambda, dL/ds) for the fixed point t of the problem and g = dL/dt."""
+    speed, dims, src, _ = _grid_args(speed, sources, None)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    g = np.ascontiguousarray(dL_dt, dtype=np.float64)
+    lam = np.empty(speed.shape)
+    gs = np.empty(speed.shape)
+    rc = lib().orc_adjoint(speed.ndim, _ptr(dims), _ptr(speed), h, _ptr(src), src.size, _ptr(t),
+                           _ptr(g), _ptr(lam), _ptr(gs))
+    if rc != 0:
+        raise RuntimeError("orc_adjoint failed")
+    return lam, gs

@@ -495,3 +495,111 @@ int64_t orc_residual(int ndim, const int64_t *dims, const double *v, double h,
     if (max_rel) *max_rel = worst;
     return bad;
 }
+
+/* ---------------------------------------------------------------------------
+ * Adjoint of the fixed point (traveltime tomography).  Not in the paper: the
+ * derivative of the real-arithmetic local equations at the computed field.
+ * For a reached non-source cell n with axis minima a_k and the active axes
+ * A(n) = {k : a_k < t_n} (both neighbours of an axis off-grid or at +inf: not
+ * active), the local equation sum_{k in A} (t_n - a_k)^2 = h^2 s_n^2 with
+ * slowness s = 1/v gives
+ *   dt_n = [ sum_{k in A} (t_n - a_k) da_k + h^2 s_n ds_n ] / S_n,
+ *   S_n  = sum_{k in A} (t_n - a_k)      (terms summed in axis order x, y, z),
+ * and a_k is the neighbour holding the axis minimum (both neighbours, weight
+ * 1/2 each, when they are equal).  For a loss L(t) with g = dL/dt:
+ *   lambda_n = g_n + sum over downwind neighbours m of lambda_m * w(m, n),
+ *   w(m, n)  = fl(fl(t_m - t_n) / S_m), halved when n shares the axis minimum
+ *              of m with m's other neighbour on that axis,
+ *   dL/ds_n  = lambda_n * fl(fl(fl(h*h) * s_n) / S_n),  s_n = fl(1/v_n),
+ * with the downwind neighbours taken in the fixed order x-, x+, y-, y+, z-, z+
+ * and every operation separately rounded.  Sources and unreached cells get
+ * dL/ds = 0.  lambda is computed in decreasing t (every downwind neighbour has
+ * a larger t).  Returns 0, or -1 on bad arguments / allocation failure.
+ * ------------------------------------------------------------------------- */
+
+typedef struct { double t; int64_t idx; } orc_tsort;
+
+static int orc_tsort_desc(const void *pa, const void *pb)
+{
+    const orc_tsort *a = (const orc_tsort *)pa, *b = (const orc_tsort *)pb;
+    if (a->t > b->t) return -1;
+    if (a->t < b->t) return 1;
+    return (a->idx > b->idx) - (a->idx < b->idx);
+}
+
+/* S_n over the active axes of a reached non-source cell (0 if none). */
+static double orc_upwind_sum(const orc_grid *g, const double *t, int64_t n)
+{
+    double a[3];
+    orc_axis_minima(g, t, n, a);
+    double S = 0.0;
+    for (int k = 0; k < g->D; ++k)
+        if (a[k] < t[n]) S = S + (t[n] - a[k]);
+    return S;
+}
+
+/* Weight of neighbour u (at offset side along axis k of m) in dt_m, or 0. */
+static double orc_weight(const orc_grid *g, const double *t, const unsigned char *is_src,
+                         int64_t m, int k, int64_t u)
+{
+    if (is_src[m] || !(t[m] < ORC_INF)) return 0.0;
+    double a[3];
+    orc_axis_minima(g, t, m, a);
+    if (!(a[k] < t[m]) || t[u] != a[k]) return 0.0;
+    double S = orc_upwind_sum(g, t, m);
+    double w = (t[m] - t[u]) / S;
+    /* the other neighbour of m on axis k, if in-grid, equal to the minimum */
+    int64_t rem = m, coord = 0;
+    for (int j = 0; j <= k; ++j) { coord = rem % g->n[j]; rem /= g->n[j]; }
+    int64_t other = (u < m) ? m + g->s[k] : m - g->s[k];
+    int in = (u < m) ? (coord + 1 < g->n[k]) : (coord > 0);
+    if (in && t[other] == t[u]) w = w * 0.5;
+    return w;
+}
+
+int orc_adjoint(int ndim, const int64_t *dims, const double *v, double h,
+                const int64_t *src_idx, int64_t nsrc, const double *t, const double *dL_dt,
+                double *lambda, double *dL_ds)
+{
+    orc_grid g;
+    if (orc_grid_make(&g, ndim, dims)) return -1;
+    unsigned char *is_src = (unsigned char *)calloc((size_t)g.N, 1);
+    orc_tsort *order = (orc_tsort *)malloc((size_t)g.N * sizeof(orc_tsort));
+    if (!is_src || !order) { free(is_src); free(order); return -1; }
+    for (int64_t s = 0; s < nsrc; ++s) is_src[src_idx[s]] = 1;
+    int64_t nr = 0;
+    for (int64_t i = 0; i < g.N; ++i) {
+        lambda[i] = 0.0;
+        dL_ds[i] = 0.0;
+        if (t[i] < ORC_INF) { order[nr].t = t[i]; order[nr].idx = i; ++nr; }
+    }
+    qsort(order, (size_t)nr, sizeof(orc_tsort), orc_tsort_desc);
+    double hh = h * h;
+    for (int64_t q = 0; q < nr; ++q) {
+        int64_t n = order[q].idx;
+        double lam = dL_dt[n];
+        int64_t rem = n;
+        for (int k = 0; k < g.D; ++k) {
+            int64_t coord = rem % g.n[k];
+            rem /= g.n[k];
+            for (int side = 0; side < 2; ++side) {
+                int64_t m;
+                if (side == 0) { if (coord == 0) continue; m = n - g.s[k]; }
+                else { if (coord + 1 == g.n[k]) continue; m = n + g.s[k]; }
+                if (!(t[m] > t[n])) continue;              /* downwind only */
+                double w = orc_weight(&g, t, is_src, m, k, n);
+                if (w != 0.0) lam = lam + lambda[m] * w;
+            }
+        }
+        lambda[n] = lam;
+        if (!is_src[n]) {
+            double S = orc_upwind_sum(&g, t, n);
+            if (S > 0.0) {
+                double s = 1.0 / v[n];
+                dL_ds[n] = lam * ((hh * s) / S);
+            }
+        }
+    }
+    free(is_src); free(order);
+    return 0;
+}

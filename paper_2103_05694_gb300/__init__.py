@@ -108,13 +108,17 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     L.eik_plan_status.restype = ctypes.c_int
     L.eik_plan_destroy.argtypes = [vp]
     L.eik_plan_destroy.restype = None
+    L.eik_adjoint.argtypes = [ctypes.POINTER(EikProblem), ctypes.c_int, ctypes.POINTER(vp),
+                              ctypes.POINTER(vp), ctypes.POINTER(EikOpts),
+                              ctypes.POINTER(EikStats), vp]
+    L.eik_adjoint.restype = ctypes.c_int
     _lib = L
     return L
 
 
 EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
             "eik_abi_version", "eik_selftest", "eik_solve_noalloc", "eik_plan_create",
-            "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy"]
+            "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy", "eik_adjoint"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3", "group2x8", "group3x8",
                    "group2x4"]
@@ -375,3 +379,77 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def eik_adjoint(problems: list[dict], dL_dt: list, dL_ds: list, opts: dict | None = None,
+                stream=None) -> dict:
+    """d(loss)/d(slowness) through the solved fields ``problems[i]["out"]``.
+    dL_dt[i] (tensor or None) is d(loss)/d(t); dL_ds[i] (tensor) receives the
+    gradient.  All torch CUDA tensors."""
+    L = load_library()
+    arr = _problem_array(problems)
+    n = len(problems)
+    gt = (ctypes.c_void_p * n)(*[_ptr(x) for x in dL_dt])
+    gs = (ctypes.c_void_p * n)(*[_ptr(x) for x in dL_ds])
+    st = EikStats()
+    o = _make_opts(opts)
+    rc = L.eik_adjoint(arr, n, gt, gs, ctypes.byref(o) if o is not None else None,
+                       ctypes.byref(st), _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    return st.as_dict()
+
+
+def _make_eikonal_fn():
+    import torch
+
+    class EikonalFn(torch.autograd.Function):
+        """Arrival times of several source sets on one slowness field, and the
+        exact adjoint as backward.
+
+        forward(slowness, h, sources): slowness (float64 CUDA tensor, 2D or 3D),
+        sources a list of int64 tensors (flat indices), one solve per entry, all
+        in one persistent launch.  Returns t with shape (len(sources), *grid).
+        backward: d(loss)/d(slowness) summed over the solves."""
+
+        @staticmethod
+        def forward(ctx, slowness, h, sources):
+            speed = torch.reciprocal(slowness).contiguous()
+            outs = []
+            probs = []
+            for src in sources:
+                out = torch.empty_like(speed)
+                probs.append({"speed": speed, "h": h, "sources": src, "out": out})
+                outs.append(out)
+            eik_solve_batched(probs)
+            t = torch.stack(outs)
+            ctx.save_for_backward(speed, t)
+            ctx.h = h
+            ctx.sources = sources
+            return t
+
+        @staticmethod
+        def backward(ctx, grad_t):
+            speed, t = ctx.saved_tensors
+            probs = []
+            grads = []
+            gts = []
+            for i, src in enumerate(ctx.sources):
+                probs.append({"speed": speed, "h": ctx.h, "sources": src, "out": t[i].contiguous()})
+                grads.append(torch.empty_like(speed))
+                gts.append(grad_t[i].contiguous())
+            eik_adjoint(probs, gts, grads)
+            return torch.stack(grads).sum(dim=0), None, None
+
+    return EikonalFn
+
+
+_eikonal_fn = None
+
+
+def eikonal(slowness, h: float, sources):
+    """Differentiable batched solve (see EikonalFn)."""
+    global _eikonal_fn
+    if _eikonal_fn is None:
+        _eikonal_fn = _make_eikonal_fn()
+    return _eikonal_fn.apply(slowness, h, list(sources))

@@ -802,3 +802,103 @@ eik_status eik_plan_status(eik_plan *pl, eik_stats *stats, void *stream) {
 void eik_plan_destroy(eik_plan *pl) { delete pl; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// eik_adjoint: d(loss)/d(slowness) through the fixed points of a batch.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct AdjWorkspace {
+  DevBuf<int> cnt;
+  DevBuf<double> S, lam;
+  DevBuf<unsigned long long> queue;
+  DevBuf<eik::AdjProb> probs;
+  DevBuf<eik::AdjCtl> ctl;
+  DevBuf<int64_t> src;
+  eik::AdjCtl *ctl_host = nullptr;
+};
+AdjWorkspace g_adj;
+
+}  // namespace
+
+extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
+                                  double *const *dL_dslowness, const eik_opts *opts,
+                                  eik_stats *stats, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (nprob <= 0 || !probs || !dL_dslowness) { set_err("bad adjoint arguments"); return EIK_EINVAL; }
+  std::vector<HostProblem> hps((size_t)nprob);
+  int64_t total = 0, total_src = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const eik_problem &q = probs[i];
+    eik_status st = check_problem(q.speed, q.h, q.ndim, q.dims, q.src_idx, q.src_t, q.nsrc,
+                                  q.out_t, hps[(size_t)i], s);
+    if (st != EIK_OK) return st;
+    if (!hps[(size_t)i].speed_dev || !hps[(size_t)i].out_dev || !is_device_ptr(dL_dslowness[i]) ||
+        (dL_dt && dL_dt[i] && !is_device_ptr(dL_dt[i]))) {
+      set_err("eik_adjoint takes device pointers only (problem %d)", i);
+      return EIK_EINVAL;
+    }
+    total += hps[(size_t)i].n;
+    total_src += (int64_t)hps[(size_t)i].src.size();
+  }
+  if (!g_adj.ctl_host) CK(cudaMallocHost(&g_adj.ctl_host, sizeof(eik::AdjCtl)), "adjoint: pinned");
+  CK(g_adj.cnt.ensure((size_t)total), "adjoint: alloc counts");
+  CK(g_adj.S.ensure((size_t)total), "adjoint: alloc S");
+  CK(g_adj.lam.ensure((size_t)total), "adjoint: alloc lambda");
+  CK(g_adj.queue.ensure((size_t)total), "adjoint: alloc queue");
+  CK(g_adj.probs.ensure((size_t)nprob), "adjoint: alloc problems");
+  CK(g_adj.ctl.ensure(1), "adjoint: alloc control");
+  CK(g_adj.src.ensure((size_t)std::max<int64_t>(total_src, 1)), "adjoint: alloc sources");
+  std::vector<eik::AdjProb> ap((size_t)nprob);
+  std::vector<int64_t> all_src;
+  int64_t base = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const HostProblem &hp = hps[(size_t)i];
+    eik::AdjProb &A = ap[(size_t)i];
+    A.t = hp.out;
+    A.v = hp.speed;
+    A.g = dL_dt ? dL_dt[i] : nullptr;
+    A.grad = dL_dslowness[i];
+    A.lam = g_adj.lam.p + base;
+    A.S = g_adj.S.p + base;
+    A.cnt = g_adj.cnt.p + base;
+    A.src_idx = g_adj.src.p + all_src.size();
+    A.nsrc = (int64_t)hp.src.size();
+    A.nx = hp.dims[2];
+    A.ny = hp.dims[1];
+    A.nz = hp.dims[0];
+    A.ndim = hp.ndim;
+    A.base = base;
+    A.hh = hp.h * hp.h;
+    all_src.insert(all_src.end(), hp.src.begin(), hp.src.end());
+    base += hp.n;
+  }
+  if (!all_src.empty())
+    CK(cudaMemcpyAsync(g_adj.src.p, all_src.data(), all_src.size() * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, s), "adjoint: upload sources");
+  CK(cudaMemcpyAsync(g_adj.probs.p, ap.data(), ap.size() * sizeof(eik::AdjProb),
+                     cudaMemcpyHostToDevice, s), "adjoint: upload problems");
+  CK(cudaMemsetAsync(g_adj.cnt.p, 0, (size_t)total * sizeof(int), s), "adjoint: clear counts");
+  CK(cudaMemsetAsync(g_adj.queue.p, 0xff, (size_t)total * sizeof(unsigned long long), s),
+     "adjoint: clear queue");
+  CK(cudaMemsetAsync(g_adj.ctl.p, 0, sizeof(eik::AdjCtl), s), "adjoint: clear control");
+  const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
+  CK(eik::launch_adjoint(g_adj.probs.p, nprob, total, g_adj.ctl.p, g_adj.queue.p,
+                         tmo_ms * 1000000ll, s), "adjoint launch");
+  CK(cudaMemcpyAsync(g_adj.ctl_host, g_adj.ctl.p, sizeof(eik::AdjCtl), cudaMemcpyDeviceToHost, s),
+     "adjoint: read status");
+  CK(cudaStreamSynchronize(s), "adjoint");
+  const eik::AdjCtl &c = *g_adj.ctl_host;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->good = (int64_t)c.done;
+    stats->visits = (int64_t)c.reached;
+  }
+  if (c.status == eik::kEtimeout) { set_err("adjoint: device wait timed out"); return EIK_ETIMEOUT; }
+  if (c.status != 0) return EIK_ECUDA;
+  if (c.done != c.reached) { set_err("adjoint: %llu of %llu cells processed",
+                                     (unsigned long long)c.done, (unsigned long long)c.reached);
+                             return EIK_ECUDA; }
+  return EIK_OK;
+}

@@ -120,4 +120,35 @@ cudaError_t launch_count_finite(const Prob *host_probs, int nprob, unsigned long
                                 cudaStream_t stream);
 int persistent_blocks_per_sm(int ndim, int arith);
 
+// Adjoint (eik_adjoint.cu).
+struct AdjProb {
+  const double *t;          // forward arrival times (the exact fixed point)
+  const double *v;          // speed
+  const double *g;          // dL/dt (NULL: 0)
+  double *grad;             // dL/ds output
+  double *lam;              // adjoint variable (workspace)
+  double *S;                // sum of the active upwind differences (workspace)
+  int *cnt;                 // downwind users not yet processed (workspace)
+  const int64_t *src_idx;   // sorted unique sources
+  int64_t nsrc;
+  int64_t nx, ny, nz;
+  int ndim;
+  int64_t base;             // first global cell index of this problem
+  double hh;                // fl(h * h)
+};
+
+struct AdjCtl {
+  unsigned long long reached;
+  unsigned long long pad0[15];
+  unsigned long long head;
+  unsigned long long pad1[15];
+  unsigned long long tail;
+  unsigned long long pad2[15];
+  unsigned long long done;
+  unsigned status;
+};
+
+cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, AdjCtl *ctl,
+                           unsigned long long *queue, long long timeout_ns, cudaStream_t stream);
+
 }  // namespace eik

@@ -1,0 +1,158 @@
+"""The GPU adjoint (eik_adjoint through the C ABI) equals the CPU oracle adjoint
+bit for bit, and the tomography gradient of the differentiable batched solve
+matches central finite differences (relative 1e-6) on the 1024^2 workload."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2103_05694_gb300 as eik  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from paper_2103_05694_gb300 import build
+    build.build()
+    eik.load_library()
+
+
+@pytest.mark.parametrize("shape", [(40, 70), (3, 300), (12, 15, 17)])
+def test_adjoint_bit_exact_vs_oracle(shape):
+    rng = np.random.Generator(np.random.PCG64(5))
+    probs, ref = [], []
+    base = synth.random_problem(21, shape, n_src=1, contrast=6.0, smooth_sigma=1.0, h=0.5)
+    speed = torch.from_numpy(base.speed).to(DEV)
+    for k in range(4):
+        src = rng.choice(base.speed.size, size=1 + k % 3, replace=False).astype(np.int64)
+        t = oracle.fmm(base.speed, base.h, src).t
+        g = np.where(rng.random(shape) < 0.05, rng.standard_normal(shape), 0.0)
+        lam, gs = oracle.adjoint(base.speed, base.h, src, t, g)
+        ref.append(gs)
+        out = torch.from_numpy(t).to(DEV)
+        probs.append(dict(speed=speed, h=base.h, sources=torch.from_numpy(src).to(DEV), out=out,
+                          g=torch.from_numpy(g).to(DEV), grad=torch.full_like(out, np.nan)))
+    st = eik.eik_adjoint([{k: p[k] for k in ("speed", "h", "sources", "out")} for p in probs],
+                         [p["g"] for p in probs], [p["grad"] for p in probs])
+    torch.cuda.synchronize()
+    for p, r in zip(probs, ref):
+        got = p["grad"].cpu().numpy()
+        assert np.array_equal(got.view(np.uint64), r.view(np.uint64))
+    assert st["good"] == st["visits"]
+
+
+def test_autograd_function_matches_oracle_adjoint():
+    p = synth.random_problem(8, (30, 40), n_src=1, contrast=4.0, smooth_sigma=2.0, h=1.0)
+    s = torch.from_numpy(1.0 / p.speed).to(DEV).requires_grad_(True)
+    srcs = [torch.tensor([0], device=DEV), torch.tensor([39, 600], device=DEV)]
+    t = eik.eikonal(s, p.h, srcs)
+    w = torch.from_numpy(np.random.default_rng(0).random((2, 30, 40))).to(DEV)
+    loss = 0.5 * (t * w).sum()
+    loss.backward()
+    speed = (1.0 / (1.0 / p.speed))      # the forward passes v = fl(1/s)
+    v_used = 1.0 / s.detach().cpu().numpy()
+    total = np.zeros((30, 40))
+    for i, src in enumerate([[0], [39, 600]]):
+        tt = oracle.fmm(v_used, p.h, src).t
+        assert np.array_equal(tt, t[i].detach().cpu().numpy())
+        _, gs = oracle.adjoint(v_used, p.h, src, tt, 0.5 * w[i].cpu().numpy())
+        total = total + gs
+    got = s.grad.cpu().numpy()
+    assert np.allclose(got, total, rtol=1e-14, atol=0)
+    del speed
+
+
+def test_adjoint_bit_exact_vs_oracle_tomography_grid():
+    """The 1024^2 tomography layout, two surface sources in one batch: forward
+    times and the adjoint gradient both equal the oracle's bit for bit."""
+    cfg = synth.config5()
+    h, rcv = cfg["h"], cfg["receivers"]
+    v = 1.0 / (1.0 / cfg["start"])
+    speed = torch.from_numpy(v).to(DEV)
+    probs, ref = [], []
+    for k in (0, 17):
+        src = np.array([int(cfg["sources"][k])], dtype=np.int64)
+        t = oracle.fmm(v, h, src).t
+        t_obs = oracle.fmm(cfg["true"], h, src).t
+        g = np.zeros(v.shape)
+        g.reshape(-1)[rcv] = (t - t_obs).reshape(-1)[rcv]
+        ref.append((t, oracle.adjoint(v, h, src, t, g)[1]))
+        out = torch.empty_like(speed)
+        probs.append(dict(speed=speed, h=h, sources=torch.from_numpy(src).to(DEV), out=out,
+                          g=torch.from_numpy(g).to(DEV), grad=torch.full_like(out, np.nan)))
+    eik.eik_solve_batched([{k: p[k] for k in ("speed", "h", "sources", "out")} for p in probs])
+    eik.eik_adjoint([{k: p[k] for k in ("speed", "h", "sources", "out")} for p in probs],
+                    [p["g"] for p in probs], [p["grad"] for p in probs])
+    torch.cuda.synchronize()
+    for p, (t, gs) in zip(probs, ref):
+        assert np.array_equal(p["out"].cpu().numpy().view(np.uint64), t.view(np.uint64))
+        assert np.array_equal(p["grad"].cpu().numpy().view(np.uint64), gs.view(np.uint64))
+
+
+@pytest.mark.slow
+def test_tomography_gradient_central_differences():
+    """1024^2, 32 sources, 512 receivers, L = 1/2 sum (t - t_obs)^2.  Finite
+    differences on 64 random cells (among those with |g| above 1e-6 of the
+    largest) with the fourth-order central stencil
+    (8 D(eps) - D(2 eps)) / (12 eps), D(e) = L(s + e) - L(s - e), eps = 1e-4 s.
+    D is formed from t+ - t- so it does not cancel in L itself.  A step of
+    1e-4 keeps the rounding of the perturbed times (a few ulps, ~1e-8 of the
+    difference) and the stencil's eps^4 term far below the tolerance.
+    Relative error against max(|g_FD|, 1e-3 max|g|) must be <= 1e-6 (a
+    perturbation may flip an upwind choice: at most a few cells may exceed it).
+    The four perturbed fields x 32 sources of one cell run as one batch."""
+    cfg = synth.config5()
+    h = cfg["h"]
+    n = cfg["start"].shape[0]
+    s_true = torch.from_numpy(1.0 / cfg["true"]).to(DEV)
+    s0 = torch.from_numpy(1.0 / cfg["start"]).to(DEV)
+    srcs = [torch.tensor([int(i)], device=DEV) for i in cfg["sources"]]
+    rcv = torch.from_numpy(cfg["receivers"]).to(DEV)
+    with torch.no_grad():
+        t_obs = eik.eikonal(s_true, h, srcs).reshape(len(srcs), -1)[:, rcv]
+    assert float((t_obs > 0).float().mean()) == 1.0
+
+    s = s0.clone().requires_grad_(True)
+    L = 0.5 * ((eik.eikonal(s, h, srcs).reshape(len(srcs), -1)[:, rcv] - t_obs) ** 2).sum()
+    L.backward()
+    flat = s.grad.detach().reshape(-1)
+    gmax = float(flat.abs().max())
+    assert gmax > 0
+    cand = torch.nonzero(flat.abs() > 1e-6 * gmax).reshape(-1).cpu().numpy()
+    rng = np.random.Generator(np.random.PCG64(64))
+    cells = rng.choice(cand, size=64, replace=False)
+
+    steps = (1.0, -1.0, 2.0, -2.0)          # multiples of eps
+    speeds = [torch.empty_like(s0) for _ in steps]
+    outs = [[torch.empty_like(s0) for _ in srcs] for _ in steps]
+    probs = [{"speed": speeds[j], "h": h, "sources": src, "out": outs[j][i]}
+             for j in range(len(steps)) for i, src in enumerate(srcs)]
+    fd = []
+    with torch.no_grad():
+        for c in cells:
+            eps = 1e-4 * float(s0.reshape(-1)[c])
+            for j, m in enumerate(steps):
+                sp = s0.clone().reshape(-1)
+                sp[c] += m * eps
+                speeds[j].copy_(torch.reciprocal(sp.reshape(n, n)))
+            eik.eik_solve_batched(probs)
+            tr = [torch.stack([o.reshape(-1)[rcv] for o in outs[j]]) for j in range(len(steps))]
+
+            def D(jp, jm):
+                return float(0.5 * ((tr[jp] - tr[jm]) * (tr[jp] + tr[jm] - 2.0 * t_obs)).sum())
+            fd.append((8.0 * D(0, 1) - D(2, 3)) / (12.0 * eps))
+    fd = np.array(fd)
+    ad = flat[torch.from_numpy(cells).to(DEV)].cpu().numpy()
+    scale = np.maximum(np.abs(fd), 1e-3 * gmax)
+    err = np.abs(ad - fd) / scale
+    print("tomography FD: median rel err %.2e, max %.2e, cells > 1e-6: %d"
+          % (np.median(err), err.max(), int((err > 1e-6).sum())))
+    assert np.median(err) <= 1e-6, (np.median(err), err.max())
+    assert int((err > 1e-6).sum()) <= 3, err
