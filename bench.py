@@ -1,16 +1,27 @@
 """Benchmark: useful grid-point updates per second of the exact Eikonal solve.
 
-One step = one pass of the whole hot path on one grid: per-cell constants
-r = fl(h/v) and t = +inf, source seeding, and the persistent bucket-scheduled
-relaxation to the exact fixed point (Algorithm 6 with the exactly monotone
-d-bar of arXiv 2103.05694).  Default workload: the 2D layered seismic-like
-model, 2301 x 751 cells, h = 4 m, one surface source (synthetic; it stands in
-for the paper's Marmousi section).
+One step = one pass of the whole hot path over one batch of synthetic input:
+per-cell constants c = fl(fl(h/v)^2) and t = +inf, source seeding, and the
+persistent bucket-scheduled relaxation to the exact fixed point (Algorithm 6
+with the exactly monotone d-bar of arXiv 2103.05694); for the tomography
+workload the step adds the adjoint gradient.  Workloads (synthetic, seeded):
+
+  layered_2d     2D layered seismic-like section 2301 x 751, h = 4 m, one
+                 surface source (default; it stands in for the Marmousi section)
+  const_2d       2D 129 x 129, constant speed, h = 1/128, centre source
+  checker_3d     3D 256^3 smooth random 1500-4500 m/s with a 10:1 checkerboard
+                 in the central 128^3 block, h = 10 m, source at (128, 128, 0)
+  batched_3d     64 single-source solves on one shared smooth 128^3 model plus
+                 24 grids of uneven size (64^3..192^3, 1-4 sources each), one
+                 plan replayed from a captured CUDA graph
+  tomography_2d  2D 1024^2, 32 surface sources, 512 receivers: batched forward
+                 solve + adjoint gradient of the receiver misfit
 
 Prints one JSON line (rank 0).  Arms:
   default          the CUDA library through its C ABI, inputs resident in HBM;
-  --impl reference the CPU oracle (single-threaded fast marching, Algorithm 2)
-                   timed on the host cores on a bounded sample of the workload.
+  --impl reference the CPU oracle (single-threaded fast marching, Algorithm 2,
+                   plus the oracle adjoint for tomography) on the host cores,
+                   on bounded samples of the same workload.
 Multi-GPU (torchrun): every rank solves its own replica (the single-grid path
 does not shard: replicas only, weak scaling); no collective touches the data.
 """
@@ -33,16 +44,18 @@ import synth  # noqa: E402
 
 METRIC = "useful grid-point updates/s and % HBM roofline (bit-exact vs FP64 FMM oracle)"
 UNIT = "updates/s"
-B_ALG = 24          # algorithmic bytes per useful update: read r once, read t once, write t once
+B_ALG = 24          # algorithmic bytes per useful update: read c once, read t once, write t once
 L2_FLUSH_BYTES = 512 << 20
 
-
-def workloads():
-    return {
-        "1": ("2d_129x129_const (config 1)", synth.config1),
-        "2": ("2d_2301x751_layered (config 2)", synth.config2),
-        "3": ("3d_256cube_smooth_checker (config 3)", synth.config3),
-    }
+WORKLOADS = {
+    "layered_2d": "2d_2301x751_layered_h4_1src",
+    "const_2d": "2d_129x129_const_h1/128_centre_src",
+    "checker_3d": "3d_256cube_smooth_checker_h10_1src",
+    "batched_3d": "3d_batch_64x128cube_shared_plus_24_uneven_grids",
+    "tomography_2d": "2d_1024x1024_tomography_32src_512rcv_fwd_adj",
+}
+SINGLE = {"layered_2d": synth.layered_2d_2301x751, "const_2d": synth.const_2d_129,
+          "checker_3d": synth.checker_3d_256}
 
 
 def scaled_layered(scale: float):
@@ -51,6 +64,12 @@ def scaled_layered(scale: float):
     speed = synth.layered_section(nx, nz, 4.0, seed=2)
     src = np.array([nx // 2], dtype=np.int64)
     return synth.Problem(f"2d_{nx}x{nz}_layered", speed, 4.0, src, np.zeros(1), {})
+
+
+def useful_of(prob) -> int:
+    """Cells the solve must settle: every cell is reachable (speeds > 0), the
+    distinct sources are set, not updated."""
+    return int(prob.ncells - len(np.unique(prob.sources)))
 
 
 def measured_peaks():
@@ -72,6 +91,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
@@ -85,7 +105,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc is not None:
             time.sleep(0.1)
             self.proc.terminate()
@@ -117,58 +136,432 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_reference(args, wl_name, prob, useful):
-    """The CPU oracle, as it stands, on bounded samples of the same workload."""
+# --------------------------------------------------------------------------
+# CPU oracle legs (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+
+def oracle_units(args):
+    """A list of (label, callable returning useful updates) units of CPU work that
+    sample the workload: one full oracle solve (plus adjoint) per unit."""
     import oracle
     oracle.build()
+    wl = args.workload
+    if wl in SINGLE:
+        prob = scaled_layered(args.scale) if (wl == "layered_2d" and args.scale != 1.0) \
+            else SINGLE[wl]()
+
+        def unit(p=prob):
+            oracle.fmm(p.speed, p.h, p.sources, p.src_t)
+            return useful_of(p), 0.0
+        return [("full single-threaded FMM solve of the workload", unit)]
+    if wl == "batched_3d":
+        units = []
+        for p in synth.batched_3d():
+            def unit(p=p):
+                oracle.fmm(p.speed, p.h, p.sources, p.src_t)
+                return useful_of(p), 0.0
+            units.append((f"FMM solve of problem {p.name}", unit))
+        return units
+    cfg = synth.tomography_2d_1024()
+    h, rcv = cfg["h"], cfg["receivers"]
+    v0 = 1.0 / (1.0 / cfg["start"])
+    observed = {}
+    units = []
+    for k, s in enumerate(cfg["sources"]):
+        def unit(s=int(s)):
+            untimed = 0.0
+            if s not in observed:                  # observed data: input, not timed
+                t0 = time.perf_counter()
+                observed[s] = oracle.fmm(cfg["true"], h, [s]).t
+                untimed = time.perf_counter() - t0
+            t = oracle.fmm(v0, h, [s]).t
+            g = np.zeros(v0.shape)
+            g.reshape(-1)[rcv] = (t - observed[s]).reshape(-1)[rcv]
+            oracle.adjoint(v0, h, [s], t, g)
+            return int(v0.size - 1), untimed
+        units.append((f"FMM solve + adjoint of source {k}", unit))
+    return units
+
+
+def time_oracle(units, seconds: float, max_units: int | None = None):
+    """Runs units round robin until `seconds` of CPU work (at least one unit)."""
+    done, useful, t_sum = 0, 0, 0.0
+    per = []
+    while True:
+        _, fn = units[done % len(units)]
+        t0 = time.perf_counter()
+        u, untimed = fn()
+        dt = time.perf_counter() - t0 - untimed
+        per.append(dt)
+        useful += u
+        t_sum += dt
+        done += 1
+        if t_sum > seconds or (max_units is not None and done >= max_units):
+            break
+    return useful, t_sum, per
+
+
+def run_reference(args, wl_name):
+    """The CPU oracle, as it stands, on bounded samples of the same workload."""
     if args.rank != 0:
         return
-    budget_s = args.ref_seconds
-    per_step = []
-    for _ in range(args.warmup):
-        oracle.fmm(prob.speed, prob.h, prob.sources, prob.src_t)
-    n_solves = 0
-    t_all0 = time.perf_counter()
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        r = oracle.fmm(prob.speed, prob.h, prob.sources, prob.src_t)
-        per_step.append(time.perf_counter() - t0)
-        n_solves += 1
-        if time.perf_counter() - t_all0 > budget_s:
-            break
-    useful_ref = int(np.isfinite(r.t).sum()) - len(np.unique(prob.sources))
-    total = sum(per_step)
-    value = useful_ref * len(per_step) / total
+    units = oracle_units(args)
+    if args.warmup > 0:
+        units[0][1]()
+        if len(units) > 1:
+            units = units[1:] + units[:1]
+    useful, total, per = time_oracle(units, args.ref_seconds, args.steps)
+    value = useful / total
+    sample = (f"{len(per)} steps, each one unit of the workload ({units[0][0]}"
+              f"{' ...' if len(units) > 1 else ''}), stopping after {args.ref_seconds:.0f} s")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": len(per_step), "warmup": args.warmup,
-        "ms_per_step": 1e3 * total / len(per_step), "higher_is_better": True,
+        "n_gpus": args.gpus, "steps": len(per), "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(per), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl_name, "cells": prob.ncells, "sources": int(len(prob.sources))},
+        "config": {"workload": wl_name},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{len(per_step)} full single-threaded FMM solves of the "
-                                   f"workload (stopping after {budget_s:.0f} s)"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(prob, seconds):
-    import oracle
-    oracle.build()
-    times = []
-    t_all = time.perf_counter()
-    r = None
-    while True:
-        t0 = time.perf_counter()
-        r = oracle.fmm(prob.speed, prob.h, prob.sources, prob.src_t)
-        times.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_all > seconds:
-            break
-    useful = int(np.isfinite(r.t).sum()) - len(np.unique(prob.sources))
-    return {"value": useful * len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} full single-threaded FMM solves of the workload "
-                      f"({sum(times):.1f} s of CPU time)", "ms_per_solve": 1e3 * sum(times) / len(times)}
+def cpu_baseline(args):
+    units = oracle_units(args)
+    useful, total, per = time_oracle(units, args.cpu_seconds)
+    return {"value": useful / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{len(per)} single-threaded oracle units of the workload "
+                      f"({units[0][0]}{' ...' if len(units) > 1 else ''}; "
+                      f"{total:.1f} s of CPU time on one host core)",
+            "ms_per_unit": 1e3 * total / len(per)}
+
+
+# --------------------------------------------------------------------------
+# GPU arms
+# --------------------------------------------------------------------------
+
+class Ctx:
+    def __init__(self, args):
+        import torch
+        import paper_2103_05694_gb300 as eik
+        from paper_2103_05694_gb300 import build as eikbuild
+        eikbuild.build()
+        eik.load_library()
+        self.torch, self.eik = torch, eik
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local_rank)
+        self.local_rank = local_rank
+        self.dev = torch.device("cuda", local_rank)
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=self.dev)
+            self.dist = dist
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=self.dev)
+        self.stream = torch.cuda.current_stream(self.dev)
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+        self.torch.cuda.synchronize(self.dev)
+
+    def max_over_ranks(self, x: float) -> float:
+        if self.dist is None:
+            return x
+        t = self.torch.tensor([x], device=self.dev, dtype=self.torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(self, steps: int, step_fn):
+        """Events around each step on the launching stream, L2 flushed between
+        steps outside the events; clocks sampled meanwhile."""
+        torch = self.torch
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        self.barrier()
+        l0 = self.eik.eik_kernel_launches()
+        with ClockSampler(self.local_rank) as clk:
+            for i in range(steps):
+                evs[i][0].record(self.stream)
+                step_fn()
+                evs[i][1].record(self.stream)
+                self.flush.zero_()
+            torch.cuda.synchronize(self.dev)
+        launches = self.eik.eik_kernel_launches() - l0
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        total = self.max_over_ranks(sum(step_ms))
+        self.barrier()
+        return total, step_ms, launches, clk.summary()
+
+
+def time_e2e(C, call, steps):
+    torch = C.torch
+    for _ in range(2):
+        call()
+    torch.cuda.synchronize(C.dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(C.stream)
+    for _ in range(steps):
+        call()
+    e1.record(C.stream)
+    torch.cuda.synchronize(C.dev)
+    return e0.elapsed_time(e1) / steps
+
+
+def roofline(useful_per_launch: int, kern_ms: float, traffic, what: str):
+    peak, kind = measured_peaks()
+    achieved = B_ALG * useful_per_launch / (kern_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": what,
+            "kernel_ms": kern_ms, "bytes_per_launch": B_ALG * useful_per_launch,
+            "peak_kind": f"{kind} copy bandwidth"}
+
+
+def base_line(args, n, wl_name, value, total_ms, extra_cfg):
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict({"workload": wl_name, "parallelism": f"replicas x{n}",
+                        "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)"},
+                       **extra_cfg),
+    }
+
+
+def make_opts(args):
+    opts = {}
+    if args.k_delta > 0:
+        opts["k_delta"] = args.k_delta
+    if args.ctas_per_sm > 0:
+        opts["ctas_per_sm"] = args.ctas_per_sm
+    if args.window > 0:
+        opts["window"] = args.window
+    if args.band > 0:
+        opts["band"] = args.band
+    return opts
+
+
+def run_single(args, C, wl_name):
+    torch, eik = C.torch, C.eik
+    prob = scaled_layered(args.scale) if (args.workload == "layered_2d" and args.scale != 1.0) \
+        else SINGLE[args.workload]()
+    if args.scale != 1.0:
+        wl_name = prob.name + "_scaled"
+    useful = useful_of(prob)
+    opts = make_opts(args)
+    speed = torch.from_numpy(prob.speed).to(C.dev)
+    src = torch.from_numpy(prob.sources).to(C.dev)
+    out = torch.empty_like(speed)
+
+    # correctness gate on the timed configuration: the exact fixed point is reached
+    st = eik.solve(speed, prob.h, src, out=out, opts=dict(opts, counters=1)).stats
+    torch.cuda.synchronize(C.dev)
+    assert st["good"] == useful, (st, useful)
+    ref = out.clone()
+
+    for _ in range(args.warmup):
+        eik.solve(speed, prob.h, src, out=out, opts=opts)
+        C.flush.zero_()
+    solve_ms = []
+
+    def step():
+        solve_ms.append(eik.solve(speed, prob.h, src, out=out, opts=opts).stats["solve_ms"])
+    total_ms, _, launches, clocks = C.timed(args.steps, step)
+    assert torch.equal(out, ref)
+    n = args.gpus
+    value = useful * args.steps * n / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers (copies inside the call)
+    h_speed = torch.from_numpy(prob.speed).pin_memory()
+    h_out = torch.empty(prob.speed.shape, dtype=torch.float64).pin_memory()
+    h_src = prob.sources.copy()
+
+    def e2e_call():
+        eik.eik_solve(h_speed.data_ptr(), prob.h, prob.speed.ndim, prob.speed.shape,
+                      h_src.ctypes.data, None, len(h_src), h_out.data_ptr(), opts or None,
+                      C.stream.cuda_stream)
+    e2e_ms = time_e2e(C, e2e_call, max(3, min(args.steps, 30)))
+    assert np.array_equal(h_out.numpy(), ref.cpu().numpy())
+
+    line = base_line(args, n, wl_name, value, total_ms,
+                     {"cells": prob.ncells, "h": prob.h, "sources": int(len(prob.sources)),
+                      "opts": opts})
+    line["grid_point_updates_per_s"] = st["evals"] * args.steps * n / (total_ms / 1e3)
+    line["work_per_step"] = {k: st[k] for k in ("evals", "decreases", "good", "visits", "pushes",
+                                                "stale_pops", "rounds")}
+    line["roofline"] = roofline(useful, statistics.mean(solve_ms), args.traffic_bytes,
+                                "persistent_kernel (tile relaxation + bucket scheduler)")
+    line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": int(prob.speed.nbytes + h_src.nbytes),
+                   "d2h_bytes_per_step": int(prob.speed.nbytes)}
+    line["gpu_launches"] = int(launches)
+    line["clocks"] = clocks
+    return line
+
+
+def run_batched(args, C, wl_name):
+    torch, eik = C.torch, C.eik
+    probs = synth.batched_3d()
+    useful = sum(useful_of(p) for p in probs)
+    opts = make_opts(args)
+    dev_speed = {}
+    problems = []
+    for p in probs:
+        key = id(p.speed)
+        if key not in dev_speed:
+            dev_speed[key] = torch.from_numpy(p.speed).to(C.dev)
+        sp = dev_speed[key]
+        problems.append({"speed": sp, "h": p.h, "sources": torch.from_numpy(p.sources).to(C.dev),
+                         "out": torch.empty_like(sp)})
+    st = eik.eik_solve_batched(problems, dict(opts, counters=1))
+    torch.cuda.synchronize(C.dev)
+    assert st["good"] == useful, (st["good"], useful)
+    refs = [q["out"].clone() for q in problems]
+
+    # kernel-only duration of the persistent launch (events inside the library)
+    solve_ms = [eik.eik_solve_batched(problems, opts)["solve_ms"] for _ in range(3)]
+
+    plan = eik.Plan([dict(q) for q in problems], opts)
+    side = torch.cuda.Stream(C.dev)
+    side.wait_stream(C.stream)
+    plan.enqueue(side)
+    plan.status(side)
+    graph = torch.cuda.CUDAGraph()
+    l0 = eik.eik_kernel_launches()
+    with torch.cuda.graph(graph, stream=side):
+        plan.enqueue(side)
+    per_replay = eik.eik_kernel_launches() - l0
+    for _ in range(args.warmup):
+        graph.replay()
+        C.flush.zero_()
+    torch.cuda.synchronize(C.dev)
+    total_ms, _, _, clocks = C.timed(args.steps, graph.replay)
+    plan.status(C.stream)                  # raises unless the last replay succeeded
+    for q, r in zip(problems, refs):
+        assert torch.equal(q["out"], r)
+    n = args.gpus
+    value = useful * args.steps * n / (total_ms / 1e3)
+
+    # end to end: each step copies the models from pinned host memory into the
+    # plan's device buffers, replays the plan and copies every field back
+    h_speed = {key: torch.from_numpy(p.speed).pin_memory() for key, p in
+               ((id(p.speed), p) for p in probs)}
+    h_out = [torch.empty(p.speed.shape, dtype=torch.float64).pin_memory() for p in probs]
+
+    def e2e_call():
+        for key, hs in h_speed.items():
+            dev_speed[key].copy_(hs, non_blocking=True)
+        graph.replay()
+        for q, ho in zip(problems, h_out):
+            ho.copy_(q["out"], non_blocking=True)
+    e2e_ms = time_e2e(C, e2e_call, 3)
+    for ho, r in zip(h_out, refs):
+        assert np.array_equal(ho.numpy(), r.cpu().numpy())
+    h2d = sum(t.numel() * 8 for t in h_speed.values())
+    d2h = sum(p.speed.nbytes for p in probs)
+
+    line = base_line(args, n, wl_name, value, total_ms,
+                     {"problems": len(probs), "cells": int(sum(p.ncells for p in probs)),
+                      "distinct_models": len(dev_speed), "captured_graph": True, "opts": opts})
+    line["roofline"] = roofline(useful, statistics.mean(solve_ms), args.traffic_bytes,
+                                "persistent_kernel (all problems in one launch)")
+    line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    line["gpu_launches"] = int(per_replay * args.steps)
+    line["clocks"] = clocks
+    plan.close()
+    return line
+
+
+def run_tomography(args, C, wl_name):
+    torch, eik = C.torch, C.eik
+    cfg = synth.tomography_2d_1024()
+    h = cfg["h"]
+    n_src = len(cfg["sources"])
+    s0 = torch.from_numpy(1.0 / cfg["start"]).to(C.dev)
+    srcs = [torch.tensor([int(i)], device=C.dev) for i in cfg["sources"]]
+    rcv = torch.from_numpy(cfg["receivers"]).to(C.dev)
+    with torch.no_grad():
+        t_obs = eik.eikonal(torch.from_numpy(1.0 / cfg["true"]).to(C.dev), h, srcs) \
+            .reshape(n_src, -1)[:, rcv].contiguous()
+    useful = n_src * (s0.numel() - 1)
+
+    def grad_of(s_dev):
+        s = s_dev.detach().requires_grad_(True)
+        t = eik.eikonal(s, h, srcs)
+        loss = 0.5 * ((t.reshape(n_src, -1)[:, rcv] - t_obs) ** 2).sum()
+        loss.backward()
+        return s.grad, loss.detach()
+
+    g_ref, _ = grad_of(s0)
+    for _ in range(args.warmup):
+        grad_of(s0)
+        C.flush.zero_()
+    torch.cuda.synchronize(C.dev)
+    total_ms, _, launches, clocks = C.timed(args.steps, lambda: grad_of(s0))
+    g_last, _ = grad_of(s0)
+    assert torch.equal(g_last, g_ref)       # the gradient is deterministic
+    n = args.gpus
+    value = useful * args.steps * n / (total_ms / 1e3)
+
+    # the same gradient from per-source solves and adjoints (one problem per call)
+    speed = torch.reciprocal(s0)
+    outs = [torch.empty_like(s0) for _ in srcs]
+    grads = [torch.empty_like(s0) for _ in srcs]
+
+    def per_source():
+        total = torch.zeros_like(s0)
+        for i, src in enumerate(srcs):
+            eik.solve(speed, h, src, out=outs[i])
+            gt = torch.zeros_like(s0)
+            gt.reshape(-1)[rcv] = outs[i].reshape(-1)[rcv] - t_obs[i]
+            eik.eik_adjoint([{"speed": speed, "h": h, "sources": src, "out": outs[i]}], [gt],
+                            [grads[i]])
+            total += grads[i]
+        return total
+    g_ps = per_source()
+    torch.cuda.synchronize(C.dev)
+    assert torch.allclose(g_ps, g_ref, rtol=1e-12, atol=1e-12 * float(g_ref.abs().max()))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, min(args.steps, 3))
+    e0.record(C.stream)
+    for _ in range(reps):
+        per_source()
+    e1.record(C.stream)
+    torch.cuda.synchronize(C.dev)
+    per_source_ms = e0.elapsed_time(e1) / reps
+
+    # kernel-only duration of the batched forward launch
+    probs = [{"speed": speed, "h": h, "sources": src, "out": outs[i]} for i, src in enumerate(srcs)]
+    solve_ms = [eik.eik_solve_batched(probs)["solve_ms"] for _ in range(3)]
+
+    # end to end: slowness from pinned host memory, gradient back to the host
+    h_s = s0.cpu().pin_memory()
+    h_g = torch.empty_like(h_s).pin_memory()
+
+    def e2e_call():
+        g, _ = grad_of(h_s.to(C.dev, non_blocking=True))
+        h_g.copy_(g, non_blocking=True)
+    e2e_ms = time_e2e(C, e2e_call, max(3, min(args.steps, 10)))
+    assert torch.equal(h_g, g_ref.cpu())
+
+    line = base_line(args, n, wl_name, value, total_ms,
+                     {"cells": int(s0.numel()), "h": h, "sources": n_src,
+                      "receivers": int(rcv.numel()), "step": "batched forward + adjoint + misfit"})
+    line["tomography"] = {"batched_step_ms": total_ms / args.steps,
+                          "per_source_step_ms": per_source_ms,
+                          "speedup_vs_per_source": per_source_ms / (total_ms / args.steps)}
+    line["roofline"] = roofline(useful, statistics.mean(solve_ms), args.traffic_bytes,
+                                "persistent_kernel (32-source forward)")
+    line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": int(h_s.numel() * 8),
+                   "d2h_bytes_per_step": int(h_g.numel() * 8)}
+    line["gpu_launches"] = int(launches)
+    line["clocks"] = clocks
+    return line
 
 
 def main():
@@ -177,11 +570,13 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="2", choices=sorted(workloads()))
+    ap.add_argument("--workload", default="layered_2d", choices=sorted(WORKLOADS))
     ap.add_argument("--scale", type=float, default=1.0,
-                    help="config 2 only: fraction of the extent per axis (profiling)")
+                    help="layered_2d only: fraction of the extent per axis (profiling)")
     ap.add_argument("--k-delta", type=float, default=0.0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--window", type=int, default=0)
+    ap.add_argument("--band", type=float, default=0.0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -190,135 +585,27 @@ def main():
     args = ap.parse_args()
     args.rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if world != args.gpus and world > 1:
+    if world > 1:
         args.gpus = world
-
-    wl_name, make = workloads()[args.config]
-    if args.config == "2" and args.scale != 1.0:
-        prob = scaled_layered(args.scale)
-        wl_name = prob.name + " (config 2 scaled)"
-    else:
-        prob = make()
-    useful = prob.ncells - len(np.unique(prob.sources))   # every cell is reachable
+    wl_name = WORKLOADS[args.workload]
 
     if args.impl == "reference":
-        run_reference(args, wl_name, prob, useful)
+        run_reference(args, wl_name)
         return
 
-    import torch
-    import paper_2103_05694_gb300 as eik
-    from paper_2103_05694_gb300 import build as eikbuild
-    eikbuild.build()
-    eik.load_library()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-
-    opts = {}
-    if args.k_delta > 0:
-        opts["k_delta"] = args.k_delta
-    if args.ctas_per_sm > 0:
-        opts["ctas_per_sm"] = args.ctas_per_sm
-    speed = torch.from_numpy(prob.speed).to(dev)
-    src = torch.from_numpy(prob.sources).to(dev)
-    out = torch.empty_like(speed)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    # correctness gate on the timed configuration: the exact fixed point
-    st = eik.solve(speed, prob.h, src, out=out, opts=dict(opts, counters=1)).stats
-    torch.cuda.synchronize(dev)
-    assert st["good"] == useful, (st, useful)
-
-    for _ in range(args.warmup):
-        eik.solve(speed, prob.h, src, out=out, opts=opts)
-        flush.zero_()
-    torch.cuda.synchronize(dev)
-
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    solve_ms = []
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local_rank) as clk:
-        for i in range(args.steps):
-            evs[i][0].record(stream)
-            s = eik.solve(speed, prob.h, src, out=out, opts=opts).stats
-            evs[i][1].record(stream)
-            solve_ms.append(s["solve_ms"])
-            flush.zero_()            # L2 flush between timed steps (outside the events)
-        torch.cuda.synchronize(dev)
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    n = args.gpus
-    value = useful * args.steps * n / (total_ms / 1e3)
-    evals_per_step = st["evals"]
-
-    # end to end through the C ABI with host buffers (copies inside the call)
-    h_speed = torch.from_numpy(prob.speed).pin_memory()
-    h_out = torch.empty(prob.speed.shape, dtype=torch.float64).pin_memory()
-    h_src = prob.sources.copy()
-    e2e_steps = max(3, min(args.steps, 30))
-    for _ in range(2):
-        eik.eik_solve(h_speed.data_ptr(), prob.h, prob.speed.ndim, prob.speed.shape,
-                      h_src.ctypes.data, None, len(h_src), h_out.data_ptr(), opts or None,
-                      stream.cuda_stream)
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        eik.eik_solve(h_speed.data_ptr(), prob.h, prob.speed.ndim, prob.speed.shape,
-                      h_src.ctypes.data, None, len(h_src), h_out.data_ptr(), opts or None,
-                      stream.cuda_stream)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    assert np.array_equal(h_out.numpy(), out.cpu().numpy())
-    e2e_value = useful * n / (e2e_ms / 1e3)
-
-    peak, peak_kind = measured_peaks()
-    kern_ms = statistics.mean(solve_ms)
-    achieved = B_ALG * useful / (kern_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": args.traffic_bytes,
-            "kernel": "persistent_kernel (tile relaxation + bucket scheduler)",
-            "kernel_ms": kern_ms, "bytes_per_launch": B_ALG * useful,
-            "peak_kind": f"{peak_kind} copy bandwidth"}
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl_name, "cells": prob.ncells, "h": prob.h,
-                   "sources": int(len(prob.sources)), "parallelism": f"replicas x{n}",
-                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MB write)",
-                   "opts": opts},
-        "grid_point_updates_per_s": evals_per_step * args.steps * n / (total_ms / 1e3),
-        "work_per_step": {k: st[k] for k in ("evals", "decreases", "good", "empty", "bad",
-                                             "visits", "pushes", "stale_pops", "rounds")},
-        "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e2e_ms,
-                "h2d_bytes_per_step": int(prob.speed.nbytes + h_src.nbytes),
-                "d2h_bytes_per_step": int(prob.speed.nbytes)},
-        "gpu_launches": 4 * args.steps,
-        "clocks": clk.summary(),
-    }
-    if args.rank == 0 and n == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
+    C = Ctx(args)
+    if args.workload in SINGLE:
+        line = run_single(args, C, wl_name)
+    elif args.workload == "batched_3d":
+        line = run_batched(args, C, wl_name)
+    else:
+        line = run_tomography(args, C, wl_name)
+    if args.rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
     if args.rank == 0:
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    if C.dist is not None:
+        C.dist.destroy_process_group()
 
 
 if __name__ == "__main__":

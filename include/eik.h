@@ -195,8 +195,13 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
  *   (halved where m's two neighbours on that axis tie), downwind neighbours in
  *   the order x-, x+, y-, y+, z-, z+;  dL/ds_n = lambda_n (h^2 s_n) / S_n.
  * Every operation is separately rounded in that order, so results are
- * reproducible bit for bit.  Device pointers only.  stats (optional): good =
- * cells processed, visits = reached cells. */
+ * reproducible bit for bit.  Device pointers only.  Runs one cooperative
+ * launch whose blocks meet at a grid barrier once per dependency level (the
+ * wait is bounded by opts->timeout_ms: EIK_ETIMEOUT).  Workspace: about
+ * 36 bytes per cell of the batch, kept for the next call (eik_release frees
+ * it).  Synchronises `stream`.  stats (optional): good = cells processed,
+ * visits = reached cells, rounds = dependency levels, solve_ms = device time
+ * of the adjoint launches. */
 eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
                        double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,
                        void *stream);
@@ -232,6 +237,12 @@ const char *eik_last_error(void);
 
 /* Version of the ABI (major * 100 + minor). */
 int eik_abi_version(void);
+
+/* Number of CUDA kernels this library has launched, or enqueued into a stream
+ * capture, since it was loaded (all devices, all threads).  A caller that
+ * replays a captured graph counts the kernels captured per enqueue itself.
+ * The paper has no counterpart: it is an instrument for counting device work. */
+uint64_t eik_kernel_launches(void);
 
 #ifdef __cplusplus
 }

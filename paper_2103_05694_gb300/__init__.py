@@ -118,7 +118,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
 
 EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
             "eik_abi_version", "eik_selftest", "eik_solve_noalloc", "eik_plan_create",
-            "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy", "eik_adjoint"]
+            "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy", "eik_adjoint",
+            "eik_kernel_launches"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3", "group2x8", "group3x8",
                    "group2x4"]
@@ -151,6 +152,13 @@ def eik_release() -> None:
 
 def eik_abi_version() -> int:
     return int(load_library().eik_abi_version())
+
+
+def eik_kernel_launches() -> int:
+    """Kernels the library has launched (or enqueued into a capture) so far."""
+    L = load_library()
+    L.eik_kernel_launches.restype = ctypes.c_uint64
+    return int(L.eik_kernel_launches())
 
 
 def _make_opts(opts: dict | None) -> EikOpts | None:

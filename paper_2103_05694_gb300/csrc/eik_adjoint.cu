@@ -12,11 +12,12 @@
 // Every operation is an explicit round-to-nearest intrinsic and the sum order
 // is fixed, so the result equals the CPU oracle's bit for bit.
 //
-// Schedule: asynchronous Kahn order.  cnt[n] = number of downwind cells that
-// use n; cells with cnt 0 are ready.  Persistent warps take ready cells from a
-// device queue, pull lambda from the (final) downwind lambdas, then decrement
-// the counts of their own upwind cells and push the ones that reach zero.
-// No global barrier; every wait is bounded by %globaltimer.
+// Schedule: Kahn order, level by level.  cnt[n] = number of downwind cells
+// that use n; cells with cnt 0 form the first frontier.  One cooperative
+// persistent launch processes a frontier (pull lambda from the final downwind
+// lambdas, decrement the counts of the cell's upwind cells, append those that
+// reach zero to the next frontier), then meets at a grid barrier whose wait is
+// bounded by %globaltimer, and moves to the next frontier.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -26,7 +27,6 @@ namespace eik {
 namespace {
 
 constexpr unsigned long long kInfB = 0x7ff0000000000000ull;
-constexpr unsigned long long kQEmpty = ~0ull;
 constexpr unsigned kFullMask = 0xffffffffu;
 
 __device__ __forceinline__ unsigned long long ubits(double x) {
@@ -87,8 +87,8 @@ __device__ __forceinline__ void neighbours(const AdjProb &P, int64_t n, Nbrs &nb
     const bool hi_in = k < P.ndim && c3[k] + 1 < n3[k];
     nb.idx[2 * k] = lo_in ? n - st[k] : -1;
     nb.idx[2 * k + 1] = hi_in ? n + st[k] : -1;
-    nb.t[2 * k] = lo_in ? ld_rlx_d(P.t + n - st[k]) : __longlong_as_double(kInfB);
-    nb.t[2 * k + 1] = hi_in ? ld_rlx_d(P.t + n + st[k]) : __longlong_as_double(kInfB);
+    nb.t[2 * k] = lo_in ? P.t[n - st[k]] : __longlong_as_double(kInfB);
+    nb.t[2 * k + 1] = hi_in ? P.t[n + st[k]] : __longlong_as_double(kInfB);
   }
 }
 
@@ -127,22 +127,31 @@ __global__ void adj_setup_kernel(const AdjProb *probs, int nprob, int64_t total,
   }
 }
 
-__device__ __forceinline__ void push_ready(AdjCtl *ctl, unsigned long long *queue, bool ready,
-                                           unsigned long long entry) {
+__device__ __forceinline__ unsigned ld_acq_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Warp-aggregated append of the lanes' ready entries to a frontier.  All 32
+// lanes of the warp call it.
+__device__ __forceinline__ void append_ready(unsigned long long *count, unsigned long long *front,
+                                             bool ready, unsigned long long entry) {
   const unsigned bal = __ballot_sync(kFullMask, ready);
   if (!bal) return;
   const unsigned lane = threadIdx.x & 31u;
+  const int leader = __ffs(bal) - 1;
   unsigned long long base = 0;
-  if (lane == static_cast<unsigned>(__ffs(bal) - 1)) base = atomicAdd(&ctl->tail, static_cast<unsigned long long>(__popc(bal)));
-  base = __shfl_sync(kFullMask, base, __ffs(bal) - 1);
-  if (ready) {
-    unsigned long long *slot = queue + base + __popc(bal & ((1u << lane) - 1u));
-    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(slot), "l"(entry) : "memory");
-  }
+  if (lane == static_cast<unsigned>(leader)) base = atomicAdd(count, static_cast<unsigned long long>(__popc(bal)));
+  base = __shfl_sync(kFullMask, base, leader);
+  if (ready) front[base + __popc(bal & ((1u << lane) - 1u))] = entry;
 }
 
 __global__ void adj_seed_kernel(const AdjProb *probs, int nprob, int64_t total, AdjCtl *ctl,
-                                unsigned long long *queue) {
+                                unsigned long long *front) {
   const int64_t span = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int64_t base = blockIdx.x * static_cast<int64_t>(blockDim.x); base < total; base += span) {
     const int64_t q = base + threadIdx.x;
@@ -152,56 +161,75 @@ __global__ void adj_seed_kernel(const AdjProb *probs, int nprob, int64_t total, 
       const int64_t n = q - P.base;
       ready = ubits(P.t[n]) < kInfB && P.cnt[n] == 0;
     }
-    push_ready(ctl, queue, ready, static_cast<unsigned long long>(q));
+    append_ready(&ctl->nfront[0], front, ready, static_cast<unsigned long long>(q));
   }
 }
 
-// lambda and dL/ds of one ready cell, then release its upwind cells.
-__device__ void adj_process(const AdjProb &P, int64_t n, AdjCtl *ctl, unsigned long long *queue,
-                            bool live) {
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The wait
+// is bounded: on expiry the status becomes EIK_ETIMEOUT and every block leaves.
+// Returns false when the launch must stop.
+__device__ bool grid_barrier(AdjCtl *ctl, long long timeout_ns) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned gen = ld_acq_u32(&ctl->bar_gen);
+    __threadfence();
+    if (atomicAdd(&ctl->bar_count, 1u) + 1u == gridDim.x) {
+      ctl->bar_count = 0u;
+      __threadfence();
+      st_rel_u32(&ctl->bar_gen, gen + 1u);
+    } else {
+      const long long t0 = gtime();
+      while (ld_acq_u32(&ctl->bar_gen) == gen) {
+        if (ld_acq_u32(&ctl->status) != 0u) break;
+        if (gtime() - t0 > timeout_ns) { atomicCAS(&ctl->status, 0u, kEtimeout); break; }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ld_acq_u32(&ctl->status) == 0u;
+}
+
+// lambda and dL/ds of one ready cell, then release its upwind cells; the ones
+// that become ready are appended to the next frontier.  All 32 lanes call it.
+__device__ void adj_process(const AdjProb &P, int64_t n, AdjCtl *ctl, unsigned long long *count,
+                            unsigned long long *front, bool live) {
   unsigned long long ready_entry[6];
   bool ready[6] = {false, false, false, false, false, false};
   if (live) {
-    const double tn = ld_rlx_d(P.t + n);
+    const double tn = P.t[n];
     Nbrs nb;
     neighbours(P, n, nb);
     double lam = P.g ? P.g[n] : 0.0;
-    // pull: downwind neighbours m for which n holds m's axis minimum (active)
+    // pull: downwind neighbours m for which n holds m's axis minimum (active);
+    // S_m = 0 marks a source or an unreached cell, whose time does not depend on n
     for (int j = 0; j < 2 * P.ndim; ++j) {
       const int64_t m = nb.idx[j];
       if (m < 0) continue;
       const double tm = nb.t[j];
       if (!(ubits(tm) > ubits(tn)) || !(ubits(tm) < kInfB)) continue;
-      if (P.nsrc > 0 && adj_is_source(P, m)) continue;
+      const double Sm = P.S[m];
+      if (!(Sm > 0.0)) continue;
       const int k = j >> 1;
-      // m's two neighbours on axis k: n (on the opposite side) and m's other one
-      const int64_t other = (j & 1) ? m + (m - n) : m - (n - m);   // beyond m, away from n
+      // m's other neighbour on axis k, beyond m, away from n
+      const int64_t other = (j & 1) ? m + (m - n) : m - (n - m);
       const int64_t mx = m % P.nx, myz = m / P.nx, my = myz % P.ny, mz = myz / P.ny;
       const int64_t mc[3] = {mx, my, mz};
       const int64_t mn[3] = {P.nx, P.ny, P.nz};
       const bool other_in = (j & 1) ? (mc[k] + 1 < mn[k]) : (mc[k] > 0);
-      const double to = other_in ? ld_rlx_d(P.t + other) : __longlong_as_double(kInfB);
+      const double to = other_in ? P.t[other] : __longlong_as_double(kInfB);
       if (ubits(to) < ubits(tn)) continue;             // the other neighbour holds the minimum
-      // S_m and the weight
-      Nbrs nm;
-      neighbours(P, m, nm);
-      const double Sm = upwind_sum(nm, tm, P.ndim);
       double w = __ddiv_rn(__dsub_rn(tm, tn), Sm);
       if (ubits(to) == ubits(tn)) w = __dmul_rn(w, 0.5);
-      const double lm = ld_rlx_d(P.lam + m);
+      const double lm = ld_rlx_d(P.lam + m);           // written by another SM
       lam = __dadd_rn(lam, __dmul_rn(lm, w));
     }
     st_rlx_d(P.lam + n, lam);
-    const bool src = P.nsrc > 0 && adj_is_source(P, n);
-    if (!src) {
-      const double Sn = P.S[n];
-      if (Sn > 0.0) {
-        const double s = __ddiv_rn(1.0, P.v[n]);
-        P.grad[n] = __dmul_rn(lam, __ddiv_rn(__dmul_rn(P.hh, s), Sn));
-      }
-    }
-    __threadfence();   // lambda_n before the counts that let upwind cells read it
-    if (!src) {
+    const double Sn = P.S[n];
+    if (Sn > 0.0) {                                    // not a source
+      const double s = __ddiv_rn(1.0, P.v[n]);
+      P.grad[n] = __dmul_rn(lam, __ddiv_rn(__dmul_rn(P.hh, s), Sn));
       for (int k = 0; k < P.ndim; ++k) {
         const unsigned long long lo = ubits(nb.t[2 * k]), hi = ubits(nb.t[2 * k + 1]);
         const unsigned long long ak = lo < hi ? lo : hi;
@@ -216,63 +244,41 @@ __device__ void adj_process(const AdjProb &P, int64_t n, AdjCtl *ctl, unsigned l
         }
       }
     }
-    atomicAdd(&ctl->done, 1ull);
-    __threadfence();   // our decrements (and the lambdas they vouch for) before the pushes
   }
-  for (int j = 0; j < 6; ++j) push_ready(ctl, queue, ready[j], ready[j] ? ready_entry[j] : 0ull);
+  const unsigned nlive = __popc(__ballot_sync(kFullMask, live));
+  if ((threadIdx.x & 31u) == 0 && nlive) atomicAdd(&ctl->done, static_cast<unsigned long long>(nlive));
+  for (int j = 0; j < 6; ++j) append_ready(count, front, ready[j], ready[j] ? ready_entry[j] : 0ull);
 }
 
-__global__ void adj_run_kernel(const AdjProb *probs, int nprob, AdjCtl *ctl,
-                               unsigned long long *queue, long long timeout_ns) {
+__global__ void adj_levels_kernel(const AdjProb *probs, int nprob, int64_t total, AdjCtl *ctl,
+                                  unsigned long long *front, long long timeout_ns) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t warp0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + (threadIdx.x & ~31u);
   const unsigned lane = threadIdx.x & 31u;
-  const unsigned long long reached = ctl->reached;
-  long long idle_since = 0;
-  for (;;) {
-    // lane 0 claims up to 32 entries that have already been pushed (never
-    // beyond the tail: a claimed entry is always being written by a lane that
-    // is not waiting on this warp)
-    unsigned long long base = 0, cnt = 0;
-    int stop = 0;
-    if (lane == 0) {
-      for (;;) {
-        const unsigned long long h = ld_rlx_u64(&ctl->head);
-        if (h >= reached || ctl->status) { stop = 1; break; }
-        const unsigned long long t = ld_rlx_u64(&ctl->tail);
-        if (t > h) {
-          const unsigned long long n = t - h < 32ull ? t - h : 32ull;
-          if (atomicCAS(&ctl->head, h, h + n) == h) { base = h; cnt = n; break; }
-          continue;
-        }
-        const long long now = gtime();
-        if (idle_since == 0) idle_since = now;
-        else if (now - idle_since > timeout_ns) { atomicCAS(&ctl->status, 0u, kEtimeout); stop = 1; break; }
-        __nanosleep(100);
+  for (unsigned long long level = 0;; ++level) {
+    const int cur = static_cast<int>(level % 3ull);
+    const int nxt = static_cast<int>((level + 1ull) % 3ull);
+    const unsigned long long n_cur = ld_rlx_u64(&ctl->nfront[cur]);
+    if (n_cur == 0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->levels = level;
+      return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nfront[(level + 2ull) % 3ull] = 0ull;
+    const unsigned long long *in = front + (level & 1ull) * static_cast<unsigned long long>(total);
+    unsigned long long *out = front + ((level + 1ull) & 1ull) * static_cast<unsigned long long>(total);
+    for (int64_t b = warp0; b < static_cast<int64_t>(n_cur); b += stride) {
+      const int64_t i = b + lane;
+      const bool live = i < static_cast<int64_t>(n_cur);
+      int pi = 0;
+      int64_t n = 0;
+      if (live) {
+        const int64_t e = static_cast<int64_t>(in[i]);
+        pi = find_adj_prob(probs, nprob, e);
+        n = e - probs[pi].base;
       }
-      if (!stop) idle_since = 0;
+      adj_process(probs[pi], n, ctl, &ctl->nfront[nxt], out, live);
     }
-    stop = __shfl_sync(kFullMask, stop, 0);
-    if (stop) return;
-    base = __shfl_sync(kFullMask, base, 0);
-    cnt = __shfl_sync(kFullMask, cnt, 0);
-    const bool mine = lane < cnt;
-    unsigned long long e = kQEmpty;
-    if (mine) {   // the entry's writer is between its tail reservation and its store
-      const long long t0 = gtime();
-      for (;;) {
-        e = ld_rlx_u64(queue + base + lane);
-        if (e != kQEmpty) break;
-        if (gtime() - t0 > timeout_ns) { atomicCAS(&ctl->status, 0u, kEtimeout); break; }
-      }
-    }
-    const bool live = e != kQEmpty;
-    if (live) __threadfence();   // the counts that made this cell ready come first
-    int pi = 0;
-    int64_t n = 0;
-    if (live) {
-      pi = find_adj_prob(probs, nprob, static_cast<int64_t>(e));
-      n = static_cast<int64_t>(e) - probs[pi].base;
-    }
-    adj_process(probs[pi], n, ctl, queue, live);
+    if (!grid_barrier(ctl, timeout_ns)) return;
   }
 }
 
@@ -291,14 +297,27 @@ int sms() {
 }  // namespace
 
 cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, AdjCtl *ctl,
-                           unsigned long long *queue, long long timeout_ns, cudaStream_t stream) {
+                           unsigned long long *front, long long timeout_ns, cudaStream_t stream) {
   int64_t g = (total + 255) / 256;
   if (g > 8 * sms()) g = 8 * sms();
   if (g < 1) g = 1;
   adj_setup_kernel<<<static_cast<int>(g), 256, 0, stream>>>(probs_dev, nprob, total, ctl);
-  adj_seed_kernel<<<static_cast<int>(g), 256, 0, stream>>>(probs_dev, nprob, total, ctl, queue);
-  adj_run_kernel<<<sms() * 4, 256, 0, stream>>>(probs_dev, nprob, ctl, queue, timeout_ns);
-  return cudaGetLastError();
+  adj_seed_kernel<<<static_cast<int>(g), 256, 0, stream>>>(probs_dev, nprob, total, ctl, front);
+  note_launches(2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // co-resident blocks only: the levels meet at a grid barrier
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_levels_kernel, 256, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  int blocks = sms() * per_sm;
+  void *args[] = {const_cast<AdjProb **>(&probs_dev), &nprob, &total, &ctl, &front, &timeout_ns};
+  e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(adj_levels_kernel), dim3(blocks),
+                                  dim3(256), args, 0, stream);
+  note_launches(1);
+  return e;
 }
 
 }  // namespace eik

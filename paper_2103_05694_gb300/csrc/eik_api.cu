@@ -374,7 +374,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     CK(eik::launch_init_c(vsrc, speed_h[j], g_ws.r.p + speed_off[j], speed_n[j], g_ws.ctl.p, stream),
        "init_c launch");
   }
-  for (auto &P : probs) CK(eik::launch_init_t(P.t, P.nx * P.ny * P.nz, stream), "init_t launch");
+  int64_t max_cells = 0;
+  for (auto &P : probs) max_cells = std::max<int64_t>(max_cells, P.nx * P.ny * P.nz);
+  CK(eik::launch_init_t_all(g_ws.probs.p, (int)probs.size(), max_cells, stream), "init_t launch");
 
   SolveParams sp;
   sp.probs = g_ws.probs.p;
@@ -480,7 +482,8 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   }
   if (sp.counters) {
     CK(cudaMemsetAsync(g_ws.count.p, 0, sizeof(unsigned long long), stream), "clear count");
-    CK(eik::launch_count_finite(probs.data(), (int)probs.size(), g_ws.count.p, stream), "count");
+    CK(eik::launch_count_finite_all(g_ws.probs.p, (int)probs.size(), max_cells, g_ws.count.p,
+                                    stream), "count");
     unsigned long long finite = 0;
     CK(cudaMemcpyAsync(&finite, g_ws.count.p, sizeof(finite), cudaMemcpyDeviceToHost, stream),
        "read count");
@@ -552,7 +555,9 @@ const char *eik_status_str(eik_status s) {
 
 const char *eik_last_error(void) { return g_err; }
 
-int eik_abi_version(void) { return 100; }
+int eik_abi_version(void) { return 101; }
+
+uint64_t eik_kernel_launches(void) { return (uint64_t)eik::kernel_launches(); }
 
 }  // extern "C"
 
@@ -569,7 +574,7 @@ struct eik_plan {
   std::vector<const double *> speeds;        // distinct speed arrays
   std::vector<int64_t> speed_off, speed_n;
   std::vector<double> speed_h;
-  int64_t total_tiles = 0, nseeds = 0, total_src = 0;
+  int64_t total_tiles = 0, nseeds = 0, total_src = 0, max_cells = 0;
   DevBuf<double> c;
   DevBuf<unsigned long long> state;
   DevBuf<unsigned char> tile_src;
@@ -649,6 +654,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
     P.ntz = (P.nz + tz - 1) / tz;
     P.tile_base = pl.total_tiles;
     pl.total_tiles += P.ntx * P.nty * P.ntz;
+    pl.max_cells = std::max<int64_t>(pl.max_cells, P.nx * P.ny * P.nz);
     P.c = pl.c.p + pl.speed_off[prob_speed[i]];
     P.t = hp.out;
     P.src_idx = pl.src_idx.p + all_src.size();
@@ -759,7 +765,7 @@ eik_status eik_plan_enqueue(eik_plan *pl, void *stream) {
     CK(eik::launch_init_c(pl->speeds[j], pl->speed_h[j], pl->c.p + pl->speed_off[j], pl->speed_n[j],
                           pl->ctl.p, s), "init_c launch");
   }
-  for (auto &P : pl->probs) CK(eik::launch_init_t(P.t, P.nx * P.ny * P.nz, s), "init_t launch");
+  CK(eik::launch_init_t_all(pl->sp.probs, (int)pl->probs.size(), pl->max_cells, s), "init_t launch");
   CK(eik::launch_seed(pl->sp, pl->seeds.p, pl->nseeds, pl->k_delta, pl->delta_fixed, s), "seed launch");
   CK(eik::launch_persistent(pl->sp, pl->grid, s), "solve launch");
   return EIK_OK;
@@ -772,7 +778,8 @@ eik_status eik_plan_status(eik_plan *pl, eik_stats *stats, void *stream) {
   unsigned long long finite = 0;
   if (stats && pl->sp.counters) {
     CK(cudaMemsetAsync(pl->count.p, 0, sizeof(unsigned long long), s), "clear count");
-    CK(eik::launch_count_finite(pl->probs.data(), (int)pl->probs.size(), pl->count.p, s), "count");
+    CK(eik::launch_count_finite_all(pl->sp.probs, (int)pl->probs.size(), pl->max_cells,
+                                    pl->count.p, s), "count");
     CK(cudaMemcpyAsync(&finite, pl->count.p, sizeof(finite), cudaMemcpyDeviceToHost, s), "read count");
   }
   CK(cudaStreamSynchronize(s), "plan status");
@@ -811,11 +818,12 @@ namespace {
 struct AdjWorkspace {
   DevBuf<int> cnt;
   DevBuf<double> S, lam;
-  DevBuf<unsigned long long> queue;
+  DevBuf<unsigned long long> front;
   DevBuf<eik::AdjProb> probs;
   DevBuf<eik::AdjCtl> ctl;
   DevBuf<int64_t> src;
   eik::AdjCtl *ctl_host = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 AdjWorkspace g_adj;
 
@@ -846,7 +854,7 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
   CK(g_adj.cnt.ensure((size_t)total), "adjoint: alloc counts");
   CK(g_adj.S.ensure((size_t)total), "adjoint: alloc S");
   CK(g_adj.lam.ensure((size_t)total), "adjoint: alloc lambda");
-  CK(g_adj.queue.ensure((size_t)total), "adjoint: alloc queue");
+  CK(g_adj.front.ensure((size_t)total * 2), "adjoint: alloc frontiers");
   CK(g_adj.probs.ensure((size_t)nprob), "adjoint: alloc problems");
   CK(g_adj.ctl.ensure(1), "adjoint: alloc control");
   CK(g_adj.src.ensure((size_t)std::max<int64_t>(total_src, 1)), "adjoint: alloc sources");
@@ -880,12 +888,16 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
   CK(cudaMemcpyAsync(g_adj.probs.p, ap.data(), ap.size() * sizeof(eik::AdjProb),
                      cudaMemcpyHostToDevice, s), "adjoint: upload problems");
   CK(cudaMemsetAsync(g_adj.cnt.p, 0, (size_t)total * sizeof(int), s), "adjoint: clear counts");
-  CK(cudaMemsetAsync(g_adj.queue.p, 0xff, (size_t)total * sizeof(unsigned long long), s),
-     "adjoint: clear queue");
   CK(cudaMemsetAsync(g_adj.ctl.p, 0, sizeof(eik::AdjCtl), s), "adjoint: clear control");
   const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
-  CK(eik::launch_adjoint(g_adj.probs.p, nprob, total, g_adj.ctl.p, g_adj.queue.p,
+  if (!g_adj.ev0) {
+    CK(cudaEventCreate(&g_adj.ev0), "adjoint: event");
+    CK(cudaEventCreate(&g_adj.ev1), "adjoint: event");
+  }
+  CK(cudaEventRecord(g_adj.ev0, s), "adjoint: event record");
+  CK(eik::launch_adjoint(g_adj.probs.p, nprob, total, g_adj.ctl.p, g_adj.front.p,
                          tmo_ms * 1000000ll, s), "adjoint launch");
+  CK(cudaEventRecord(g_adj.ev1, s), "adjoint: event record");
   CK(cudaMemcpyAsync(g_adj.ctl_host, g_adj.ctl.p, sizeof(eik::AdjCtl), cudaMemcpyDeviceToHost, s),
      "adjoint: read status");
   CK(cudaStreamSynchronize(s), "adjoint");
@@ -894,6 +906,9 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
     std::memset(stats, 0, sizeof(*stats));
     stats->good = (int64_t)c.done;
     stats->visits = (int64_t)c.reached;
+    stats->rounds = (int64_t)c.levels;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g_adj.ev0, g_adj.ev1) == cudaSuccess) stats->solve_ms = ms;
   }
   if (c.status == eik::kEtimeout) { set_err("adjoint: device wait timed out"); return EIK_ETIMEOUT; }
   if (c.status != 0) return EIK_ECUDA;

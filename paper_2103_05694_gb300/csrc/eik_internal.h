@@ -104,6 +104,10 @@ constexpr int kTX3 = 16, kTY3 = 4, kTZ3 = 4;       // 3D
 cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
                           cudaStream_t stream);
 cudaError_t launch_init_t(double *t, int64_t n, cudaStream_t stream);
+// t = +inf on every problem of a batch in one launch (dev_probs: device array;
+// max_cells: the largest problem's cell count).
+cudaError_t launch_init_t_all(const Prob *dev_probs, int nprob, int64_t max_cells,
+                              cudaStream_t stream);
 // One source of one problem, flattened over the batch for the seed kernel.
 struct SeedItem {
   int64_t prob;
@@ -118,6 +122,13 @@ cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int npro
 cudaError_t launch_persistent(const SolveParams &p, int grid, cudaStream_t stream);
 cudaError_t launch_count_finite(const Prob *host_probs, int nprob, unsigned long long *out,
                                 cudaStream_t stream);
+// Finite times over every problem of a batch in one launch (adds into *out).
+cudaError_t launch_count_finite_all(const Prob *dev_probs, int nprob, int64_t max_cells,
+                                    unsigned long long *out, cudaStream_t stream);
+// Kernels this library has launched (or enqueued into a stream capture) since
+// it was loaded; every launch wrapper adds its launches.
+void note_launches(unsigned long long n);
+unsigned long long kernel_launches();
 int persistent_blocks_per_sm(int ndim, int arith);
 
 // Adjoint (eik_adjoint.cu).
@@ -137,18 +148,26 @@ struct AdjProb {
   double hh;                // fl(h * h)
 };
 
+// Control block of the adjoint's level-synchronous schedule.  Frontier counts
+// rotate over three slots: level L reads slot L % 3, appends to (L + 1) % 3 and
+// clears (L + 2) % 3.
 struct AdjCtl {
-  unsigned long long reached;
+  unsigned long long reached;        // cells with a finite time
   unsigned long long pad0[15];
-  unsigned long long head;
+  unsigned long long done;           // cells processed
   unsigned long long pad1[15];
-  unsigned long long tail;
-  unsigned long long pad2[15];
-  unsigned long long done;
+  unsigned long long nfront[3];
+  unsigned long long pad2[13];
+  unsigned bar_count;                // grid barrier: arrivals and generation
+  unsigned bar_gen;
+  unsigned pad3[30];
+  unsigned long long levels;
   unsigned status;
 };
 
+// setup (counts, S, zeroed outputs), first frontier, and one cooperative
+// persistent launch over all levels.  `front` holds 2 * total entries.
 cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, AdjCtl *ctl,
-                           unsigned long long *queue, long long timeout_ns, cudaStream_t stream);
+                           unsigned long long *front, long long timeout_ns, cudaStream_t stream);
 
 }  // namespace eik

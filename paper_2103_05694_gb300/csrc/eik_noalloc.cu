@@ -221,6 +221,7 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
     return EIK_ECUDA;
   }
   na::sources_kernel<<<1, na::kSortThreads, 0, s>>>(src_idx, src_t, nsrc, prob, n, base);
+  note_launches(1);
   if (cudaGetLastError() != cudaSuccess) return EIK_ECUDA;
 
   SolveParams sp;

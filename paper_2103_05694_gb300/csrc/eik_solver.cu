@@ -28,6 +28,7 @@
 //    cell is evaluated only when a neighbour changed.
 //  * Every wait is bounded by %globaltimer; on expiry the kernel records
 //    EIK_ETIMEOUT in the control block and returns (no trap).
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -935,14 +936,45 @@ __global__ void reseed_kernel(SolveParams p, int tx_, int ty_, int tz_, int64_t 
     const int64_t lt = g - P.tile_base;
     const int64_t tx = lt % P.ntx, rest = lt / P.ntx;
     const int64_t ty = rest % P.nty, tz = rest / P.nty;
+    // the tile and its one-cell halo: a tile that is still all +inf but borders a
+    // finite cell may have lost the activation its neighbour pushed when the
+    // frontier overflowed, so it is activated too
     unsigned long long best = kInfBits;
-    for (int64_t z = tz * tz_; z < (tz + 1) * tz_ && z < P.nz; ++z)
-      for (int64_t y = ty * ty_; y < (ty + 1) * ty_ && y < P.ny; ++y)
-        for (int64_t x = tx * tx_; x < (tx + 1) * tx_ && x < P.nx; ++x)
+    const int64_t z0 = tz * tz_ > 0 ? tz * tz_ - 1 : 0, z1 = (tz + 1) * tz_ + 1 < P.nz ? (tz + 1) * tz_ + 1 : P.nz;
+    const int64_t y0 = ty * ty_ > 0 ? ty * ty_ - 1 : 0, y1 = (ty + 1) * ty_ + 1 < P.ny ? (ty + 1) * ty_ + 1 : P.ny;
+    const int64_t x0 = tx * tx_ > 0 ? tx * tx_ - 1 : 0, x1 = (tx + 1) * tx_ + 1 < P.nx ? (tx + 1) * tx_ + 1 : P.nx;
+    for (int64_t z = z0; z < z1; ++z)
+      for (int64_t y = y0; y < y1; ++y)
+        for (int64_t x = x0; x < x1; ++x)
           best = umin64(best, bits_of(ld_time(P.t + (z * P.ny + y) * P.nx + x)));
     if (best < kInfBits) activate(p, static_cast<unsigned long long>(g), 1u << kFaceFull,
                                   bucket_of_time(best, inv));
   }
+}
+
+// Batched forms: blockIdx.y selects the problem (first + y), blockIdx.x strides
+// over its cells.
+__global__ void init_t_all_kernel(const Prob *__restrict__ probs, int first) {
+  const Prob &P = probs[first + blockIdx.y];
+  const int64_t n = P.nx * P.ny * P.nz;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    P.t[i] = from_bits(kInfBits);
+  }
+}
+
+__global__ void count_finite_all_kernel(const Prob *__restrict__ probs, int first,
+                                        unsigned long long *out) {
+  const Prob &P = probs[first + blockIdx.y];
+  const int64_t n = P.nx * P.ny * P.nz;
+  unsigned long long cnt = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    cnt += bits_of(P.t[i]) < kInfBits ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
 }
 
 __global__ void count_finite_kernel(const double *__restrict__ t, int64_t n,
@@ -969,6 +1001,8 @@ int num_sms() {
   return g_num_sms;
 }
 
+std::atomic<unsigned long long> g_launches{0};
+
 int grid_for(int64_t n, int per_sm) {
   int64_t g = (n + 255) / 256;
   const int64_t cap = static_cast<int64_t>(num_sms()) * per_sm;
@@ -979,16 +1013,55 @@ int grid_for(int64_t n, int per_sm) {
 
 }  // namespace
 
+void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
+
 cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
                           cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   init_c_kernel<<<grid_for(n, 8), 256, 0, stream>>>(speed, h, c, n, ctl);
+  note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_init_t(double *t, int64_t n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   init_t_kernel<<<grid_for(n, 8), 256, 0, stream>>>(t, n);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// blocks per problem for the batched element-wise kernels: about 8 per SM in
+// total, at least one per problem
+static int per_prob_blocks(int nprob, int64_t max_cells) {
+  int64_t g = (max_cells + 255) / 256;
+  const int64_t share = (static_cast<int64_t>(num_sms()) * 8 + nprob - 1) / nprob;
+  if (g > share) g = share;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+cudaError_t launch_init_t_all(const Prob *dev_probs, int nprob, int64_t max_cells,
+                              cudaStream_t stream) {
+  if (nprob <= 0 || max_cells <= 0) return cudaSuccess;
+  const int gx = per_prob_blocks(nprob, max_cells);
+  for (int first = 0; first < nprob; first += 65535) {
+    const int ny = nprob - first < 65535 ? nprob - first : 65535;
+    init_t_all_kernel<<<dim3(gx, ny), 256, 0, stream>>>(dev_probs, first);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_finite_all(const Prob *dev_probs, int nprob, int64_t max_cells,
+                                    unsigned long long *out, cudaStream_t stream) {
+  if (nprob <= 0 || max_cells <= 0) return cudaSuccess;
+  const int gx = per_prob_blocks(nprob, max_cells);
+  for (int first = 0; first < nprob; first += 65535) {
+    const int ny = nprob - first < 65535 ? nprob - first : 65535;
+    count_finite_all_kernel<<<dim3(gx, ny), 256, 0, stream>>>(dev_probs, first, out);
+    note_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -1003,6 +1076,7 @@ cudaError_t launch_seed(const SolveParams &p, const SeedItem *items, int64_t nit
   tile_dims(p.ndim, tx, ty, tz);
   const int grid = grid_for(nitems > 0 ? nitems : 1, 4);
   seed_kernel<<<grid, 256, 0, stream>>>(p, items, nitems, k_delta, delta_fixed, tx, ty, tz);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -1013,6 +1087,7 @@ cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int npro
   const Prob &last = host_probs[nprob - 1];
   const int64_t total = last.tile_base + last.ntx * last.nty * last.ntz;
   reseed_kernel<<<grid_for(total, 4), 256, 0, stream>>>(p, tx, ty, tz, total);
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -1048,6 +1123,7 @@ cudaError_t launch_persistent(const SolveParams &p, int grid, cudaStream_t strea
     else
       persistent_kernel<2, kTX2, kTY2, 1, kArithFp64><<<grid, kTX2 * kTY2, 0, stream>>>(p);
   }
+  note_launches(1);
   return cudaGetLastError();
 }
 
@@ -1057,6 +1133,7 @@ cudaError_t launch_count_finite(const Prob *host_probs, int nprob, unsigned long
     const Prob &P = host_probs[i];
     const int64_t n = P.nx * P.ny * P.nz;
     count_finite_kernel<<<grid_for(n, 8), 256, 0, stream>>>(P.t, n, out);
+    note_launches(1);
   }
   return cudaGetLastError();
 }

@@ -51,13 +51,13 @@ def _flat(shape, *coords) -> int:
     return int(np.ravel_multi_index(tuple(int(c) for c in coords), shape))
 
 
-def config1() -> Problem:
+def const_2d_129() -> Problem:
     """2D 129 x 129, h = 1/128, constant speed 1, one source at the centre cell."""
     n = 129
     speed = np.ones((n, n), dtype=np.float64)
     src = np.array([_flat((n, n), 64, 64)], dtype=np.int64)
     return Problem("2d_129x129_const", speed, 1.0 / 128.0, src, np.zeros(1),
-                   {"config": 1})
+                   {})
 
 
 def layered_section(nx: int = 2301, nz: int = 751, h: float = 4.0, seed: int = 2,
@@ -95,13 +95,13 @@ def layered_section(nx: int = 2301, nz: int = 751, h: float = 4.0, seed: int = 2
     return np.clip(v, 1500.0, 5500.0)
 
 
-def config2() -> Problem:
+def layered_2d_2301x751() -> Problem:
     """2D layered seismic-like model 2301 (x) x 751 (z), h = 4 m, one surface
     source at x = 4600 m."""
     h = 4.0
     speed = layered_section(2301, 751, h, seed=2)
     src = np.array([_flat(speed.shape, 0, 1150)], dtype=np.int64)
-    return Problem("2d_2301x751_layered", speed, h, src, np.zeros(1), {"config": 2})
+    return Problem("2d_2301x751_layered", speed, h, src, np.zeros(1), {})
 
 
 def smooth_random_volume(n: int, seed: int, vmin: float, vmax: float,
@@ -114,7 +114,7 @@ def smooth_random_volume(n: int, seed: int, vmin: float, vmax: float,
     return vmin + (g - lo) * ((vmax - vmin) / (hi - lo))
 
 
-def config3() -> Problem:
+def checker_3d_256() -> Problem:
     """3D 256^3, h = 10 m, smooth random 1500-4500 m/s with a 16^3-cell 10:1
     checkerboard (slow cells v/10) in the central 128^3 block; source at
     (x, y, z) = (128, 128, 0)."""
@@ -127,26 +127,26 @@ def config3() -> Problem:
     block = v[lo:hi, lo:hi, lo:hi]
     v[lo:hi, lo:hi, lo:hi] = np.where(slow, block / 10.0, block)
     src = np.array([_flat(v.shape, 0, 128, 128)], dtype=np.int64)
-    return Problem("3d_256_checker", v, 10.0, src, np.zeros(1), {"config": 3})
+    return Problem("3d_256_checker", v, 10.0, src, np.zeros(1), {})
 
 
-def config4_shared_model(n: int = 128) -> np.ndarray:
+def smooth_model_3d_128(n: int = 128) -> np.ndarray:
     return smooth_random_volume(n, 4, 1500.0, 4500.0, 8.0)
 
 
-def config4(n_lattice: int = 8, n_grids: int = 24, model_n: int = 128) -> list[Problem]:
+def batched_3d(n_lattice: int = 8, n_grids: int = 24, model_n: int = 128) -> list[Problem]:
     """Batched multi-source work: one solve per source on a lattice of surface
     sources over a shared smooth 128^3 model, plus independent grids of uneven
     size (side uniform in 64..192, own model, 1-4 sources solved together)."""
     h = 10.0
-    model = config4_shared_model(model_n)
+    model = smooth_model_3d_128(model_n)
     probs: list[Problem] = []
     coords = [8 + 16 * i for i in range(n_lattice)]
     for yy in coords:
         for xx in coords:
             src = np.array([_flat(model.shape, 0, yy, xx)], dtype=np.int64)
             probs.append(Problem(f"shared_src_{yy}_{xx}", model, h, src, np.zeros(1),
-                                 {"config": 4, "shared_model": True}))
+                                 {"shared_model": True}))
     for k in range(n_grids):
         rng = np.random.Generator(np.random.PCG64(400 + k))
         side = int(rng.integers(64, 193))
@@ -154,11 +154,11 @@ def config4(n_lattice: int = 8, n_grids: int = 24, model_n: int = 128) -> list[P
         ns = int(rng.integers(1, 5))
         src = np.unique(rng.integers(0, side ** 3, ns)).astype(np.int64)
         probs.append(Problem(f"grid_{k}_{side}", v, h, src, np.zeros(src.size),
-                             {"config": 4, "shared_model": False}))
+                             {"shared_model": False}))
     return probs
 
 
-def config5(n: int = 1024, n_src: int = 32, n_rcv: int = 512, z_c: float | None = None):
+def tomography_2d_1024(n: int = 1024, n_src: int = 32, n_rcv: int = 512, z_c: float | None = None):
     """Tomography pair on a 1024^2 grid, h = 5 m: smooth random background
     2000-4000 m/s (sigma 16 cells); the true model adds a +10 % and a -10 %
     Gaussian anomaly (sigma 60 cells) at 1/3 and 2/3 of the width, centred at

@@ -47,7 +47,7 @@ def test_status_strings_without_gpu(lib):
     assert lib.eik_status_str(0) == b"EIK_OK"
     assert lib.eik_status_str(3) == b"EIK_ECAPACITY"
     lib.eik_abi_version.restype = ctypes.c_int
-    assert lib.eik_abi_version() == 100
+    assert lib.eik_abi_version() == 101
 
 
 def test_struct_layouts_match_header():
@@ -66,3 +66,8 @@ def test_missing_library_fails_loudly(tmp_path):
             eik.load_library(str(tmp_path / "nope.so"))
     finally:
         eik._lib = saved
+
+
+def test_kernel_launch_counter_without_gpu(lib):
+    lib.eik_kernel_launches.restype = ctypes.c_uint64
+    assert lib.eik_kernel_launches() == 0      # nothing launched in this process yet

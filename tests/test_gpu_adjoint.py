@@ -72,7 +72,7 @@ def test_autograd_function_matches_oracle_adjoint():
 def test_adjoint_bit_exact_vs_oracle_tomography_grid():
     """The 1024^2 tomography layout, two surface sources in one batch: forward
     times and the adjoint gradient both equal the oracle's bit for bit."""
-    cfg = synth.config5()
+    cfg = synth.tomography_2d_1024()
     h, rcv = cfg["h"], cfg["receivers"]
     v = 1.0 / (1.0 / cfg["start"])
     speed = torch.from_numpy(v).to(DEV)
@@ -108,7 +108,7 @@ def test_tomography_gradient_central_differences():
     Relative error against max(|g_FD|, 1e-3 max|g|) must be <= 1e-6 (a
     perturbation may flip an upwind choice: at most a few cells may exceed it).
     The four perturbed fields x 32 sources of one cell run as one batch."""
-    cfg = synth.config5()
+    cfg = synth.tomography_2d_1024()
     h = cfg["h"]
     n = cfg["start"].shape[0]
     s_true = torch.from_numpy(1.0 / cfg["true"]).to(DEV)

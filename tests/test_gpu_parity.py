@@ -83,31 +83,31 @@ def test_smooth_media_bit_exact(shape):
     assert st["evals"] >= st["decreases"] >= st["good"] > 0
 
 
-def test_config1_bit_exact_and_closed_form():
-    p = synth.config1()
+def test_const_2d_129_bit_exact_and_closed_form():
+    p = synth.const_2d_129()
     ref = oracle.fmm(p.speed, p.h, p.sources).t
     got, _ = gpu_solve(p)
-    assert_bits_equal(got, ref, "config1")
+    assert_bits_equal(got, ref, "const_2d_129")
     m = 64
     for k in range(-m, m + 1):
         assert got[m, m + k] == abs(k) * p.h and got[m + k, m] == abs(k) * p.h
 
 
 @pytest.mark.parametrize("arith", ARITHS)
-def test_config2_bit_exact(arith):
-    p = synth.config2()
+def test_layered_2d_bit_exact(arith):
+    p = synth.layered_2d_2301x751()
     ref = oracle.fmm(p.speed, p.h, p.sources).t
     got, st = gpu_solve(p, opts={"counters": 1, "arith": arith})
-    assert_bits_equal(got, ref, "config2")
+    assert_bits_equal(got, ref, "layered_2d_2301x751")
     assert st["good"] == p.ncells - 1
 
 
 _C3 = {}
 
 
-def _config3_ref():
+def _checker_3d_ref():
     if not _C3:
-        p = synth.config3()
+        p = synth.checker_3d_256()
         _C3["p"] = p
         _C3["ref"] = oracle.fmm(p.speed, p.h, p.sources).t
     return _C3["p"], _C3["ref"]
@@ -115,10 +115,10 @@ def _config3_ref():
 
 @pytest.mark.slow
 @pytest.mark.parametrize("arith", ARITHS)
-def test_config3_bit_exact(arith):
-    p, ref = _config3_ref()
+def test_checker_3d_bit_exact(arith):
+    p, ref = _checker_3d_ref()
     got, st = gpu_solve(p, opts={"counters": 1, "arith": arith})
-    assert_bits_equal(got, ref, "config3")
+    assert_bits_equal(got, ref, "checker_3d_256")
     assert st["good"] == p.ncells - 1
 
 

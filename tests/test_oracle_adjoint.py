@@ -68,7 +68,7 @@ def test_tomography_shaped_gradient_fourth_order_differences():
     anomalies in the illuminated depth): the oracle gradient of
     L = 1/2 sum (t - t_obs)^2 against the fourth-order central stencil
     (8 D(eps) - D(2 eps)) / (12 eps), D(e) = L(s + e) - L(s - e), eps = 1e-4 s."""
-    cfg = synth.config5(n=256, n_src=2, n_rcv=128)
+    cfg = synth.tomography_2d_1024(n=256, n_src=2, n_rcv=128)
     h, rcv = cfg["h"], cfg["receivers"]
     s0 = 1.0 / cfg["start"]
     v = 1.0 / s0

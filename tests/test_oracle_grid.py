@@ -171,8 +171,8 @@ def test_duplicate_sources_take_the_min():
 
 
 @pytest.mark.slow
-def test_config1_matches_brute_force_sweeps():
-    p = synth.config1()
+def test_const_2d_129_matches_brute_force_sweeps():
+    p = synth.const_2d_129()
     f = oracle.fmm(p.speed, p.h, p.sources)
     s = oracle.sweep(p.speed, p.h, p.sources, mode=1)
     assert np.array_equal(f.t, s.t)

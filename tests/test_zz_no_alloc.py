@@ -35,7 +35,7 @@ def _problems():
     src2 = np.concatenate([p2.sources, p2.sources[:2]])
     t2 = np.concatenate([p2.src_t, [0.0, p2.src_t[1] + 1.0]])
     p3 = synth.random_problem(32, (40, 50, 60), n_src=3, contrast=5.0, smooth_sigma=2.0, h=2.0)
-    p1 = synth.config1()
+    p1 = synth.const_2d_129()
     return [(p2.speed, p2.h, src2, t2), (p3.speed, p3.h, p3.sources, p3.src_t),
             (p1.speed, p1.h, p1.sources, None)]
 
