@@ -341,7 +341,20 @@ def make_opts(args):
         opts["window"] = args.window
     if args.band > 0:
         opts["band"] = args.band
+    if args.tile > 0:
+        opts["tile"] = args.tile
     return opts
+
+
+def autotuned(args, C, problems, opts):
+    """Options from eik_autotune on the timed problems (outside the timed region)."""
+    if not args.autotune:
+        return opts, None
+    t0 = time.perf_counter()
+    best, trials = C.eik.eik_autotune(problems, base=opts or None, repeats=1 if len(problems) > 8 else 2)
+    info = {"trials": len(trials), "seconds": round(time.perf_counter() - t0, 1),
+            "start_ms": trials[0]["ms"], "best_ms": min(t["ms"] for t in trials if t["ms"] > 0)}
+    return best, info
 
 
 def run_single(args, C, wl_name):
@@ -355,6 +368,8 @@ def run_single(args, C, wl_name):
     speed = torch.from_numpy(prob.speed).to(C.dev)
     src = torch.from_numpy(prob.sources).to(C.dev)
     out = torch.empty_like(speed)
+    opts, tune = autotuned(args, C, [{"speed": speed, "h": prob.h, "sources": src, "out": out}],
+                           opts)
 
     # correctness gate on the timed configuration: the exact fixed point is reached
     st = eik.solve(speed, prob.h, src, out=out, opts=dict(opts, counters=1)).stats
@@ -388,7 +403,7 @@ def run_single(args, C, wl_name):
 
     line = base_line(args, n, wl_name, value, total_ms,
                      {"cells": prob.ncells, "h": prob.h, "sources": int(len(prob.sources)),
-                      "opts": opts})
+                      "opts": opts, "autotune": tune})
     line["grid_point_updates_per_s"] = st["evals"] * args.steps * n / (total_ms / 1e3)
     line["work_per_step"] = {k: st[k] for k in ("evals", "decreases", "good", "visits", "pushes",
                                                 "stale_pops", "rounds")}
@@ -416,6 +431,7 @@ def run_batched(args, C, wl_name):
         sp = dev_speed[key]
         problems.append({"speed": sp, "h": p.h, "sources": torch.from_numpy(p.sources).to(C.dev),
                          "out": torch.empty_like(sp)})
+    opts, tune = autotuned(args, C, problems, opts)
     st = eik.eik_solve_batched(problems, dict(opts, counters=1))
     torch.cuda.synchronize(C.dev)
     assert st["good"] == useful, (st["good"], useful)
@@ -465,7 +481,8 @@ def run_batched(args, C, wl_name):
 
     line = base_line(args, n, wl_name, value, total_ms,
                      {"problems": len(probs), "cells": int(sum(p.ncells for p in probs)),
-                      "distinct_models": len(dev_speed), "captured_graph": True, "opts": opts})
+                      "distinct_models": len(dev_speed), "captured_graph": True, "opts": opts,
+                      "autotune": tune})
     line["roofline"] = roofline(useful, statistics.mean(solve_ms), args.traffic_bytes,
                                 "persistent_kernel (all problems in one launch)")
     line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
@@ -577,6 +594,9 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--band", type=float, default=0.0)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the scheduling options with eik_autotune on the workload first")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -88,6 +88,11 @@ typedef struct {
                               {int64 t_claim_ns, t_end_ns; uint32 tile, lowest bucket,
                               rounds, flags}; NULL: no trace */
     int64_t trace_cap;
+    int tile;              /* tile shape, cells x*y(*z), one CTA thread per cell; 0: default.
+                              2D: 0 = 16x16, 1 = 32x8, 2 = 32x4, 3 = 16x8;
+                              3D: 0 = 8x8x4, 1 = 16x4x4, 2 = 32x4x2, 3 = 8x4x4.
+                              Shapes 1-3 need arith 0/1 (EIK_EINVAL otherwise). */
+    int reserved;          /* keep 0 */
 } eik_opts;
 
 /* Work accounting (the paper's good/empty/bad updates, Results section). */
@@ -205,6 +210,31 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
 eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
                        double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,
                        void *stream);
+
+/* One configuration tried by eik_autotune. */
+typedef struct {
+    eik_opts opts;         /* the configuration, with explicit values */
+    double ms;             /* fastest device time of the solve over the repeats; -1 on failure */
+    int status;            /* eik_status of the trial */
+    int reserved;
+} eik_tune_trial;
+
+/* Autotuner (the paper leaves the bucket width Delta open; tile shape,
+ * look-ahead window, acceptance band, CTAs per SM and frontier capacity are
+ * this implementation's).  Solves the batch (device pointers only, as
+ * eik_solve_batched) `repeats` times per configuration (<= 0: 2) and does
+ * coordinate descent from `base` (NULL: defaults) over tile, k_delta (unless
+ * base->delta > 0), window, band and ctas_per_sm, at most two passes; a change
+ * is kept when it saves more than 1 % of the fastest device time.  Then sets
+ * capacity (unless base->capacity > 0) to 4x the deepest bucket slot seen.
+ * Every trial's output must equal the first trial's bit for bit (a digest of
+ * all outputs is compared; the fixed point does not depend on the schedule,
+ * Theorem 1): otherwise EIK_ECUDA.  The outputs hold the solution on return.
+ * best receives the chosen options; trials[0..*ntrials) (optional, up to
+ * max_trials) the configurations tried, in order.  Synchronous. */
+eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *base, int repeats,
+                        eik_opts *best, eik_tune_trial *trials, int max_trials, int *ntrials,
+                        void *stream);
 
 /* Plans: a batch prepared once and solved many times.
  * eik_plan_create checks the problems (device pointers only; all of one ndim),

@@ -34,7 +34,24 @@ class EikOpts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int), ("counters", ctypes.c_int),
                 ("test_stall", ctypes.c_int), ("window", ctypes.c_int),
                 ("band", ctypes.c_double), ("arith", ctypes.c_int), ("sched_flags", ctypes.c_int),
-                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64)]
+                ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
+                ("tile", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+TILE_SHAPES = {2: [(16, 16), (32, 8), (32, 4), (16, 8)],
+               3: [(8, 8, 4), (16, 4, 4), (32, 4, 2), (8, 4, 4)]}
+
+
+TUNED_FIELDS = ("delta", "k_delta", "capacity", "ctas_per_sm", "window", "band", "arith", "tile")
+
+
+def opts_dict(o: EikOpts) -> dict:
+    """The scheduling fields of an EikOpts as a dict (for eik_* calls)."""
+    return {k: getattr(o, k) for k in TUNED_FIELDS}
+
+
+class EikTuneTrial(ctypes.Structure):
+    _fields_ = [("opts", EikOpts), ("ms", ctypes.c_double), ("status", ctypes.c_int),
+                ("reserved", ctypes.c_int)]
 
 
 class EikStats(ctypes.Structure):
@@ -119,7 +136,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
 EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
             "eik_abi_version", "eik_selftest", "eik_solve_noalloc", "eik_plan_create",
             "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy", "eik_adjoint",
-            "eik_kernel_launches"]
+            "eik_kernel_launches", "eik_autotune"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3", "group2x8", "group3x8",
                    "group2x4"]
@@ -317,7 +334,8 @@ def _problem_array(problems: list[dict]):
             arr[i].dims[k] = int(sp.shape[k]) if k < sp.ndim else 1
         arr[i].src_idx = _ptr(p["sources"])
         arr[i].src_t = _ptr(p.get("src_t"))
-        arr[i].nsrc = int(p["sources"].numel())
+        src = p["sources"]
+        arr[i].nsrc = int(src.numel() if hasattr(src, "numel") else np.asarray(src).size)
         arr[i].out_t = _ptr(p["out"])
     return arr
 
@@ -406,6 +424,28 @@ def eik_adjoint(problems: list[dict], dL_dt: list, dL_ds: list, opts: dict | Non
     if rc != EIK_OK:
         raise EikError(rc, eik_last_error())
     return st.as_dict()
+
+
+def eik_autotune(problems: list[dict], base: dict | None = None, repeats: int = 2,
+                 max_trials: int = 128, stream=None) -> tuple[dict, list[dict]]:
+    """Pick tile shape, bucket width, look-ahead, band, CTAs per SM and frontier
+    capacity for this batch by timing it (torch CUDA tensors as in
+    eik_solve_batched).  Returns (options, trials); every trial reproduced the
+    same bits."""
+    L = load_library()
+    arr = _problem_array(problems)
+    best = EikOpts()
+    tr = (EikTuneTrial * max_trials)()
+    nt = ctypes.c_int(0)
+    o = _make_opts(base)
+    rc = L.eik_autotune(arr, len(problems), ctypes.byref(o) if o is not None else None,
+                        int(repeats), ctypes.byref(best), tr, max_trials, ctypes.byref(nt),
+                        _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    trials = [dict(opts_dict(tr[i].opts), ms=tr[i].ms, status=tr[i].status)
+              for i in range(nt.value)]
+    return opts_dict(best), trials
 
 
 def _make_eikonal_fn():

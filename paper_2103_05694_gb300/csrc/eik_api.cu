@@ -36,9 +36,11 @@ constexpr uint64_t kMaxCapEntries = uint64_t(1) << 30;   // whole ring storage l
 // Defaults per dimension (from parameter sweeps on the 2D layered and 3D
 // checkerboard workloads): bucket width in cell travel times, look-ahead
 // window in buckets, in-tile acceptance band, persistent CTAs per SM.
-constexpr double kDefaultKDelta[2] = {8.0, 4.0};
-constexpr int kDefaultWindow = 4;
-constexpr double kDefaultBand[2] = {8.0, 4.0};
+// Defaults per dimension (2D, 3D), from sweeps over the 2D layered, constant
+// and tomography workloads and the 3D checkerboard and batched workloads.
+constexpr double kDefaultKDelta[2] = {16.0, 4.0};
+constexpr int kDefaultWindow[2] = {8, 16};
+constexpr double kDefaultBand[2] = {16.0, 8.0};
 constexpr int kDefaultCtasPerSm[2] = {1, 2};
 constexpr int kMaxRetries = 4;
 
@@ -210,9 +212,29 @@ eik_status check_problem(const double *speed, double h, int ndim, const int64_t 
   return EIK_OK;
 }
 
-void tile_shape(int ndim, int64_t &tx, int64_t &ty, int64_t &tz) {
-  if (ndim == 3) { tx = eik::kTX3; ty = eik::kTY3; tz = eik::kTZ3; }
-  else { tx = eik::kTX2; ty = eik::kTY2; tz = 1; }
+// Tile shape of opts (validated): shape index and cells per axis.
+eik_status tile_shape(const eik_opts *opts, int ndim, int &shape, int64_t &tx, int64_t &ty,
+                      int64_t &tz) {
+  shape = opts ? opts->tile : 0;
+  if (shape < 0 || shape >= eik::kNumTileShapes) {
+    set_err("opts.tile must be in 0..%d", eik::kNumTileShapes - 1);
+    return EIK_EINVAL;
+  }
+  if (shape != 0 && opts->arith == 2) {
+    set_err("integer-pipe arithmetic (arith 2) runs the default tile shape only");
+    return EIK_EINVAL;
+  }
+  const eik::TileShape ts = eik::tile_shape_of(ndim, shape);
+  tx = ts.tx;
+  ty = ts.ty;
+  tz = ts.tz;
+  return EIK_OK;
+}
+
+// Default persistent CTAs per SM: the per-dimension default for 256-cell
+// tiles, scaled up for smaller tiles.
+int default_ctas_per_sm(int di, int64_t tile_cells) {
+  return (int)std::max<int64_t>(1, kDefaultCtasPerSm[di] * 256 / tile_cells);
 }
 
 eik_status ensure_device() {
@@ -242,7 +264,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     if (hp.ndim != ndim) { set_err("all problems of a batch must have the same ndim"); return EIK_EINVAL; }
   }
   int64_t tx, ty, tz;
-  tile_shape(ndim, tx, ty, tz);
+  int shape = 0;
+  st = tile_shape(opts, ndim, shape, tx, ty, tz);
+  if (st != EIK_OK) return st;
   // distinct speed arrays share one r array
   std::vector<const double *> speeds;
   std::vector<int64_t> speed_off, speed_n;
@@ -379,17 +403,19 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   CK(eik::launch_init_t_all(g_ws.probs.p, (int)probs.size(), max_cells, stream), "init_t launch");
 
   SolveParams sp;
+  std::memset(&sp, 0, sizeof(sp));
   sp.probs = g_ws.probs.p;
   sp.nprob = (int)probs.size();
   sp.ndim = ndim;
   sp.state = g_ws.state.p;
   sp.tile_src = g_ws.tile_src.p;
   sp.pend = g_ws.pend.p;
-  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow);
   const int di = ndim == 3 ? 1 : 0;
+  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow[di]);
   sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand[di];
   sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
+  sp.tile_shape = shape;
   sp.trace = opts && opts->trace && opts->trace_cap > 0 ? static_cast<eik::TraceRec *>(opts->trace)
                                                         : nullptr;
   sp.trace_cap = sp.trace ? (unsigned long long)opts->trace_cap : 0ull;
@@ -405,8 +431,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
 
   CK(eik::launch_seed(sp, g_ws.seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
      "seed launch");
-  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : kDefaultCtasPerSm[di];
-  const int occ = eik::persistent_blocks_per_sm(ndim, sp.arith);
+  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm
+                                             : default_ctas_per_sm(di, tx * ty * tz);
+  const int occ = eik::persistent_blocks_per_sm(ndim, sp.arith, shape);
   if (per_sm > occ) per_sm = occ;
   int dev_sms = 0;
   CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g_ws.device), "SM count");
@@ -536,6 +563,172 @@ eik_status eik_solve_batched(const eik_problem *probs, int nprob, const eik_opts
   return run(hps, opts, stats, s);
 }
 
+// Autotuner: coordinate descent over the scheduling parameters, timing the
+// persistent launch of the caller's own batch.  The fixed point does not
+// depend on the schedule (Theorem 1), so every trial must reproduce the first
+// trial's bits; a device digest of all outputs checks that.
+eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *base, int repeats,
+                        eik_opts *best, eik_tune_trial *trials, int max_trials, int *ntrials,
+                        void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ntrials) *ntrials = 0;
+  if (nprob <= 0 || !probs || !best) { set_err("bad autotune arguments"); return EIK_EINVAL; }
+  if (repeats <= 0) repeats = 2;
+  std::vector<HostProblem> hps((size_t)nprob);
+  int64_t max_cells = 0;
+  for (int i = 0; i < nprob; ++i) {
+    const eik_problem &q = probs[i];
+    eik_status st = check_problem(q.speed, q.h, q.ndim, q.dims, q.src_idx, q.src_t, q.nsrc,
+                                  q.out_t, hps[(size_t)i], s);
+    if (st != EIK_OK) return st;
+    if (!hps[(size_t)i].speed_dev || !hps[(size_t)i].out_dev) {
+      set_err("eik_autotune takes device pointers only (problem %d)", i);
+      return EIK_EINVAL;
+    }
+    max_cells = std::max<int64_t>(max_cells, hps[(size_t)i].n);
+  }
+  const int ndim = hps[0].ndim;
+  const int di = ndim == 3 ? 1 : 0;
+  eik_opts cur;
+  std::memset(&cur, 0, sizeof(cur));
+  if (base) cur = *base;
+  cur.counters = 0;
+  cur.test_stall = 0;
+  cur.trace = nullptr;
+  cur.trace_cap = 0;
+  if (cur.k_delta <= 0) cur.k_delta = kDefaultKDelta[di];
+  if (cur.window <= 0) cur.window = kDefaultWindow[di];
+  if (cur.band <= 0) cur.band = kDefaultBand[di];
+  const bool int_arith = cur.arith == 2;
+
+  unsigned long long ref[2] = {0, 0};
+  bool have_ref = false;
+  int n = 0;
+  auto trial = [&](const eik_opts &o, double &ms) -> eik_status {
+    ms = 1e300;
+    eik_status st = EIK_OK;
+    for (int r = 0; r < repeats && st == EIK_OK; ++r) {
+      std::vector<HostProblem> h2 = hps;
+      eik_stats stt;
+      st = run(h2, &o, &stt, s);
+      if (st != EIK_OK) break;
+      ms = std::min(ms, stt.solve_ms);
+      if (r == 0) {
+        unsigned long long dig[2] = {0, 0};
+        CK(g_ws.count.ensure(2), "autotune: digest buffer");
+        CK(cudaMemsetAsync(g_ws.count.p, 0, 2 * sizeof(unsigned long long), s), "autotune: clear");
+        CK(eik::launch_checksum_all(g_ws.probs.p, nprob, max_cells, g_ws.count.p, s), "digest");
+        CK(cudaMemcpyAsync(dig, g_ws.count.p, sizeof(dig), cudaMemcpyDeviceToHost, s), "digest");
+        CK(cudaStreamSynchronize(s), "digest");
+        if (!have_ref) {
+          ref[0] = dig[0];
+          ref[1] = dig[1];
+          have_ref = true;
+        } else if (dig[0] != ref[0] || dig[1] != ref[1]) {
+          set_err("autotune: trial %d (tile %d, k_delta %g, window %d, band %g, ctas/SM %d) "
+                  "changed the result bits", n, o.tile, o.k_delta, o.window, o.band, o.ctas_per_sm);
+          return EIK_ECUDA;
+        }
+      }
+    }
+    if (trials && n < max_trials) {
+      trials[n].opts = o;
+      trials[n].ms = st == EIK_OK ? ms : -1.0;
+      trials[n].status = (int)st;
+      trials[n].reserved = 0;
+    }
+    ++n;
+    return st;
+  };
+
+  double best_ms = 0;
+  eik_status st = trial(cur, best_ms);
+  if (st != EIK_OK) { if (ntrials) *ntrials = std::min(n, max_trials); return st; }
+  static const double kds[] = {1, 2, 4, 8, 16, 32};
+  static const int wins[] = {1, 2, 4, 8, 16};
+  static const double bands[] = {1, 2, 4, 8, 16};
+  constexpr double kGain = 0.01;   // a change must save more than 1 %
+  auto consider = [&](const eik_opts &o) -> eik_status {
+    double ms = 0;
+    eik_status e = trial(o, ms);
+    if (e == EIK_ECUDA) return e;                  // changed bits or a CUDA failure
+    if (e == EIK_OK && ms < best_ms * (1.0 - kGain)) { best_ms = ms; cur = o; }
+    return EIK_OK;
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    const eik_opts start = cur;
+    if (!int_arith) {
+      const int t0 = cur.tile;
+      for (int t = 0; t < eik::kNumTileShapes; ++t) {
+        if (t == t0) continue;
+        eik_opts o = cur;
+        o.tile = t;
+        o.ctas_per_sm = 0;
+        if ((st = consider(o)) != EIK_OK) break;
+      }
+      if (st != EIK_OK) break;
+    }
+    if (cur.delta <= 0) {
+      const double k0 = cur.k_delta;
+      for (double k : kds) {
+        if (k == k0) continue;
+        eik_opts o = cur;
+        o.k_delta = k;
+        if ((st = consider(o)) != EIK_OK) break;
+      }
+      if (st != EIK_OK) break;
+    }
+    {
+      const int w0 = cur.window;
+      for (int w : wins) {
+        if (w == w0) continue;
+        eik_opts o = cur;
+        o.window = w;
+        if ((st = consider(o)) != EIK_OK) break;
+      }
+      if (st != EIK_OK) break;
+    }
+    {
+      const double b0 = cur.band;
+      for (double b : bands) {
+        if (b == b0) continue;
+        eik_opts o = cur;
+        o.band = b;
+        if ((st = consider(o)) != EIK_OK) break;
+      }
+      if (st != EIK_OK) break;
+    }
+    {
+      const int occ = eik::persistent_blocks_per_sm(ndim, int_arith ? eik::kArithInt : eik::kArithFp64,
+                                                    cur.tile);
+      const int c0 = cur.ctas_per_sm;
+      for (int c = 1; c <= occ; ++c) {
+        if (c == c0) continue;
+        eik_opts o = cur;
+        o.ctas_per_sm = c;
+        if ((st = consider(o)) != EIK_OK) break;
+      }
+      if (st != EIK_OK) break;
+    }
+    if (std::memcmp(&start, &cur, sizeof(cur)) == 0) break;   // no change in a whole pass
+  }
+  if (st != EIK_OK) { if (ntrials) *ntrials = std::min(n, max_trials); return st; }
+  // frontier capacity from the deepest slot the chosen schedule reaches
+  if (!base || base->capacity <= 0) {
+    eik_opts o = cur;
+    o.counters = 1;
+    std::vector<HostProblem> h2 = hps;
+    eik_stats stt;
+    st = run(h2, &o, &stt, s);
+    if (st != EIK_OK) { if (ntrials) *ntrials = std::min(n, max_trials); return st; }
+    cur.capacity = (int64_t)next_pow2((uint64_t)std::max<int64_t>(64, 4 * stt.max_queue));
+  }
+  *best = cur;
+  if (ntrials) *ntrials = std::min(n, max_trials);
+  return EIK_OK;
+}
+
 void eik_release(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_ws.release_all();
@@ -555,7 +748,7 @@ const char *eik_status_str(eik_status s) {
 
 const char *eik_last_error(void) { return g_err; }
 
-int eik_abi_version(void) { return 101; }
+int eik_abi_version(void) { return 102; }
 
 uint64_t eik_kernel_launches(void) { return (uint64_t)eik::kernel_launches(); }
 
@@ -611,7 +804,9 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
     if (!hp.speed_dev || !hp.out_dev) { set_err("plans take device pointers only"); return EIK_EINVAL; }
   }
   int64_t tx, ty, tz;
-  tile_shape(pl.ndim, tx, ty, tz);
+  int shape = 0;
+  eik_status tst = tile_shape(opts, pl.ndim, shape, tx, ty, tz);
+  if (tst != EIK_OK) return tst;
   std::vector<int> prob_speed(hps.size());
   int64_t c_total = 0;
   for (size_t i = 0; i < hps.size(); ++i) {
@@ -705,16 +900,18 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   sp.counters = opts ? opts->counters : 0;
   sp.test_stall = 0;
   const int di = pl.ndim == 3 ? 1 : 0;
-  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow);
+  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow[di]);
   sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand[di];
   sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
+  sp.tile_shape = shape;
   sp.trace = nullptr;
   sp.trace_cap = 0;
   pl.k_delta = opts && opts->k_delta > 0 ? opts->k_delta : kDefaultKDelta[di];
   pl.delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
-  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm : kDefaultCtasPerSm[di];
-  const int occ = eik::persistent_blocks_per_sm(pl.ndim, sp.arith);
+  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm
+                                             : default_ctas_per_sm(di, tx * ty * tz);
+  const int occ = eik::persistent_blocks_per_sm(pl.ndim, sp.arith, shape);
   if (per_sm > occ) per_sm = occ;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl.device), "SM count");

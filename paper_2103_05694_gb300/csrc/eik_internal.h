@@ -83,6 +83,7 @@ struct SolveParams {
   double band;                    // in-tile acceptance band, in units of min r / sqrt(D)
   int arith;                      // kArithFp64 or kArithInt
   int gate_pending_only;          // window follows pending entries only, not running tiles
+  int tile_shape;                 // index into tile_shape_of (0: default)
   struct TraceRec *trace;         // optional visit trace (device), NULL when off
   unsigned long long trace_cap;
 };
@@ -93,12 +94,33 @@ struct TraceRec {
   unsigned tile, lo, rounds, flags;   // flags: bit 0 deferred cells, bits 8.. CTA index
 };
 
-constexpr int kPendWords = 8;            // 256 cells per tile / 32
+constexpr int kPendWords = 8;            // pending-mask words per tile (up to 256 cells)
 constexpr int kArithFp64 = 1, kArithInt = 2;   // d-bar on the FP64 unit / on the integer pipes
 
-// Tile shapes (cells): one thread per cell, 256 threads per CTA.
-constexpr int kTX2 = 32, kTY2 = 8;                 // 2D
-constexpr int kTX3 = 16, kTY3 = 4, kTZ3 = 4;       // 3D
+// Tile shapes (cells): one thread per cell.  Shape 0 of each dimension is the
+// default; the others are alternatives (opts.tile) for the autotuner.
+constexpr int kTX2 = 16, kTY2 = 16;                // 2D default
+constexpr int kTX3 = 8, kTY3 = 8, kTZ3 = 4;        // 3D default
+constexpr int kNumTileShapes = 4;
+struct TileShape {
+  int tx, ty, tz;
+};
+__host__ __device__ inline TileShape tile_shape_of(int ndim, int shape) {
+  if (ndim == 3) {
+    switch (shape) {
+      case 1: return TileShape{16, 4, 4};
+      case 2: return TileShape{32, 4, 2};
+      case 3: return TileShape{8, 4, 4};
+      default: return TileShape{kTX3, kTY3, kTZ3};
+    }
+  }
+  switch (shape) {
+    case 1: return TileShape{32, 8, 1};
+    case 2: return TileShape{32, 4, 1};
+    case 3: return TileShape{16, 8, 1};
+    default: return TileShape{kTX2, kTY2, 1};
+  }
+}
 
 // Launch wrappers (eik_solver.cu).  All enqueue on `stream`.
 cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
@@ -125,11 +147,14 @@ cudaError_t launch_count_finite(const Prob *host_probs, int nprob, unsigned long
 // Finite times over every problem of a batch in one launch (adds into *out).
 cudaError_t launch_count_finite_all(const Prob *dev_probs, int nprob, int64_t max_cells,
                                     unsigned long long *out, cudaStream_t stream);
+// 128-bit digest (out[0] sum, out[1] xor; caller zeroes) of all problems' times.
+cudaError_t launch_checksum_all(const Prob *dev_probs, int nprob, int64_t max_cells,
+                               unsigned long long *out, cudaStream_t stream);
 // Kernels this library has launched (or enqueued into a stream capture) since
 // it was loaded; every launch wrapper adds its launches.
 void note_launches(unsigned long long n);
 unsigned long long kernel_launches();
-int persistent_blocks_per_sm(int ndim, int arith);
+int persistent_blocks_per_sm(int ndim, int arith, int tile_shape);
 
 // Adjoint (eik_adjoint.cu).
 struct AdjProb {

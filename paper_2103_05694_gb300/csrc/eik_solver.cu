@@ -9,8 +9,8 @@
 // (Theorem 1).
 //
 // GB300 design:
-//  * Work item = a tile of cells (2D 32x8, 3D 16x4x4), one CTA (256 threads,
-//    one cell per thread) relaxes it in shared memory: tile plus a one-cell
+//  * Work item = a tile of cells (default 2D 16x16, 3D 8x8x4; other shapes by
+//    option), one CTA (one thread per cell) relaxes it in shared memory: tile plus a one-cell
 //    halo staged with coalesced relaxed loads, x-neighbours by warp shuffles,
 //    y/z neighbours from shared memory, rounds of Jacobi relaxation driven by
 //    per-cell change stamps until the tile is locally converged.
@@ -370,9 +370,9 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 // re-queued at their bucket.  Only accepted values are written to memory.
 // ---------------------------------------------------------------------------
 template <int D, int TX, int TY, int TZ, int ARITH>
-__global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams p) {
+__global__ void __launch_bounds__(TX * TY * TZ, 512 / (TX * TY * TZ)) persistent_kernel(SolveParams p) {
   constexpr int NT = TX * TY * TZ;
-  static_assert(NT == 32 * kPendWords, "one pending bit per cell");
+  static_assert(NT % 32 == 0 && NT <= 32 * kPendWords, "whole warps, one pending bit per cell");
   constexpr int HZ = (D == 3) ? 1 : 0;
   constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2 * HZ;
   static_assert(32 % TX == 0 || TX == 32, "a tile row must not straddle warps");
@@ -614,8 +614,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, 2) persistent_kernel(SolveParams
         const int cnt = s_cnt[R & 1u];
         unsigned long long nv = kInfBits;
         bool part = false;
-        if (ARITH == kArithFp64 && cnt <= 64) {
-          const int L = cnt <= 32 ? 8 : 4;
+        if (ARITH == kArithFp64 && cnt * 4 <= NT) {
+          const int L = cnt * 8 <= NT ? 8 : 4;
           if (warp < (cnt * L + 31) / 32) {
             part = true;
             const int g = tid / L;
@@ -977,6 +977,34 @@ __global__ void count_finite_all_kernel(const Prob *__restrict__ probs, int firs
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(out, cnt);
 }
 
+// Order-dependent 64-bit digest of every problem's times (sum of bit patterns
+// times odd per-cell multipliers, and an xor of mixed patterns): equal
+// digests of two solves of the same batch mean identical bits, short of a
+// collision.
+__global__ void checksum_all_kernel(const Prob *__restrict__ probs, int first,
+                                    unsigned long long *out) {
+  const int pi = first + static_cast<int>(blockIdx.y);
+  const Prob &P = probs[pi];
+  const int64_t n = P.nx * P.ny * P.nz;
+  unsigned long long sum = 0, x = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const unsigned long long b = bits_of(P.t[i]);
+    const unsigned long long k = (static_cast<unsigned long long>(pi) << 40) ^ static_cast<unsigned long long>(i);
+    sum += b * (2ull * k + 1ull);
+    x ^= (b + 0x9e3779b97f4a7c15ull * (k + 1ull)) * 0xbf58476d1ce4e5b9ull;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sum += __shfl_xor_sync(kFull, sum, o);
+    x ^= __shfl_xor_sync(kFull, x, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(out, sum);
+    atomicXor(out + 1, x);
+  }
+}
+
 __global__ void count_finite_kernel(const double *__restrict__ t, int64_t n,
                                     unsigned long long *out) {
   unsigned long long cnt = 0;
@@ -1053,6 +1081,18 @@ cudaError_t launch_init_t_all(const Prob *dev_probs, int nprob, int64_t max_cell
   return cudaGetLastError();
 }
 
+cudaError_t launch_checksum_all(const Prob *dev_probs, int nprob, int64_t max_cells,
+                               unsigned long long *out, cudaStream_t stream) {
+  if (nprob <= 0 || max_cells <= 0) return cudaSuccess;
+  const int gx = per_prob_blocks(nprob, max_cells);
+  for (int first = 0; first < nprob; first += 65535) {
+    const int ny = nprob - first < 65535 ? nprob - first : 65535;
+    checksum_all_kernel<<<dim3(gx, ny), 256, 0, stream>>>(dev_probs, first, out);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_count_finite_all(const Prob *dev_probs, int nprob, int64_t max_cells,
                                     unsigned long long *out, cudaStream_t stream) {
   if (nprob <= 0 || max_cells <= 0) return cudaSuccess;
@@ -1065,15 +1105,17 @@ cudaError_t launch_count_finite_all(const Prob *dev_probs, int nprob, int64_t ma
   return cudaGetLastError();
 }
 
-static void tile_dims(int ndim, int &tx, int &ty, int &tz) {
-  if (ndim == 3) { tx = kTX3; ty = kTY3; tz = kTZ3; }
-  else { tx = kTX2; ty = kTY2; tz = 1; }
+static void tile_dims(const SolveParams &p, int &tx, int &ty, int &tz) {
+  const TileShape ts = tile_shape_of(p.ndim, p.tile_shape);
+  tx = ts.tx;
+  ty = ts.ty;
+  tz = ts.tz;
 }
 
 cudaError_t launch_seed(const SolveParams &p, const SeedItem *items, int64_t nitems,
                         double k_delta, double delta_fixed, cudaStream_t stream) {
   int tx, ty, tz;
-  tile_dims(p.ndim, tx, ty, tz);
+  tile_dims(p, tx, ty, tz);
   const int grid = grid_for(nitems > 0 ? nitems : 1, 4);
   seed_kernel<<<grid, 256, 0, stream>>>(p, items, nitems, k_delta, delta_fixed, tx, ty, tz);
   note_launches(1);
@@ -1083,7 +1125,7 @@ cudaError_t launch_seed(const SolveParams &p, const SeedItem *items, int64_t nit
 cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int nprob,
                           cudaStream_t stream) {
   int tx, ty, tz;
-  tile_dims(p.ndim, tx, ty, tz);
+  tile_dims(p, tx, ty, tz);
   const Prob &last = host_probs[nprob - 1];
   const int64_t total = last.tile_base + last.ntx * last.nty * last.ntz;
   reseed_kernel<<<grid_for(total, 4), 256, 0, stream>>>(p, tx, ty, tz, total);
@@ -1091,40 +1133,67 @@ cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int npro
   return cudaGetLastError();
 }
 
-int persistent_blocks_per_sm(int ndim, int arith) {
-  int nb = 0;
-  if (ndim == 3) {
-    if (arith == kArithInt)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, persistent_kernel<3, kTX3, kTY3, kTZ3, kArithInt>, kTX3 * kTY3 * kTZ3, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, persistent_kernel<3, kTX3, kTY3, kTZ3, kArithFp64>, kTX3 * kTY3 * kTZ3, 0);
-  } else {
-    if (arith == kArithInt)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, persistent_kernel<2, kTX2, kTY2, 1, kArithInt>, kTX2 * kTY2, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nb, persistent_kernel<2, kTX2, kTY2, 1, kArithFp64>, kTX2 * kTY2, 0);
+// Launch / occupancy per (dimension, shape, arithmetic).  The integer-pipe
+// arithmetic exists for the default shapes only.
+template <int D, int TX, int TY, int TZ, bool WithInt>
+struct ShapeOps {
+  static int blocks_per_sm(int arith) {
+    int nb = 0;
+    if constexpr (WithInt) {
+      if (arith == kArithInt) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, persistent_kernel<D, TX, TY, TZ, kArithInt>, TX * TY * TZ, 0);
+        return nb;
+      }
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<D, TX, TY, TZ, kArithFp64>,
+                                                  TX * TY * TZ, 0);
+    return nb;
   }
+  static cudaError_t launch(const SolveParams &p, int grid, cudaStream_t stream) {
+    if (p.arith == kArithInt) {
+      if constexpr (WithInt) {
+        persistent_kernel<D, TX, TY, TZ, kArithInt><<<grid, TX * TY * TZ, 0, stream>>>(p);
+        return cudaGetLastError();
+      } else {
+        return cudaErrorInvalidValue;
+      }
+    }
+    persistent_kernel<D, TX, TY, TZ, kArithFp64><<<grid, TX * TY * TZ, 0, stream>>>(p);
+    return cudaGetLastError();
+  }
+};
+
+#define EIK_SHAPE_SWITCH(ndim, shape, CALL)                                   \
+  do {                                                                       \
+    if ((ndim) == 3) {                                                       \
+      switch (shape) {                                                       \
+        case 1: { using S = ShapeOps<3, 16, 4, 4, false>; CALL; } break;     \
+        case 2: { using S = ShapeOps<3, 32, 4, 2, false>; CALL; } break;     \
+        case 3: { using S = ShapeOps<3, 8, 4, 4, false>; CALL; } break;      \
+        default: { using S = ShapeOps<3, kTX3, kTY3, kTZ3, true>; CALL; }    \
+      }                                                                      \
+    } else {                                                                 \
+      switch (shape) {                                                       \
+        case 1: { using S = ShapeOps<2, 32, 8, 1, false>; CALL; } break;     \
+        case 2: { using S = ShapeOps<2, 32, 4, 1, false>; CALL; } break;     \
+        case 3: { using S = ShapeOps<2, 16, 8, 1, false>; CALL; } break;     \
+        default: { using S = ShapeOps<2, kTX2, kTY2, 1, true>; CALL; }       \
+      }                                                                      \
+    }                                                                        \
+  } while (0)
+
+int persistent_blocks_per_sm(int ndim, int arith, int tile_shape) {
+  int nb = 0;
+  EIK_SHAPE_SWITCH(ndim, tile_shape, nb = S::blocks_per_sm(arith));
   return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_persistent(const SolveParams &p, int grid, cudaStream_t stream) {
-  if (p.ndim == 3) {
-    if (p.arith == kArithInt)
-      persistent_kernel<3, kTX3, kTY3, kTZ3, kArithInt><<<grid, kTX3 * kTY3 * kTZ3, 0, stream>>>(p);
-    else
-      persistent_kernel<3, kTX3, kTY3, kTZ3, kArithFp64><<<grid, kTX3 * kTY3 * kTZ3, 0, stream>>>(p);
-  } else {
-    if (p.arith == kArithInt)
-      persistent_kernel<2, kTX2, kTY2, 1, kArithInt><<<grid, kTX2 * kTY2, 0, stream>>>(p);
-    else
-      persistent_kernel<2, kTX2, kTY2, 1, kArithFp64><<<grid, kTX2 * kTY2, 0, stream>>>(p);
-  }
+  cudaError_t e = cudaSuccess;
+  EIK_SHAPE_SWITCH(p.ndim, p.tile_shape, e = S::launch(p, grid, stream));
   note_launches(1);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_count_finite(const Prob *host_probs, int nprob, unsigned long long *out,

@@ -47,12 +47,12 @@ def test_status_strings_without_gpu(lib):
     assert lib.eik_status_str(0) == b"EIK_OK"
     assert lib.eik_status_str(3) == b"EIK_ECAPACITY"
     lib.eik_abi_version.restype = ctypes.c_int
-    assert lib.eik_abi_version() == 101
+    assert lib.eik_abi_version() == 102
 
 
 def test_struct_layouts_match_header():
-    # eik_opts: double, double, int64, int64, 4 x int, double, 2 x int, ptr, int64 -> 80 bytes
-    assert ctypes.sizeof(eik.EikOpts) == 80
+    # eik_opts: double, double, int64, int64, 4 x int, double, 2 x int, ptr, int64, 2 x int
+    assert ctypes.sizeof(eik.EikOpts) == 88
     assert ctypes.sizeof(eik.EikStats) == 23 * 8
     # eik_problem: ptr, double, int(+pad), int64[3], ptr, ptr, int64, ptr
     assert ctypes.sizeof(eik.EikProblem) == 8 + 8 + 8 + 24 + 8 + 8 + 8 + 8
@@ -71,3 +71,8 @@ def test_missing_library_fails_loudly(tmp_path):
 def test_kernel_launch_counter_without_gpu(lib):
     lib.eik_kernel_launches.restype = ctypes.c_uint64
     assert lib.eik_kernel_launches() == 0      # nothing launched in this process yet
+
+
+def test_tune_trial_layout():
+    # eik_tune_trial: eik_opts, double, int, int
+    assert ctypes.sizeof(eik.EikTuneTrial) == 88 + 8 + 4 + 4
