@@ -46,6 +46,10 @@ METRIC = "useful grid-point updates/s and % HBM roofline (bit-exact vs FP64 FMM 
 UNIT = "updates/s"
 B_ALG = 24          # algorithmic bytes per useful update: read c once, read t once, write t once
 L2_FLUSH_BYTES = 512 << 20
+# ncu DRAM bytes (read + write) per launch of the persistent kernel in its default
+# configuration, from the one-pass captures summarised in profiles/ (refresh them
+# whenever the kernel changes)
+MEASURED_TRAFFIC = {"layered_2d": 28116480 + 738304, "checker_3d": 280578304 + 104352512}
 
 WORKLOADS = {
     "layered_2d": "2d_2301x751_layered_h4_1src",
@@ -407,7 +411,10 @@ def run_single(args, C, wl_name):
     line["grid_point_updates_per_s"] = st["evals"] * args.steps * n / (total_ms / 1e3)
     line["work_per_step"] = {k: st[k] for k in ("evals", "decreases", "good", "visits", "pushes",
                                                 "stale_pops", "rounds")}
-    line["roofline"] = roofline(useful, statistics.mean(solve_ms), args.traffic_bytes,
+    traffic = args.traffic_bytes
+    if traffic is None and not opts and args.scale == 1.0:
+        traffic = MEASURED_TRAFFIC.get(args.workload)
+    line["roofline"] = roofline(useful, statistics.mean(solve_ms), traffic,
                                 "persistent_kernel (tile relaxation + bucket scheduler)")
     line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(prob.speed.nbytes + h_src.nbytes),
@@ -497,9 +504,10 @@ def run_tomography(args, C, wl_name):
     torch, eik = C.torch, C.eik
     cfg = synth.tomography_2d_1024()
     h = cfg["h"]
-    n_src = len(cfg["sources"])
+    sources = cfg["sources"][:args.sources] if args.sources > 0 else cfg["sources"]
+    n_src = len(sources)
     s0 = torch.from_numpy(1.0 / cfg["start"]).to(C.dev)
-    srcs = [torch.tensor([int(i)], device=C.dev) for i in cfg["sources"]]
+    srcs = [torch.tensor([int(i)], device=C.dev) for i in sources]
     rcv = torch.from_numpy(cfg["receivers"]).to(C.dev)
     with torch.no_grad():
         t_obs = eik.eikonal(torch.from_numpy(1.0 / cfg["true"]).to(C.dev), h, srcs) \
@@ -590,6 +598,8 @@ def main():
     ap.add_argument("--workload", default="layered_2d", choices=sorted(WORKLOADS))
     ap.add_argument("--scale", type=float, default=1.0,
                     help="layered_2d only: fraction of the extent per axis (profiling)")
+    ap.add_argument("--sources", type=int, default=0,
+                    help="tomography_2d only: use the first N sources (profiling cases)")
     ap.add_argument("--k-delta", type=float, default=0.0)
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--window", type=int, default=0)
@@ -608,6 +618,8 @@ def main():
     if world > 1:
         args.gpus = world
     wl_name = WORKLOADS[args.workload]
+    if args.workload == "tomography_2d" and args.sources > 0:
+        wl_name = wl_name.replace("32src", f"{args.sources}src")
 
     if args.impl == "reference":
         run_reference(args, wl_name)
