@@ -200,13 +200,14 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
  *   (halved where m's two neighbours on that axis tie), downwind neighbours in
  *   the order x-, x+, y-, y+, z-, z+;  dL/ds_n = lambda_n (h^2 s_n) / S_n.
  * Every operation is separately rounded in that order, so results are
- * reproducible bit for bit.  Device pointers only.  Runs one cooperative
- * launch whose blocks meet at a grid barrier once per dependency level (the
- * wait is bounded by opts->timeout_ms: EIK_ETIMEOUT).  Workspace: about
- * 36 bytes per cell of the batch, kept for the next call (eik_release frees
+ * reproducible bit for bit.  Device pointers only.  A parallel set-up pass
+ * evaluates every weight; then one cooperative launch processes the cells in
+ * dependency order, its blocks meeting at a grid barrier between frontiers
+ * (the wait is bounded by opts->timeout_ms: EIK_ETIMEOUT).  Workspace: about
+ * 53 bytes per cell of the batch, kept for the next call (eik_release frees
  * it).  Synchronises `stream`.  stats (optional): good = cells processed,
- * visits = reached cells, rounds = dependency levels, solve_ms = device time
- * of the adjoint launches. */
+ * visits = reached cells, rounds = frontiers, solve_ms = device time of the
+ * adjoint launches. */
 eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
                        double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,
                        void *stream);

@@ -12,12 +12,20 @@
 // Every operation is an explicit round-to-nearest intrinsic and the sum order
 // is fixed, so the result equals the CPU oracle's bit for bit.
 //
-// Schedule: Kahn order, level by level.  cnt[n] = number of downwind cells
-// that use n; cells with cnt 0 form the first frontier.  One cooperative
-// persistent launch processes a frontier (pull lambda from the final downwind
-// lambdas, decrement the counts of the cell's upwind cells, append those that
-// reach zero to the next frontier), then meets at a grid barrier whose wait is
-// bounded by %globaltimer, and moves to the next frontier.
+// Set-up (fully parallel) evaluates everything that does not depend on lambda:
+// per cell m the mask of its upwind sides, the weight of each active axis
+// W_k(m) = fl(fl(t_m - a_k) / S_m) (halved on a tie) and the coefficient
+// fl(fl(h^2 fl(1 / v)) / S), and counts for every cell the downwind cells that
+// use it.  The dependent part is then one multiply-add per downwind neighbour.
+//
+// Schedule: Kahn order, level by level.  Cells with count 0 form the first
+// frontier.  One cooperative persistent launch processes a frontier (each cell
+// pulls lambda from its downwind cells, writes lambda and dL/ds, decrements its
+// upwind cells' counts and appends those that reach zero to the next
+// frontier), then its blocks meet at a grid barrier bounded by %globaltimer.
+// (Letting a thread follow the cells it releases does not pay on this graph:
+// in 2D most cells have two downwind users, so chains merge after about two
+// steps while the few long chains stretch every frontier.)
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -28,6 +36,7 @@ namespace {
 
 constexpr unsigned long long kInfB = 0x7ff0000000000000ull;
 constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kThreads = 1024;   // threads per block of the level kernel
 
 __device__ __forceinline__ unsigned long long ubits(double x) {
   return static_cast<unsigned long long>(__double_as_longlong(x));
@@ -44,6 +53,14 @@ __device__ __forceinline__ unsigned long long ld_rlx_u64(const unsigned long lon
 }
 __device__ __forceinline__ void st_rlx_d(double *p, double v) {
   asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acq_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ long long gtime() {
   long long t;
@@ -71,69 +88,82 @@ __device__ __forceinline__ bool adj_is_source(const AdjProb &P, int64_t n) {
   return false;
 }
 
-struct Nbrs {
-  int64_t idx[6];      // neighbour index per (axis, side), -1 off-grid
-  double t[6];
+// A cell with its coordinates, so that neighbours need no division.
+struct Cell {
+  int64_t n;
+  int64_t c[3];
 };
 
-__device__ __forceinline__ void neighbours(const AdjProb &P, int64_t n, Nbrs &nb) {
-  const int64_t x = n % P.nx, yz = n / P.nx, y = yz % P.ny, z = yz / P.ny;
-  const int64_t c3[3] = {x, y, z};
-  const int64_t n3[3] = {P.nx, P.ny, P.nz};
-  const int64_t st[3] = {1, P.nx, P.nx * P.ny};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const bool lo_in = k < P.ndim && c3[k] > 0;
-    const bool hi_in = k < P.ndim && c3[k] + 1 < n3[k];
-    nb.idx[2 * k] = lo_in ? n - st[k] : -1;
-    nb.idx[2 * k + 1] = hi_in ? n + st[k] : -1;
-    nb.t[2 * k] = lo_in ? P.t[n - st[k]] : __longlong_as_double(kInfB);
-    nb.t[2 * k + 1] = hi_in ? P.t[n + st[k]] : __longlong_as_double(kInfB);
-  }
+__device__ __forceinline__ Cell cell_of(const AdjProb &P, int64_t n) {
+  Cell e;
+  e.n = n;
+  const int64_t yz = n / P.nx;
+  e.c[0] = n - yz * P.nx;
+  e.c[1] = yz % P.ny;
+  e.c[2] = yz / P.ny;
+  return e;
 }
 
-// S_n over the active axes (0 if none), terms summed in axis order.
-__device__ __forceinline__ double upwind_sum(const Nbrs &nb, double tn, int ndim) {
-  double S = 0.0;
-  for (int k = 0; k < ndim; ++k) {
-    const double ak = ubits(nb.t[2 * k]) < ubits(nb.t[2 * k + 1]) ? nb.t[2 * k] : nb.t[2 * k + 1];
-    if (ak < tn) S = __dadd_rn(S, __dsub_rn(tn, ak));
-  }
-  return S;
+// Neighbour of a cell on side j (0..5: x-, x+, y-, y+, z-, z+), -1 off the grid.
+__device__ __forceinline__ int64_t nbr(const AdjProb &P, const Cell &e, int j) {
+  const int k = j >> 1;
+  if (k >= P.ndim) return -1;
+  const int64_t ext = k == 0 ? P.nx : (k == 1 ? P.ny : P.nz);
+  const int64_t st = k == 0 ? 1 : (k == 1 ? P.nx : P.nx * P.ny);
+  if (j & 1) return e.c[k] + 1 < ext ? e.n + st : -1;
+  return e.c[k] > 0 ? e.n - st : -1;
 }
 
-// counts, S, zeroed outputs, number of reached cells
+// Per cell: zeroed lambda, the upwind-side mask, per-axis weights, the gradient
+// coefficient (kept in grad until lambda is known), reached count, and the
+// downwind-use counts of the upwind cells.
 __global__ void adj_setup_kernel(const AdjProb *probs, int nprob, int64_t total, AdjCtl *ctl) {
+  unsigned long long reached = 0;
   for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < total;
        q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const AdjProb &P = probs[find_adj_prob(probs, nprob, q)];
     const int64_t n = q - P.base;
-    P.grad[n] = 0.0;
     P.lam[n] = 0.0;
+    P.grad[n] = 0.0;
+    P.mask[n] = 0;
     const double tn = P.t[n];
-    if (!(ubits(tn) < kInfB)) { P.S[n] = 0.0; continue; }
-    atomicAdd(&ctl->reached, 1ull);
-    if (P.nsrc > 0 && adj_is_source(P, n)) { P.S[n] = 0.0; continue; }
-    Nbrs nb;
-    neighbours(P, n, nb);
-    P.S[n] = upwind_sum(nb, tn, P.ndim);
+    if (!(ubits(tn) < kInfB)) continue;
+    ++reached;
+    if (P.nsrc > 0 && adj_is_source(P, n)) continue;
+    const Cell e = cell_of(P, n);
+    unsigned long long lo[3], hi[3], ak[3];
+    double S = 0.0;
     for (int k = 0; k < P.ndim; ++k) {
-      const unsigned long long lo = ubits(nb.t[2 * k]), hi = ubits(nb.t[2 * k + 1]);
-      const unsigned long long ak = lo < hi ? lo : hi;
-      if (!(ak < ubits(tn))) continue;                 // axis not active
-      if (lo == ak) atomicAdd(P.cnt + nb.idx[2 * k], 1);
-      if (hi == ak) atomicAdd(P.cnt + nb.idx[2 * k + 1], 1);
+      const int64_t a = nbr(P, e, 2 * k), b = nbr(P, e, 2 * k + 1);
+      lo[k] = a >= 0 ? ubits(P.t[a]) : kInfB;
+      hi[k] = b >= 0 ? ubits(P.t[b]) : kInfB;
+      ak[k] = lo[k] < hi[k] ? lo[k] : hi[k];
+      if (ak[k] < ubits(tn))
+        S = __dadd_rn(S, __dsub_rn(tn, __longlong_as_double(static_cast<long long>(ak[k]))));
     }
+    if (!(S > 0.0)) continue;   // unreachable for a reached non-source cell
+    unsigned char mask = 0;
+    for (int k = 0; k < P.ndim; ++k) {
+      if (!(ak[k] < ubits(tn))) continue;               // axis not active
+      double w = __ddiv_rn(__dsub_rn(tn, __longlong_as_double(static_cast<long long>(ak[k]))), S);
+      if (lo[k] == hi[k]) w = __dmul_rn(w, 0.5);        // tie: half to each side
+      P.W[k][n] = w;
+      if (lo[k] == ak[k]) {
+        mask |= static_cast<unsigned char>(1u << (2 * k));
+        atomicAdd(P.cnt + nbr(P, e, 2 * k), 1);
+      }
+      if (hi[k] == ak[k]) {
+        mask |= static_cast<unsigned char>(1u << (2 * k + 1));
+        atomicAdd(P.cnt + nbr(P, e, 2 * k + 1), 1);
+      }
+    }
+    P.mask[n] = mask;
+    const double s = __ddiv_rn(1.0, P.v[n]);
+    P.grad[n] = __ddiv_rn(__dmul_rn(P.hh, s), S);
   }
-}
-
-__device__ __forceinline__ unsigned ld_acq_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_rel_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) reached += __shfl_xor_sync(kFullMask, reached, o);
+  if ((threadIdx.x & 31) == 0 && reached) atomicAdd(&ctl->reached, reached);
 }
 
 // Warp-aggregated append of the lanes' ready entries to a frontier.  All 32
@@ -145,7 +175,8 @@ __device__ __forceinline__ void append_ready(unsigned long long *count, unsigned
   const unsigned lane = threadIdx.x & 31u;
   const int leader = __ffs(bal) - 1;
   unsigned long long base = 0;
-  if (lane == static_cast<unsigned>(leader)) base = atomicAdd(count, static_cast<unsigned long long>(__popc(bal)));
+  if (lane == static_cast<unsigned>(leader))
+    base = atomicAdd(count, static_cast<unsigned long long>(__popc(bal)));
   base = __shfl_sync(kFullMask, base, leader);
   if (ready) front[base + __popc(bal & ((1u << lane) - 1u))] = entry;
 }
@@ -193,75 +224,62 @@ __device__ bool grid_barrier(AdjCtl *ctl, long long timeout_ns) {
 
 // lambda and dL/ds of one ready cell, then release its upwind cells; the ones
 // that become ready are appended to the next frontier.  All 32 lanes call it.
-__device__ void adj_process(const AdjProb &P, int64_t n, AdjCtl *ctl, unsigned long long *count,
-                            unsigned long long *front, bool live) {
+__device__ void adj_process(const AdjProb *probs, int nprob, int64_t q, bool live,
+                            unsigned long long *count, unsigned long long *front) {
   unsigned long long ready_entry[6];
   bool ready[6] = {false, false, false, false, false, false};
   if (live) {
-    const double tn = P.t[n];
-    Nbrs nb;
-    neighbours(P, n, nb);
+    const AdjProb &P = probs[find_adj_prob(probs, nprob, q)];
+    const Cell e = cell_of(P, q - P.base);
+    const int64_t n = e.n;
+    int64_t m[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) m[j] = nbr(P, e, j);
+    unsigned mm[6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) mm[j] = m[j] >= 0 ? P.mask[m[j]] : 0u;
     double lam = P.g ? P.g[n] : 0.0;
-    // pull: downwind neighbours m for which n holds m's axis minimum (active);
-    // S_m = 0 marks a source or an unreached cell, whose time does not depend on n
-    for (int j = 0; j < 2 * P.ndim; ++j) {
-      const int64_t m = nb.idx[j];
-      if (m < 0) continue;
-      const double tm = nb.t[j];
-      if (!(ubits(tm) > ubits(tn)) || !(ubits(tm) < kInfB)) continue;
-      const double Sm = P.S[m];
-      if (!(Sm > 0.0)) continue;
-      const int k = j >> 1;
-      // m's other neighbour on axis k, beyond m, away from n
-      const int64_t other = (j & 1) ? m + (m - n) : m - (n - m);
-      const int64_t mx = m % P.nx, myz = m / P.nx, my = myz % P.ny, mz = myz / P.ny;
-      const int64_t mc[3] = {mx, my, mz};
-      const int64_t mn[3] = {P.nx, P.ny, P.nz};
-      const bool other_in = (j & 1) ? (mc[k] + 1 < mn[k]) : (mc[k] > 0);
-      const double to = other_in ? P.t[other] : __longlong_as_double(kInfB);
-      if (ubits(to) < ubits(tn)) continue;             // the other neighbour holds the minimum
-      double w = __ddiv_rn(__dsub_rn(tm, tn), Sm);
-      if (ubits(to) == ubits(tn)) w = __dmul_rn(w, 0.5);
-      const double lm = ld_rlx_d(P.lam + m);           // written by another SM
-      lam = __dadd_rn(lam, __dmul_rn(lm, w));
+    // pull from the downwind neighbours m for which n is an upwind side
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      if (!((mm[j] >> (j ^ 1)) & 1u)) continue;          // n is m's side j^1
+      const double lm = ld_rlx_d(P.lam + m[j]);           // written by another thread
+      lam = __dadd_rn(lam, __dmul_rn(lm, P.W[j >> 1][m[j]]));
     }
     st_rlx_d(P.lam + n, lam);
-    const double Sn = P.S[n];
-    if (Sn > 0.0) {                                    // not a source
-      const double s = __ddiv_rn(1.0, P.v[n]);
-      P.grad[n] = __dmul_rn(lam, __ddiv_rn(__dmul_rn(P.hh, s), Sn));
-      for (int k = 0; k < P.ndim; ++k) {
-        const unsigned long long lo = ubits(nb.t[2 * k]), hi = ubits(nb.t[2 * k + 1]);
-        const unsigned long long ak = lo < hi ? lo : hi;
-        if (!(ak < ubits(tn))) continue;
-        for (int side = 0; side < 2; ++side) {
-          if ((side ? hi : lo) != ak) continue;
-          const int64_t u = nb.idx[2 * k + side];
-          if (atomicSub(P.cnt + u, 1) == 1) {
-            ready[2 * k + side] = true;
-            ready_entry[2 * k + side] = static_cast<unsigned long long>(P.base + u);
-          }
+    const unsigned mk = P.mask[n];
+    if (mk) {                                              // a reached non-source cell
+      P.grad[n] = __dmul_rn(lam, P.grad[n]);
+      __threadfence();   // lambda_n before the counts that let upwind cells read it
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        if (!((mk >> j) & 1u)) continue;
+        if (atomicSub(P.cnt + m[j], 1) == 1) {
+          ready[j] = true;
+          ready_entry[j] = static_cast<unsigned long long>(P.base + m[j]);
         }
       }
     }
   }
-  const unsigned nlive = __popc(__ballot_sync(kFullMask, live));
-  if ((threadIdx.x & 31u) == 0 && nlive) atomicAdd(&ctl->done, static_cast<unsigned long long>(nlive));
+#pragma unroll
   for (int j = 0; j < 6; ++j) append_ready(count, front, ready[j], ready[j] ? ready_entry[j] : 0ull);
 }
 
-__global__ void adj_levels_kernel(const AdjProb *probs, int nprob, int64_t total, AdjCtl *ctl,
-                                  unsigned long long *front, long long timeout_ns) {
+__global__ void __launch_bounds__(kThreads) adj_levels_kernel(const AdjProb *probs, int nprob,
+                                                               int64_t total, AdjCtl *ctl,
+                                                               unsigned long long *front,
+                                                               long long timeout_ns) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   const int64_t warp0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + (threadIdx.x & ~31u);
   const unsigned lane = threadIdx.x & 31u;
+  unsigned long long done = 0;
   for (unsigned long long level = 0;; ++level) {
     const int cur = static_cast<int>(level % 3ull);
     const int nxt = static_cast<int>((level + 1ull) % 3ull);
     const unsigned long long n_cur = ld_rlx_u64(&ctl->nfront[cur]);
     if (n_cur == 0) {
       if (blockIdx.x == 0 && threadIdx.x == 0) ctl->levels = level;
-      return;
+      break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->nfront[(level + 2ull) % 3ull] = 0ull;
     const unsigned long long *in = front + (level & 1ull) * static_cast<unsigned long long>(total);
@@ -269,17 +287,15 @@ __global__ void adj_levels_kernel(const AdjProb *probs, int nprob, int64_t total
     for (int64_t b = warp0; b < static_cast<int64_t>(n_cur); b += stride) {
       const int64_t i = b + lane;
       const bool live = i < static_cast<int64_t>(n_cur);
-      int pi = 0;
-      int64_t n = 0;
-      if (live) {
-        const int64_t e = static_cast<int64_t>(in[i]);
-        pi = find_adj_prob(probs, nprob, e);
-        n = e - probs[pi].base;
-      }
-      adj_process(probs[pi], n, ctl, &ctl->nfront[nxt], out, live);
+      adj_process(probs, nprob, live ? static_cast<int64_t>(in[i]) : 0, live, &ctl->nfront[nxt], out);
+      done += live ? 1u : 0u;
     }
-    if (!grid_barrier(ctl, timeout_ns)) return;
+    // the other blocks' decrements and lambdas before the next frontier
+    if (!grid_barrier(ctl, timeout_ns)) break;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(kFullMask, done, o);
+  if (lane == 0 && done) atomicAdd(&ctl->done, done);
 }
 
 int g_sms = 0;
@@ -308,14 +324,14 @@ cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, A
   if (e != cudaSuccess) return e;
   // co-resident blocks only: the levels meet at a grid barrier
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_levels_kernel, 256, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_levels_kernel, kThreads, 0);
   if (e != cudaSuccess) return e;
-  if (per_sm > 4) per_sm = 4;
+  if (per_sm > 2) per_sm = 2;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   int blocks = sms() * per_sm;
   void *args[] = {const_cast<AdjProb **>(&probs_dev), &nprob, &total, &ctl, &front, &timeout_ns};
   e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(adj_levels_kernel), dim3(blocks),
-                                  dim3(256), args, 0, stream);
+                                  dim3(kThreads), args, 0, stream);
   note_launches(1);
   return e;
 }

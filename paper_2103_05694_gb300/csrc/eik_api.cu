@@ -529,6 +529,31 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   return EIK_OK;
 }
 
+struct AdjWorkspace {
+  int device = -1;
+  DevBuf<int> cnt;
+  DevBuf<double> W, lam;
+  DevBuf<unsigned char> mask;
+  DevBuf<unsigned long long> front;
+  DevBuf<eik::AdjProb> probs;
+  DevBuf<eik::AdjCtl> ctl;
+  DevBuf<int64_t> src;
+  eik::AdjCtl *ctl_host = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  void release_all() {
+    cnt.release(); W.release(); lam.release(); mask.release(); front.release();
+    probs.release(); ctl.release(); src.release();
+    if (ctl_host) cudaFreeHost(ctl_host);
+    ctl_host = nullptr;
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    ev0 = ev1 = nullptr;
+    device = -1;
+  }
+};
+AdjWorkspace g_adj;
+
 }  // namespace
 
 extern "C" {
@@ -732,6 +757,7 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
 void eik_release(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_ws.release_all();
+  g_adj.release_all();
 }
 
 const char *eik_status_str(eik_status s) {
@@ -1010,21 +1036,6 @@ void eik_plan_destroy(eik_plan *pl) { delete pl; }
 // ---------------------------------------------------------------------------
 // eik_adjoint: d(loss)/d(slowness) through the fixed points of a batch.
 // ---------------------------------------------------------------------------
-namespace {
-
-struct AdjWorkspace {
-  DevBuf<int> cnt;
-  DevBuf<double> S, lam;
-  DevBuf<unsigned long long> front;
-  DevBuf<eik::AdjProb> probs;
-  DevBuf<eik::AdjCtl> ctl;
-  DevBuf<int64_t> src;
-  eik::AdjCtl *ctl_host = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
-AdjWorkspace g_adj;
-
-}  // namespace
 
 extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
                                   double *const *dL_dslowness, const eik_opts *opts,
@@ -1047,9 +1058,18 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
     total += hps[(size_t)i].n;
     total_src += (int64_t)hps[(size_t)i].src.size();
   }
+  {
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (g_adj.device != dev) {
+      if (g_adj.device >= 0) g_adj.release_all();
+      g_adj.device = dev;
+    }
+  }
   if (!g_adj.ctl_host) CK(cudaMallocHost(&g_adj.ctl_host, sizeof(eik::AdjCtl)), "adjoint: pinned");
   CK(g_adj.cnt.ensure((size_t)total), "adjoint: alloc counts");
-  CK(g_adj.S.ensure((size_t)total), "adjoint: alloc S");
+  CK(g_adj.W.ensure((size_t)total * 3), "adjoint: alloc weights");
+  CK(g_adj.mask.ensure((size_t)total), "adjoint: alloc masks");
   CK(g_adj.lam.ensure((size_t)total), "adjoint: alloc lambda");
   CK(g_adj.front.ensure((size_t)total * 2), "adjoint: alloc frontiers");
   CK(g_adj.probs.ensure((size_t)nprob), "adjoint: alloc problems");
@@ -1066,7 +1086,8 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
     A.g = dL_dt ? dL_dt[i] : nullptr;
     A.grad = dL_dslowness[i];
     A.lam = g_adj.lam.p + base;
-    A.S = g_adj.S.p + base;
+    for (int k = 0; k < 3; ++k) A.W[k] = g_adj.W.p + (size_t)k * (size_t)total + base;
+    A.mask = g_adj.mask.p + base;
     A.cnt = g_adj.cnt.p + base;
     A.src_idx = g_adj.src.p + all_src.size();
     A.nsrc = (int64_t)hp.src.size();

@@ -163,7 +163,8 @@ struct AdjProb {
   const double *g;          // dL/dt (NULL: 0)
   double *grad;             // dL/ds output
   double *lam;              // adjoint variable (workspace)
-  double *S;                // sum of the active upwind differences (workspace)
+  double *W[3];             // per axis: weight of the axis' upwind side(s) (workspace)
+  unsigned char *mask;      // upwind sides (bit 2k + side) of each cell (workspace)
   int *cnt;                 // downwind users not yet processed (workspace)
   const int64_t *src_idx;   // sorted unique sources
   int64_t nsrc;
@@ -190,8 +191,9 @@ struct AdjCtl {
   unsigned status;
 };
 
-// setup (counts, S, zeroed outputs), first frontier, and one cooperative
-// persistent launch over all levels.  `front` holds 2 * total entries.
+// set-up (masks, weights, coefficients, counts), first frontier, and one
+// cooperative persistent launch over the frontiers.  `front` holds 2 * total
+// entries.
 cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, AdjCtl *ctl,
                            unsigned long long *front, long long timeout_ns, cudaStream_t stream);
 
