@@ -92,7 +92,12 @@ typedef struct {
                               2D: 0 = 16x16, 1 = 32x8, 2 = 32x4, 3 = 16x8;
                               3D: 0 = 8x8x4, 1 = 16x4x4, 2 = 32x4x2, 3 = 8x4x4.
                               Shapes 1-3 need arith 0/1 (EIK_EINVAL otherwise). */
-    int reserved;          /* keep 0 */
+    int update;            /* the local update: 0 = d-bar, exactly monotone (section "Achieving
+                              Exact Monotonicity"), the default; for the ablation of the
+                              Mitigation Strategies section, 2D only: 1 = Algorithm 1 with the
+                              classical explicit root d-tilde, 2 = with the rearranged root
+                              d-hat.  1 and 2 are not monotone: their results may depend on the
+                              schedule and are not a fixed point (Table 3). */
 } eik_opts;
 
 /* Work accounting (the paper's good/empty/bad updates, Results section). */
@@ -212,6 +217,25 @@ eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const 
                        double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,
                        void *stream);
 
+/* Update-form ablation (Mitigation Strategies section, Tables 1 and 2): for
+ * i < n, out[i] = one application of Algorithm 1 at a cell of speed v = speed[i]
+ * with axis minima t_h[i], t_v[i] (2D): form 1 = classical root d-tilde,
+ * form 2 = rearranged root d-hat (one-sided min + h/v when |t_h - t_v| >= h/v
+ * or one minimum is +inf), form 0 = d-bar.  +inf when both minima are +inf.
+ * Device pointers only; EIK_EINVAL otherwise.  Synchronises `stream`.  The
+ * paper has no interface of this kind: it exposes the update for testing. */
+eik_status eik_eval_update(int form, const double *speed, double h, const double *t_h,
+                           const double *t_v, int64_t n, double *out, void *stream);
+
+/* The fixed-point residual of Table 3: re-applies the update (form as in
+ * eik_eval_update; 1 and 2: 2D only) at every cell of prob->out_t using the
+ * final values of its neighbours.  *bad = cells whose value changes (sources:
+ * value != their smallest t0), *max_rel = the largest |t - tau| / t over cells
+ * where both are finite and t > 0 (+inf if a changing cell is not), 0 for a
+ * fixed point.  prob: device pointers only.  Synchronises `stream`. */
+eik_status eik_residual(const eik_problem *prob, int form, int64_t *bad, double *max_rel,
+                        void *stream);
+
 /* One configuration tried by eik_autotune. */
 typedef struct {
     eik_opts opts;         /* the configuration, with explicit values */
@@ -232,7 +256,8 @@ typedef struct {
  * all outputs is compared; the fixed point does not depend on the schedule,
  * Theorem 1): otherwise EIK_ECUDA.  The outputs hold the solution on return.
  * best receives the chosen options; trials[0..*ntrials) (optional, up to
- * max_trials) the configurations tried, in order.  Synchronous. */
+ * max_trials) the configurations tried, in order.  base->update must be 0 (the
+ * explicit forms give schedule-dependent bits): EIK_EINVAL.  Synchronous. */
 eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *base, int repeats,
                         eik_opts *best, eik_tune_trial *trials, int max_trials, int *ntrials,
                         void *stream);

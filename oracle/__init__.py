@@ -16,7 +16,10 @@ Functions and the passages they follow:
 * ``sweep`` -- topology-driven solver, Algorithm 4 (mode 0) and the fast sweeping
   method, Algorithm 5 (mode 1).
 * ``relax_order`` -- relaxation in a caller-given order (Theorem 1).
-* ``residual`` -- the fixed-point residual of Table 3.
+* ``residual`` -- the fixed-point residual of Table 3 (d-bar, or in 2D Algorithm 1
+  with the explicit roots d-tilde / d-hat: ``form`` 1 / 2).
+* ``update_form`` -- one application of Algorithm 1 with d-tilde (form 1), d-hat
+  (form 2) or d-bar (form 0) (Mitigation Strategies section).
 * ``adjoint`` -- d(loss)/d(slowness) through the fixed point (not in the paper:
   implicit differentiation of the real-arithmetic local equations).
 """
@@ -80,6 +83,11 @@ def lib():
         L.orc_residual.argtypes = [ctypes.c_int, _p, _p, _d, _p, _p, _i64, _p,
                                    ctypes.POINTER(_d)]
         L.orc_residual.restype = _i64
+        L.orc_residual_form.argtypes = [ctypes.c_int, ctypes.c_int, _p, _p, _d, _p, _p, _i64, _p,
+                                        ctypes.POINTER(_d)]
+        L.orc_residual_form.restype = _i64
+        L.orc_update_form.argtypes = [ctypes.c_int, _d, _d, _d, _d]
+        L.orc_update_form.restype = _d
         L.orc_adjoint.argtypes = [ctypes.c_int, _p, _p, _d, _p, _i64, _p, _p, _p, _p]
         L.orc_adjoint.restype = ctypes.c_int
     return _lib
@@ -168,16 +176,22 @@ def relax_order(speed: np.ndarray, h: float, sources, perm, src_t=None) -> Oracl
     return OracleResult(t, s.as_dict())
 
 
-def residual(speed: np.ndarray, h: float, sources, t: np.ndarray, src_t=None):
+def update_form(form: int, v: float, h: float, tH: float, tV: float) -> float:
+    """Algorithm 1 with root d-tilde (1), d-hat (2) or d-bar (0)."""
+    return lib().orc_update_form(int(form), v, h, tH, tV)
+
+
+def residual(speed: np.ndarray, h: float, sources, t: np.ndarray, src_t=None, form: int = 0):
     """Table 3 residual of a field: (number of cells that are not fixed under the
-    operator, largest relative difference)."""
+    operator, largest relative difference).  ``form`` as in update_form (1, 2:
+    2D only)."""
     speed, dims, src, st = _grid_args(speed, sources, src_t)
     t = np.ascontiguousarray(t, dtype=np.float64)
     if t.shape != speed.shape:
         raise ValueError("shape mismatch")
     mr = _d(0.0)
-    bad = lib().orc_residual(speed.ndim, _ptr(dims), _ptr(speed), h, _ptr(src), _ptr(st),
-                             src.size, _ptr(t), ctypes.byref(mr))
+    bad = lib().orc_residual_form(int(form), speed.ndim, _ptr(dims), _ptr(speed), h, _ptr(src),
+                                  _ptr(st), src.size, _ptr(t), ctypes.byref(mr))
     if bad < 0:
         raise RuntimeError("orc_residual failed")
     return int(bad), float(mr.value)

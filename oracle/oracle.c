@@ -161,6 +161,27 @@ double orc_dbar_bisect(const double *a, int D, double c)
     return bitsd(hi);
 }
 
+/* One application of Algorithm 1 (the Eikonal update operator) with an
+ * explicit root in place of Eq. difference_as_root, for the ablation of the
+ * Mitigation Strategies section (2D): form 1 = d-tilde (the classical root, "no
+ * mitigation"), form 2 = d-hat (the rearranged root).  One-sided when
+ * |tH - tV| >= h/v or one minimum is +inf: min(tH, tV) + h/v.  form 0 = d-bar.
+ * +inf when both minima are +inf. */
+double orc_update_form(int form, double v, double h, double tH, double tV)
+{
+    double r = h / v;
+    if (form == 0) {
+        double a[2] = {tH, tV};
+        return orc_dbar(a, 2, r, r * r);
+    }
+    double lo = tH < tV ? tH : tV;
+    if (lo == ORC_INF) return ORC_INF;
+    if (tH == ORC_INF || tV == ORC_INF) return lo + r;
+    double d = tH - tV;
+    if (fabs(d) >= r) return lo + r;
+    return form == 1 ? orc_dtilde(v, h, tH, tV) : orc_dhat(v, h, tH, tV);
+}
+
 /* ---------------------------------------------------------------------------
  * Grid helpers.
  * ------------------------------------------------------------------------- */
@@ -452,12 +473,16 @@ int orc_relax_order(int ndim, const int64_t *dims, const double *v, double h,
  * relative difference |t - D(n,t)(n)| / t over finite cells to *max_rel and
  * returns the number of cells where the re-applied value differs from t at
  * all (0 for the exact fixed point), plus source cells whose value is not
- * their t0.  Returns -1 on bad arguments.
+ * their t0.  The operator is d-bar (form 0) or, in 2D, Algorithm 1 with the
+ * explicit root d-tilde (form 1) or d-hat (form 2): the residual of a field
+ * computed with that form, as Table 3 measures it.  Returns -1 on bad
+ * arguments.
  * ------------------------------------------------------------------------- */
-int64_t orc_residual(int ndim, const int64_t *dims, const double *v, double h,
-                     const int64_t *src_idx, const double *src_t, int64_t nsrc,
-                     const double *t, double *max_rel)
+int64_t orc_residual_form(int form, int ndim, const int64_t *dims, const double *v, double h,
+                          const int64_t *src_idx, const double *src_t, int64_t nsrc,
+                          const double *t, double *max_rel)
 {
+    if (form != 0 && ndim != 2) return -1;
     orc_grid g;
     if (orc_grid_make(&g, ndim, dims)) return -1;
     unsigned char *is_src = (unsigned char *)calloc((size_t)g.N, 1);
@@ -480,7 +505,7 @@ int64_t orc_residual(int ndim, const int64_t *dims, const double *v, double h,
         double c = r * r;
         double a[3];
         orc_axis_minima(&g, t, i, a);
-        double tau = orc_dbar(a, g.D, r, c);
+        double tau = form == 0 ? orc_dbar(a, g.D, r, c) : orc_update_form(form, v[i], h, a[0], a[1]);
         if (tau != t[i]) {
             bad++;
             if (t[i] < ORC_INF && tau < ORC_INF && t[i] > 0.0) {
@@ -494,6 +519,13 @@ int64_t orc_residual(int ndim, const int64_t *dims, const double *v, double h,
     free(is_src); free(t0);
     if (max_rel) *max_rel = worst;
     return bad;
+}
+
+int64_t orc_residual(int ndim, const int64_t *dims, const double *v, double h,
+                     const int64_t *src_idx, const double *src_t, int64_t nsrc,
+                     const double *t, double *max_rel)
+{
+    return orc_residual_form(0, ndim, dims, v, h, src_idx, src_t, nsrc, t, max_rel);
 }
 
 /* ---------------------------------------------------------------------------

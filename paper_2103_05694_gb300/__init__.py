@@ -35,7 +35,7 @@ class EikOpts(ctypes.Structure):
                 ("test_stall", ctypes.c_int), ("window", ctypes.c_int),
                 ("band", ctypes.c_double), ("arith", ctypes.c_int), ("sched_flags", ctypes.c_int),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
-                ("tile", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("tile", ctypes.c_int), ("update", ctypes.c_int)]
 
 TILE_SHAPES = {2: [(16, 16), (32, 8), (32, 4), (16, 8)],
                3: [(8, 8, 4), (16, 4, 4), (32, 4, 2), (8, 4, 4)]}
@@ -129,6 +129,18 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                               ctypes.POINTER(vp), ctypes.POINTER(EikOpts),
                               ctypes.POINTER(EikStats), vp]
     L.eik_adjoint.restype = ctypes.c_int
+    L.eik_kernel_launches.argtypes = []
+    L.eik_kernel_launches.restype = ctypes.c_uint64
+    L.eik_autotune.argtypes = [ctypes.POINTER(EikProblem), ctypes.c_int, ctypes.POINTER(EikOpts),
+                               ctypes.c_int, ctypes.POINTER(EikOpts),
+                               ctypes.POINTER(EikTuneTrial), ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int), vp]
+    L.eik_autotune.restype = ctypes.c_int
+    L.eik_eval_update.argtypes = [ctypes.c_int, vp, ctypes.c_double, vp, vp, i64, vp, vp]
+    L.eik_eval_update.restype = ctypes.c_int
+    L.eik_residual.argtypes = [ctypes.POINTER(EikProblem), ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), vp]
+    L.eik_residual.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -136,7 +148,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
 EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
             "eik_abi_version", "eik_selftest", "eik_solve_noalloc", "eik_plan_create",
             "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy", "eik_adjoint",
-            "eik_kernel_launches", "eik_autotune"]
+            "eik_kernel_launches", "eik_autotune", "eik_eval_update", "eik_residual"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3", "group2x8", "group3x8",
                    "group2x4"]
@@ -173,9 +185,7 @@ def eik_abi_version() -> int:
 
 def eik_kernel_launches() -> int:
     """Kernels the library has launched (or enqueued into a capture) so far."""
-    L = load_library()
-    L.eik_kernel_launches.restype = ctypes.c_uint64
-    return int(L.eik_kernel_launches())
+    return int(load_library().eik_kernel_launches())
 
 
 def _make_opts(opts: dict | None) -> EikOpts | None:
@@ -446,6 +456,37 @@ def eik_autotune(problems: list[dict], base: dict | None = None, repeats: int = 
     trials = [dict(opts_dict(tr[i].opts), ms=tr[i].ms, status=tr[i].status)
               for i in range(nt.value)]
     return opts_dict(best), trials
+
+
+UPDATE_FORMS = {"dbar": 0, "dtilde": 1, "dhat": 2}
+
+
+def eik_eval_update(form: int, speed, h: float, t_h, t_v, out=None, stream=None):
+    """One application of the update per point (form 0 = d-bar, 1 = d-tilde,
+    2 = d-hat; 2D).  torch CUDA float64 tensors of one shape; returns ``out``."""
+    import torch
+    if out is None:
+        out = torch.empty_like(speed)
+    L = load_library()
+    rc = L.eik_eval_update(int(form), _ptr(speed), float(h), _ptr(t_h), _ptr(t_v),
+                           int(speed.numel()), _ptr(out), _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    return out
+
+
+def eik_residual(problem: dict, form: int = 0, stream=None) -> tuple[int, float]:
+    """Table 3 residual of problem["out"] (device tensors as in eik_solve_batched):
+    (cells not fixed under the update, largest relative change)."""
+    L = load_library()
+    arr = _problem_array([problem])
+    bad = ctypes.c_int64(0)
+    rel = ctypes.c_double(0.0)
+    rc = L.eik_residual(arr, int(form), ctypes.byref(bad), ctypes.byref(rel),
+                        _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    return int(bad.value), float(rel.value)
 
 
 def _make_eikonal_fn():

@@ -231,6 +231,15 @@ eik_status tile_shape(const eik_opts *opts, int ndim, int &shape, int64_t &tx, i
   return EIK_OK;
 }
 
+// Update form of opts (validated): 0 = d-bar; 1 = d-tilde, 2 = d-hat (2D).
+eik_status update_form(const eik_opts *opts, int ndim, int &form) {
+  form = opts ? opts->update : 0;
+  if (form == 0) return EIK_OK;
+  if (form < 0 || form > 2) { set_err("opts.update must be 0, 1 or 2"); return EIK_EINVAL; }
+  if (ndim != 2) { set_err("the explicit update forms (opts.update 1, 2) are 2D only"); return EIK_EINVAL; }
+  return EIK_OK;
+}
+
 // Default persistent CTAs per SM: the per-dimension default for 256-cell
 // tiles, scaled up for smaller tiles.
 int default_ctas_per_sm(int di, int64_t tile_cells) {
@@ -266,6 +275,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   int64_t tx, ty, tz;
   int shape = 0;
   st = tile_shape(opts, ndim, shape, tx, ty, tz);
+  if (st != EIK_OK) return st;
+  int form = 0;
+  st = update_form(opts, ndim, form);
   if (st != EIK_OK) return st;
   // distinct speed arrays share one r array
   std::vector<const double *> speeds;
@@ -395,8 +407,8 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
       vsrc = g_ws.v_stage.p + v_off;
       v_off += speed_n[j];
     }
-    CK(eik::launch_init_c(vsrc, speed_h[j], g_ws.r.p + speed_off[j], speed_n[j], g_ws.ctl.p, stream),
-       "init_c launch");
+    CK(eik::launch_init_c(vsrc, speed_h[j], g_ws.r.p + speed_off[j], speed_n[j], g_ws.ctl.p, stream,
+                          form != 0), "init_c launch");
   }
   int64_t max_cells = 0;
   for (auto &P : probs) max_cells = std::max<int64_t>(max_cells, P.nx * P.ny * P.nz);
@@ -416,6 +428,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
   sp.tile_shape = shape;
+  sp.update = form;
   sp.trace = opts && opts->trace && opts->trace_cap > 0 ? static_cast<eik::TraceRec *>(opts->trace)
                                                         : nullptr;
   sp.trace_cap = sp.trace ? (unsigned long long)opts->trace_cap : 0ull;
@@ -615,6 +628,11 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
   }
   const int ndim = hps[0].ndim;
   const int di = ndim == 3 ? 1 : 0;
+  if (base && base->update != 0) {
+    set_err("eik_autotune needs the exact update (opts.update 0): only then are the bits "
+            "independent of the schedule");
+    return EIK_EINVAL;
+  }
   eik_opts cur;
   std::memset(&cur, 0, sizeof(cur));
   if (base) cur = *base;
@@ -754,6 +772,66 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
   return EIK_OK;
 }
 
+// Update-form ablation: one application of Algorithm 1 (or d-bar) per point.
+eik_status eik_eval_update(int form, const double *speed, double h, const double *t_h,
+                           const double *t_v, int64_t n, double *out, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (form < 0 || form > 2 || n < 0 || !(h > 0.0) || (n > 0 && (!speed || !t_h || !t_v || !out))) {
+    set_err("bad eik_eval_update arguments");
+    return EIK_EINVAL;
+  }
+  if (n == 0) return EIK_OK;
+  if (!is_device_ptr(speed) || !is_device_ptr(t_h) || !is_device_ptr(t_v) || !is_device_ptr(out)) {
+    set_err("eik_eval_update takes device pointers only");
+    return EIK_EINVAL;
+  }
+  CK(eik::launch_eval_update(form, speed, h, t_h, t_v, n, out, s), "eval launch");
+  CK(cudaStreamSynchronize(s), "eval");
+  return EIK_OK;
+}
+
+// The fixed-point residual of Table 3 on the device.
+eik_status eik_residual(const eik_problem *prob, int form, int64_t *bad, double *max_rel,
+                        void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!prob || !bad || !max_rel) { set_err("bad eik_residual arguments"); return EIK_EINVAL; }
+  HostProblem hp;
+  eik_status st = check_problem(prob->speed, prob->h, prob->ndim, prob->dims, prob->src_idx,
+                                prob->src_t, prob->nsrc, prob->out_t, hp, s);
+  if (st != EIK_OK) return st;
+  if (!hp.speed_dev || !hp.out_dev) { set_err("eik_residual takes device pointers only"); return EIK_EINVAL; }
+  eik_opts o;
+  std::memset(&o, 0, sizeof(o));
+  o.update = form;
+  int f = 0;
+  st = update_form(&o, hp.ndim, f);
+  if (st != EIK_OK) return st;
+  st = ensure_device();
+  if (st != EIK_OK) return st;
+  const size_t ns = hp.src.size();
+  CK(g_ws.src_idx.ensure(std::max<size_t>(ns, 1)), "residual: sources");
+  CK(g_ws.src_t.ensure(std::max<size_t>(ns, 1)), "residual: source times");
+  CK(g_ws.count.ensure(2), "residual: result");
+  if (ns) {
+    CK(cudaMemcpyAsync(g_ws.src_idx.p, hp.src.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s),
+       "residual: upload sources");
+    CK(cudaMemcpyAsync(g_ws.src_t.p, hp.t0.data(), ns * sizeof(double), cudaMemcpyHostToDevice, s),
+       "residual: upload source times");
+  }
+  CK(cudaMemsetAsync(g_ws.count.p, 0, 2 * sizeof(unsigned long long), s), "residual: clear");
+  CK(eik::launch_residual(f, hp.ndim, hp.speed, hp.h, hp.out, hp.dims[2], hp.dims[1], hp.dims[0],
+                          g_ws.src_idx.p, g_ws.src_t.p, (int64_t)ns, g_ws.count.p, s),
+     "residual launch");
+  unsigned long long res[2] = {0, 0};
+  CK(cudaMemcpyAsync(res, g_ws.count.p, sizeof(res), cudaMemcpyDeviceToHost, s), "residual: read");
+  CK(cudaStreamSynchronize(s), "residual");
+  *bad = (int64_t)res[0];
+  std::memcpy(max_rel, &res[1], sizeof(double));
+  return EIK_OK;
+}
+
 void eik_release(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_ws.release_all();
@@ -774,7 +852,7 @@ const char *eik_status_str(eik_status s) {
 
 const char *eik_last_error(void) { return g_err; }
 
-int eik_abi_version(void) { return 102; }
+int eik_abi_version(void) { return 103; }
 
 uint64_t eik_kernel_launches(void) { return (uint64_t)eik::kernel_launches(); }
 
@@ -832,6 +910,9 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   int64_t tx, ty, tz;
   int shape = 0;
   eik_status tst = tile_shape(opts, pl.ndim, shape, tx, ty, tz);
+  if (tst != EIK_OK) return tst;
+  int form = 0;
+  tst = update_form(opts, pl.ndim, form);
   if (tst != EIK_OK) return tst;
   std::vector<int> prob_speed(hps.size());
   int64_t c_total = 0;
@@ -931,6 +1012,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
   sp.tile_shape = shape;
+  sp.update = form;
   sp.trace = nullptr;
   sp.trace_cap = 0;
   pl.k_delta = opts && opts->k_delta > 0 ? opts->k_delta : kDefaultKDelta[di];
@@ -986,7 +1068,7 @@ eik_status eik_plan_enqueue(eik_plan *pl, void *stream) {
   CK(cudaMemsetAsync(pl->slots.p, 0xff, pl->slots.n * sizeof(unsigned long long), s), "clear frontier");
   for (size_t j = 0; j < pl->speeds.size(); ++j) {
     CK(eik::launch_init_c(pl->speeds[j], pl->speed_h[j], pl->c.p + pl->speed_off[j], pl->speed_n[j],
-                          pl->ctl.p, s), "init_c launch");
+                          pl->ctl.p, s, pl->sp.update != 0), "init_c launch");
   }
   CK(eik::launch_init_t_all(pl->sp.probs, (int)pl->probs.size(), pl->max_cells, s), "init_t launch");
   CK(eik::launch_seed(pl->sp, pl->seeds.p, pl->nseeds, pl->k_delta, pl->delta_fixed, s), "seed launch");

@@ -84,6 +84,7 @@ struct SolveParams {
   int arith;                      // kArithFp64 or kArithInt
   int gate_pending_only;          // window follows pending entries only, not running tiles
   int tile_shape;                 // index into tile_shape_of (0: default)
+  int update;                     // 0: d-bar; 2D ablation: 1 = d-tilde, 2 = d-hat (c holds r)
   struct TraceRec *trace;         // optional visit trace (device), NULL when off
   unsigned long long trace_cap;
 };
@@ -123,8 +124,9 @@ __host__ __device__ inline TileShape tile_shape_of(int ndim, int shape) {
 }
 
 // Launch wrappers (eik_solver.cu).  All enqueue on `stream`.
+// store_r: write r = fl(h/v) instead of c (the explicit update forms use r).
 cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
-                          cudaStream_t stream);
+                          cudaStream_t stream, int store_r = 0);
 cudaError_t launch_init_t(double *t, int64_t n, cudaStream_t stream);
 // t = +inf on every problem of a batch in one launch (dev_probs: device array;
 // max_cells: the largest problem's cell count).
@@ -155,6 +157,15 @@ cudaError_t launch_checksum_all(const Prob *dev_probs, int nprob, int64_t max_ce
 void note_launches(unsigned long long n);
 unsigned long long kernel_launches();
 int persistent_blocks_per_sm(int ndim, int arith, int tile_shape);
+
+// Update-form ablation (eik_ablation.cu): Algorithm 1 / d-bar at n points, and
+// the Table 3 residual of one field (out[0] += count, out[1] = max bits).
+cudaError_t launch_eval_update(int form, const double *speed, double h, const double *t_h,
+                               const double *t_v, int64_t n, double *out, cudaStream_t stream);
+cudaError_t launch_residual(int form, int ndim, const double *speed, double h, const double *t,
+                            int64_t nx, int64_t ny, int64_t nz, const int64_t *src_idx,
+                            const double *src_t, int64_t nsrc, unsigned long long *out,
+                            cudaStream_t stream);
 
 // Adjoint (eik_adjoint.cu).
 struct AdjProb {

@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include "eik_exact.cuh"
+#include "eik_forms.cuh"
 #include "eik_internal.h"
 
 namespace eik {
@@ -543,7 +544,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, 512 / (TX * TY * TZ)) persistent
     if (timing) { const long long c1 = clock64(); cyc[0] += c1 - c0; c0 = c1; }
     if (first && tid == 0) {   // band = k * sqrt(c_min) / sqrt(D): one cell's travel time
       const float cm = s_cmin < kInfBits ? __double2float_rn(from_bits(s_cmin)) : 0.0f;
-      s_band = bits_of(static_cast<double>(sqrtf(cm) * band_scale));
+      // s_cmin is the smallest c (or r for the explicit roots): one cell's travel time
+      s_band = bits_of(static_cast<double>((p.update ? cm : sqrtf(cm)) * band_scale));
       s_cmin = kInfBits;
     }
     vlim = s_vlim;
@@ -614,7 +616,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, 512 / (TX * TY * TZ)) persistent
         const int cnt = s_cnt[R & 1u];
         unsigned long long nv = kInfBits;
         bool part = false;
-        if (ARITH == kArithFp64 && cnt * 4 <= NT) {
+        if (ARITH == kArithFp64 && cnt * 4 <= NT && !p.update) {
           const int L = cnt * 8 <= NT ? 8 : 4;
           if (warp < (cnt * L + 31) / 32) {
             part = true;
@@ -641,10 +643,15 @@ __global__ void __launch_bounds__(TX * TY * TZ, 512 / (TX * TY * TZ)) persistent
             unsigned long long a[D];
 #pragma unroll
             for (int k = 0; k < D; ++k) a[k] = s_a[k][c];
-            const bool dec = ARITH == kArithInt
-                                 ? xf::relax<D>(s_best[c], a, s_c[c], nv)
-                                 : hw::relax<D>(s_best[c], a, s_c[c], nv,
-                                                p.counters >= 2 ? path : nullptr);
+            bool dec;
+            if (D == 2 && p.update) {   // explicit roots: s_c holds r = fl(h/v)
+              nv = forms::explicit_update(p.update, a[0], a[D - 1], from_bits(s_c[c]));
+              dec = nv < s_best[c];
+            } else {
+              dec = ARITH == kArithInt ? xf::relax<D>(s_best[c], a, s_c[c], nv)
+                                       : hw::relax<D>(s_best[c], a, s_c[c], nv,
+                                                      p.counters >= 2 ? path : nullptr);
+            }
             if (dec) s_pv[c] = nv; else nv = kInfBits;
           }
         }
@@ -848,7 +855,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, 512 / (TX * TY * TZ)) persistent
 // (h/v)^2 of Eq. difference_as_root); checks v > 0 finite and r, c finite and
 // positive; sums r = fl(h / v) for the auto bucket width.
 __global__ void init_c_kernel(const double *__restrict__ speed, double h, double *__restrict__ c_out,
-                              int64_t n, Ctl *ctl) {
+                              int64_t n, Ctl *ctl, int store_r) {
   double sum = 0.0;
   unsigned long long cnt = 0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
@@ -859,7 +866,7 @@ __global__ void init_c_kernel(const double *__restrict__ speed, double h, double
     const bool ok = v > 0.0 && bits_of(v) < kInfBits && ri > 0.0 && bits_of(ri) < kInfBits &&
                     c > 0.0 && bits_of(c) < kInfBits;
     if (!ok) raise_status(ctl, kEinval, static_cast<unsigned long long>(i));
-    c_out[i] = c;
+    c_out[i] = store_r ? ri : c;
     sum += ri;
     ++cnt;
   }
@@ -1045,9 +1052,9 @@ void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_o
 unsigned long long kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, int store_r) {
   if (n <= 0) return cudaSuccess;
-  init_c_kernel<<<grid_for(n, 8), 256, 0, stream>>>(speed, h, c, n, ctl);
+  init_c_kernel<<<grid_for(n, 8), 256, 0, stream>>>(speed, h, c, n, ctl, store_r);
   note_launches(1);
   return cudaGetLastError();
 }
