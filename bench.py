@@ -349,6 +349,8 @@ def make_opts(args):
         opts["tile"] = args.tile
     if args.update > 0:
         opts["update"] = args.update
+    if args.schedule > 0:
+        opts["schedule"] = args.schedule
     return opts
 
 
@@ -402,6 +404,11 @@ def run_single(args, C, wl_name):
     h_src = prob.sources.copy()
 
     def e2e_call():
+        if args.schedule:     # device pointers only: copies around the call
+            speed.copy_(h_speed, non_blocking=True)
+            eik.solve(speed, prob.h, src, out=out, opts=opts)
+            h_out.copy_(out, non_blocking=True)
+            return
         eik.eik_solve(h_speed.data_ptr(), prob.h, prob.speed.ndim, prob.speed.shape,
                       h_src.ctypes.data, None, len(h_src), h_out.data_ptr(), opts or None,
                       C.stream.cuda_stream)
@@ -417,13 +424,17 @@ def run_single(args, C, wl_name):
     line["grid_point_updates_per_s"] = st["evals"] * args.steps * n / (total_ms / 1e3)
     line["work_per_step"] = {k: st[k] for k in ("evals", "decreases", "good", "visits", "pushes",
                                                 "stale_pops", "rounds")}
+    line["work_per_step"].update(empty=st["evals"] - st["decreases"],
+                                 bad=st["decreases"] - st["good"])
     line["residual"] = {"update": ["d-bar", "d-tilde", "d-hat"][args.update], "cells": bad,
                         "max_rel": max_rel, "same_bits_every_step": same_bits}
     traffic = args.traffic_bytes
     if traffic is None and not opts and args.scale == 1.0 and not args.autotune:
         traffic = MEASURED_TRAFFIC.get(args.workload)
     line["roofline"] = roofline(useful, statistics.mean(solve_ms), traffic,
-                                "persistent_kernel (tile relaxation + bucket scheduler)")
+                                ["persistent_kernel (tile relaxation + bucket scheduler)",
+                                 "fim_kernel (Algorithm 3 rounds)",
+                                 "topo_kernel (Algorithm 4 iterations)"][args.schedule])
     line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(prob.speed.nbytes + h_src.nbytes),
                    "d2h_bytes_per_step": int(prob.speed.nbytes)}
@@ -613,6 +624,9 @@ def main():
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--band", type=float, default=0.0)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--schedule", type=int, default=0,
+                    help="single grids: 1 = fast iterative method (Algorithm 3), 2 = "
+                         "topology-driven (Algorithm 4); 0: asynchronous tiles (Algorithm 6)")
     ap.add_argument("--update", type=int, default=0,
                     help="2D ablation: 1 = Algorithm 1 with d-tilde, 2 = with d-hat (0: d-bar)")
     ap.add_argument("--autotune", action="store_true",

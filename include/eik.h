@@ -98,6 +98,13 @@ typedef struct {
                               classical explicit root d-tilde, 2 = with the rearranged root
                               d-hat.  1 and 2 are not monotone: their results may depend on the
                               schedule and are not a fixed point (Table 3). */
+    int schedule;          /* 0 = asynchronous bucketed tiles (Algorithm 6), the default;
+                              single problems only, device pointers, for comparison:
+                              1 = fast iterative method (Algorithm 3, epsilon = 0, rounds),
+                              2 = topology-driven (Algorithm 4, every cell every iteration).
+                              Same bits (Theorem 1), different work and time.  Options other
+                              than timeout_ms and counters do not apply to 1 and 2. */
+    int reserved;          /* keep 0 */
 } eik_opts;
 
 /* Work accounting (the paper's good/empty/bad updates, Results section). */

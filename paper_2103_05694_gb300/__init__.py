@@ -35,7 +35,8 @@ class EikOpts(ctypes.Structure):
                 ("test_stall", ctypes.c_int), ("window", ctypes.c_int),
                 ("band", ctypes.c_double), ("arith", ctypes.c_int), ("sched_flags", ctypes.c_int),
                 ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_int64),
-                ("tile", ctypes.c_int), ("update", ctypes.c_int)]
+                ("tile", ctypes.c_int), ("update", ctypes.c_int),
+                ("schedule", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 TILE_SHAPES = {2: [(16, 16), (32, 8), (32, 4), (16, 8)],
                3: [(8, 8, 4), (16, 4, 4), (32, 4, 2), (8, 4, 4)]}

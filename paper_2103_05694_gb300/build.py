@@ -17,8 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "_libeik.so")
 SOURCES = ["eik_solver.cu", "eik_api.cu", "eik_selftest.cu", "eik_noalloc.cu", "eik_adjoint.cu",
-           "eik_ablation.cu"]
-HEADERS = ["eik_internal.h", "eik_exact.cuh", "eik_forms.cuh",
+           "eik_ablation.cu", "eik_schedules.cu"]
+HEADERS = ["eik_internal.h", "eik_exact.cuh", "eik_forms.cuh", "eik_grid.cuh",
            os.path.join("..", "..", "include", "eik.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

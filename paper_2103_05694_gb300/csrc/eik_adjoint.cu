@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "eik_grid.cuh"
 #include "eik_internal.h"
 
 namespace eik {
@@ -53,19 +54,6 @@ __device__ __forceinline__ unsigned long long ld_rlx_u64(const unsigned long lon
 }
 __device__ __forceinline__ void st_rlx_d(double *p, double v) {
   asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acq_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void st_rel_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ long long gtime() {
-  long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
 }
 
 __device__ __forceinline__ int find_adj_prob(const AdjProb *probs, int nprob, int64_t q) {
@@ -196,32 +184,6 @@ __global__ void adj_seed_kernel(const AdjProb *probs, int nprob, int64_t total, 
   }
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks co-resident).  The wait
-// is bounded: on expiry the status becomes EIK_ETIMEOUT and every block leaves.
-// Returns false when the launch must stop.
-__device__ bool grid_barrier(AdjCtl *ctl, long long timeout_ns) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned gen = ld_acq_u32(&ctl->bar_gen);
-    __threadfence();
-    if (atomicAdd(&ctl->bar_count, 1u) + 1u == gridDim.x) {
-      ctl->bar_count = 0u;
-      __threadfence();
-      st_rel_u32(&ctl->bar_gen, gen + 1u);
-    } else {
-      const long long t0 = gtime();
-      while (ld_acq_u32(&ctl->bar_gen) == gen) {
-        if (ld_acq_u32(&ctl->status) != 0u) break;
-        if (gtime() - t0 > timeout_ns) { atomicCAS(&ctl->status, 0u, kEtimeout); break; }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return ld_acq_u32(&ctl->status) == 0u;
-}
-
 // lambda and dL/ds of one ready cell, then release its upwind cells; the ones
 // that become ready are appended to the next frontier.  All 32 lanes call it.
 __device__ void adj_process(const AdjProb *probs, int nprob, int64_t q, bool live,
@@ -291,7 +253,7 @@ __global__ void __launch_bounds__(kThreads) adj_levels_kernel(const AdjProb *pro
       done += live ? 1u : 0u;
     }
     // the other blocks' decrements and lambdas before the next frontier
-    if (!grid_barrier(ctl, timeout_ns)) break;
+    if (!grid::barrier(&ctl->bar_count, &ctl->bar_gen, &ctl->status, timeout_ns)) break;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) done += __shfl_xor_sync(kFullMask, done, o);

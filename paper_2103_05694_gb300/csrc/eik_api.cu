@@ -103,6 +103,57 @@ struct Workspace {
 
 Workspace g_ws;
 
+struct AdjWorkspace {
+  int device = -1;
+  DevBuf<int> cnt;
+  DevBuf<double> W, lam;
+  DevBuf<unsigned char> mask;
+  DevBuf<unsigned long long> front;
+  DevBuf<eik::AdjProb> probs;
+  DevBuf<eik::AdjCtl> ctl;
+  DevBuf<int64_t> src;
+  eik::AdjCtl *ctl_host = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  void release_all() {
+    cnt.release(); W.release(); lam.release(); mask.release(); front.release();
+    probs.release(); ctl.release(); src.release();
+    if (ctl_host) cudaFreeHost(ctl_host);
+    ctl_host = nullptr;
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    ev0 = ev1 = nullptr;
+    device = -1;
+  }
+};
+AdjWorkspace g_adj;
+
+// Workspace of the comparison schedules (opts.schedule 1, 2).
+struct BspWorkspace {
+  int device = -1;
+  DevBuf<double> c;
+  DevBuf<unsigned char> fixed;
+  DevBuf<unsigned> mark;
+  DevBuf<unsigned long long> front;
+  DevBuf<eik::BspCtl> ctl;
+  DevBuf<int64_t> src;
+  DevBuf<double> src_t;
+  eik::BspCtl *ctl_host = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  void release_all() {
+    c.release(); fixed.release(); mark.release(); front.release(); ctl.release(); src.release();
+    src_t.release();
+    if (ctl_host) cudaFreeHost(ctl_host);
+    ctl_host = nullptr;
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    ev0 = ev1 = nullptr;
+    device = -1;
+  }
+};
+BspWorkspace g_bsp;
+
 eik_status cuda_fail(cudaError_t e, const char *what) {
   set_err("%s: %s", what, cudaGetErrorString(e));
   return EIK_ECUDA;
@@ -263,6 +314,115 @@ eik_status ensure_device() {
   return EIK_OK;
 }
 
+// A single problem with one of the comparison schedules (Algorithm 3 or 4).
+eik_status run_schedule(HostProblem &hp, const eik_opts *opts, eik_stats *stats,
+                        cudaStream_t stream) {
+  const int schedule = opts->schedule;
+  if (schedule != eik::kScheduleFim && schedule != eik::kScheduleTopo) {
+    set_err("opts.schedule must be 0, 1 or 2");
+    return EIK_EINVAL;
+  }
+  if (!hp.speed_dev || !hp.out_dev) { set_err("opts.schedule 1, 2 take device pointers only"); return EIK_EINVAL; }
+  if (opts->update != 0 || opts->arith == 2) {
+    set_err("opts.schedule 1, 2 run the exact update on the FP64 unit only");
+    return EIK_EINVAL;
+  }
+  {
+    int dev = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    if (g_bsp.device != dev) {
+      if (g_bsp.device >= 0) g_bsp.release_all();
+      g_bsp.device = dev;
+    }
+  }
+  eik_status st = ensure_device();
+  if (st != EIK_OK) return st;
+  const int64_t n = hp.n;
+  const size_t ns = hp.src.size();
+  CK(g_bsp.c.ensure((size_t)n), "schedule: c");
+  CK(g_bsp.fixed.ensure((size_t)n), "schedule: flags");
+  CK(g_bsp.mark.ensure((size_t)n * 2), "schedule: marks");
+  CK(g_bsp.front.ensure((size_t)n * 2), "schedule: worklists");
+  CK(g_bsp.ctl.ensure(1), "schedule: control");
+  CK(g_ws.ctl.ensure(1), "schedule: validation block");
+  CK(g_bsp.src.ensure(std::max<size_t>(ns, 1)), "schedule: sources");
+  CK(g_bsp.src_t.ensure(std::max<size_t>(ns, 1)), "schedule: source times");
+  if (!g_bsp.ctl_host) CK(cudaMallocHost(&g_bsp.ctl_host, sizeof(eik::BspCtl)), "schedule: pinned");
+  if (!g_bsp.ev0) {
+    CK(cudaEventCreate(&g_bsp.ev0), "schedule: event");
+    CK(cudaEventCreate(&g_bsp.ev1), "schedule: event");
+  }
+  if (ns) {
+    CK(cudaMemcpyAsync(g_bsp.src.p, hp.src.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, stream),
+       "schedule: upload sources");
+    CK(cudaMemcpyAsync(g_bsp.src_t.p, hp.t0.data(), ns * sizeof(double), cudaMemcpyHostToDevice, stream),
+       "schedule: upload source times");
+  }
+  CK(cudaMemsetAsync(g_bsp.fixed.p, 0, (size_t)n, stream), "schedule: clear flags");
+  CK(cudaMemsetAsync(g_bsp.mark.p, 0, (size_t)n * 2 * sizeof(unsigned), stream), "schedule: clear marks");
+  CK(cudaMemsetAsync(g_bsp.ctl.p, 0, sizeof(eik::BspCtl), stream), "schedule: clear control");
+  CK(cudaMemsetAsync(g_ws.ctl.p, 0, sizeof(Ctl), stream), "schedule: clear validation");
+  CK(eik::launch_init_c(hp.speed, hp.h, g_bsp.c.p, n, g_ws.ctl.p, stream), "schedule: c");
+  CK(eik::launch_init_t(hp.out, n, stream), "schedule: t");
+  eik::BspParams bp;
+  std::memset(&bp, 0, sizeof(bp));
+  bp.t = hp.out;
+  bp.c = g_bsp.c.p;
+  bp.ndim = hp.ndim;
+  bp.nx = hp.dims[2];
+  bp.ny = hp.dims[1];
+  bp.nz = hp.dims[0];
+  bp.fixed = g_bsp.fixed.p;
+  bp.mark[0] = g_bsp.mark.p;
+  bp.mark[1] = g_bsp.mark.p + n;
+  bp.front[0] = g_bsp.front.p;
+  bp.front[1] = g_bsp.front.p + n;
+  bp.ctl = g_bsp.ctl.p;
+  bp.timeout_ns = (opts->timeout_ms > 0 ? opts->timeout_ms : 60000) * 1000000ll;
+  CK(eik::launch_bsp_seed(bp, g_bsp.src.p, g_bsp.src_t.p, (int64_t)ns, stream), "schedule: seed");
+  CK(cudaMemcpyAsync(g_ws.ctl_host, g_ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, stream),
+     "schedule: validation");
+  CK(cudaStreamSynchronize(stream), "schedule: set-up");
+  if (g_ws.ctl_host->status == eik::kEinval) {
+    set_err("invalid input data (cell %llu: speed must be finite and > 0, h/v finite and > 0)",
+            (unsigned long long)g_ws.ctl_host->error_info[0]);
+    return EIK_EINVAL;
+  }
+  CK(cudaEventRecord(g_bsp.ev0, stream), "schedule: event");
+  CK(eik::launch_schedule(schedule, bp, stream), "schedule launch");
+  CK(cudaEventRecord(g_bsp.ev1, stream), "schedule: event");
+  CK(cudaMemcpyAsync(g_bsp.ctl_host, g_bsp.ctl.p, sizeof(eik::BspCtl), cudaMemcpyDeviceToHost, stream),
+     "schedule: status");
+  unsigned long long finite = 0;
+  if (opts->counters) {
+    CK(g_ws.count.ensure(1), "schedule: count");
+    CK(cudaMemsetAsync(g_ws.count.p, 0, sizeof(unsigned long long), stream), "schedule: count");
+    eik::Prob P;
+    std::memset(&P, 0, sizeof(P));
+    P.t = hp.out;
+    P.nx = bp.nx;
+    P.ny = bp.ny;
+    P.nz = bp.nz;
+    CK(eik::launch_count_finite(&P, 1, g_ws.count.p, stream), "schedule: count");
+    CK(cudaMemcpyAsync(&finite, g_ws.count.p, sizeof(finite), cudaMemcpyDeviceToHost, stream),
+       "schedule: count");
+  }
+  CK(cudaStreamSynchronize(stream), "schedule");
+  const eik::BspCtl &c = *g_bsp.ctl_host;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->evals = (int64_t)c.evals;
+    stats->decreases = (int64_t)c.decreases;
+    stats->rounds = (int64_t)c.rounds;
+    if (opts->counters) stats->good = (int64_t)finite - (int64_t)ns;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g_bsp.ev0, g_bsp.ev1) == cudaSuccess) stats->solve_ms = ms;
+  }
+  if (c.status == eik::kEtimeout) { set_err("device wait timed out"); return EIK_ETIMEOUT; }
+  if (c.status != 0) return EIK_ECUDA;
+  return EIK_OK;
+}
+
 // The whole solve for a list of host-checked problems (1 = eik_solve).
 eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *stats,
                cudaStream_t stream) {
@@ -271,6 +431,10 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   const int ndim = hps[0].ndim;
   for (auto &hp : hps) {
     if (hp.ndim != ndim) { set_err("all problems of a batch must have the same ndim"); return EIK_EINVAL; }
+  }
+  if (opts && opts->schedule != 0) {
+    if (hps.size() != 1) { set_err("opts.schedule 1, 2 solve single problems only"); return EIK_EINVAL; }
+    return run_schedule(hps[0], opts, stats, stream);
   }
   int64_t tx, ty, tz;
   int shape = 0;
@@ -542,30 +706,6 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   return EIK_OK;
 }
 
-struct AdjWorkspace {
-  int device = -1;
-  DevBuf<int> cnt;
-  DevBuf<double> W, lam;
-  DevBuf<unsigned char> mask;
-  DevBuf<unsigned long long> front;
-  DevBuf<eik::AdjProb> probs;
-  DevBuf<eik::AdjCtl> ctl;
-  DevBuf<int64_t> src;
-  eik::AdjCtl *ctl_host = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-
-  void release_all() {
-    cnt.release(); W.release(); lam.release(); mask.release(); front.release();
-    probs.release(); ctl.release(); src.release();
-    if (ctl_host) cudaFreeHost(ctl_host);
-    ctl_host = nullptr;
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
-    ev0 = ev1 = nullptr;
-    device = -1;
-  }
-};
-AdjWorkspace g_adj;
 
 }  // namespace
 
@@ -628,6 +768,10 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
   }
   const int ndim = hps[0].ndim;
   const int di = ndim == 3 ? 1 : 0;
+  if (base && base->schedule != 0) {
+    set_err("eik_autotune tunes the asynchronous schedule (opts.schedule 0)");
+    return EIK_EINVAL;
+  }
   if (base && base->update != 0) {
     set_err("eik_autotune needs the exact update (opts.update 0): only then are the bits "
             "independent of the schedule");
@@ -836,6 +980,7 @@ void eik_release(void) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_ws.release_all();
   g_adj.release_all();
+  g_bsp.release_all();
 }
 
 const char *eik_status_str(eik_status s) {
@@ -852,7 +997,7 @@ const char *eik_status_str(eik_status s) {
 
 const char *eik_last_error(void) { return g_err; }
 
-int eik_abi_version(void) { return 103; }
+int eik_abi_version(void) { return 104; }
 
 uint64_t eik_kernel_launches(void) { return (uint64_t)eik::kernel_launches(); }
 
@@ -914,6 +1059,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   int form = 0;
   tst = update_form(opts, pl.ndim, form);
   if (tst != EIK_OK) return tst;
+  if (opts && opts->schedule != 0) { set_err("plans run the asynchronous schedule (opts.schedule 0)"); return EIK_EINVAL; }
   std::vector<int> prob_speed(hps.size());
   int64_t c_total = 0;
   for (size_t i = 0; i < hps.size(); ++i) {

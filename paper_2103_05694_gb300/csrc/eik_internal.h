@@ -158,6 +158,34 @@ void note_launches(unsigned long long n);
 unsigned long long kernel_launches();
 int persistent_blocks_per_sm(int ndim, int arith, int tile_shape);
 
+// Other schedules of the same update (eik_schedules.cu): opts.schedule.
+constexpr int kScheduleAmm = 0, kScheduleFim = 1, kScheduleTopo = 2;
+
+struct BspCtl {
+  unsigned long long nfront[3];   // worklist sizes (FIM) / changes per iteration (topology)
+  unsigned long long pad0[13];
+  unsigned bar_count, bar_gen;
+  unsigned pad1[30];
+  unsigned long long evals, decreases, rounds;
+  unsigned status;
+};
+
+struct BspParams {
+  double *t;
+  const double *c;                // c = fl(fl(h/v)^2)
+  int ndim;
+  int64_t nx, ny, nz;
+  unsigned char *fixed;           // 1 at source cells
+  unsigned *mark[2];              // round stamps: w_r is mark[r & 1] == r
+  unsigned long long *front[2];   // worklists of consecutive rounds
+  BspCtl *ctl;
+  long long timeout_ns;
+};
+
+cudaError_t launch_bsp_seed(const BspParams &p, const int64_t *src_idx, const double *src_t,
+                            int64_t nsrc, cudaStream_t stream);
+cudaError_t launch_schedule(int schedule, BspParams p, cudaStream_t stream);
+
 // Update-form ablation (eik_ablation.cu): Algorithm 1 / d-bar at n points, and
 // the Table 3 residual of one field (out[0] += count, out[1] = max bits).
 cudaError_t launch_eval_update(int form, const double *speed, double h, const double *t_h,

@@ -168,7 +168,8 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
     if (n > na::kMaxCells) return EIK_EINVAL;                 // beyond the scratch limit
   }
   if (nsrc < 0 || nsrc > na::kMaxSources) return EIK_EINVAL;  // beyond the scratch limit
-  if (opts && (opts->update != 0 || opts->tile != 0)) return EIK_EINVAL;   // default form and tile only
+  if (opts && (opts->update != 0 || opts->tile != 0 || opts->schedule != 0))
+    return EIK_EINVAL;   // default form, tile and schedule only
   if (!na::device_ptr(speed) || !na::device_ptr(out_t)) return EIK_EINVAL;
   if (nsrc > 0 && !na::device_ptr(src_idx)) return EIK_EINVAL;
   if (src_t && !na::device_ptr(src_t)) return EIK_EINVAL;

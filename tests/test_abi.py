@@ -47,12 +47,12 @@ def test_status_strings_without_gpu(lib):
     assert lib.eik_status_str(0) == b"EIK_OK"
     assert lib.eik_status_str(3) == b"EIK_ECAPACITY"
     lib.eik_abi_version.restype = ctypes.c_int
-    assert lib.eik_abi_version() == 103
+    assert lib.eik_abi_version() == 104
 
 
 def test_struct_layouts_match_header():
-    # eik_opts: double, double, int64, int64, 4 x int, double, 2 x int, ptr, int64, 2 x int
-    assert ctypes.sizeof(eik.EikOpts) == 88
+    # eik_opts: double, double, int64, int64, 4 x int, double, 2 x int, ptr, int64, 4 x int
+    assert ctypes.sizeof(eik.EikOpts) == 96
     assert ctypes.sizeof(eik.EikStats) == 23 * 8
     # eik_problem: ptr, double, int(+pad), int64[3], ptr, ptr, int64, ptr
     assert ctypes.sizeof(eik.EikProblem) == 8 + 8 + 8 + 24 + 8 + 8 + 8 + 8
@@ -75,4 +75,4 @@ def test_kernel_launch_counter_without_gpu(lib):
 
 def test_tune_trial_layout():
     # eik_tune_trial: eik_opts, double, int, int
-    assert ctypes.sizeof(eik.EikTuneTrial) == 88 + 8 + 4 + 4
+    assert ctypes.sizeof(eik.EikTuneTrial) == 96 + 8 + 4 + 4
