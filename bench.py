@@ -242,6 +242,27 @@ def cpu_baseline(args):
 
 
 # --------------------------------------------------------------------------
+# Multi-rank timing (replicas: every rank solves its own copy; the only
+# collectives are the timing barrier and the max over ranks)
+# --------------------------------------------------------------------------
+
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The largest of every rank's x (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, n_ranks: int, total_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank processes the same units)."""
+    return units_per_rank * n_ranks / (total_ms / 1e3)
+
+
+# --------------------------------------------------------------------------
 # GPU arms
 # --------------------------------------------------------------------------
 
@@ -272,11 +293,7 @@ class Ctx:
         self.torch.cuda.synchronize(self.dev)
 
     def max_over_ranks(self, x: float) -> float:
-        if self.dist is None:
-            return x
-        t = self.torch.tensor([x], device=self.dev, dtype=self.torch.float64)
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, self.dist, self.dev)
 
     def timed(self, steps: int, step_fn):
         """Events around each step on the launching stream, L2 flushed between
@@ -396,7 +413,7 @@ def run_single(args, C, wl_name):
     same_bits = bool(torch.equal(out, ref))
     assert same_bits or args.update != 0      # d-bar: the same bits on every run (Theorem 1)
     n = args.gpus
-    value = useful * args.steps * n / (total_ms / 1e3)
+    value = job_value(useful * args.steps, n, total_ms)
 
     # end to end through the C ABI with host buffers (copies inside the call)
     h_speed = torch.from_numpy(prob.speed).pin_memory()
@@ -485,7 +502,7 @@ def run_batched(args, C, wl_name):
     for q, r in zip(problems, refs):
         assert torch.equal(q["out"], r)
     n = args.gpus
-    value = useful * args.steps * n / (total_ms / 1e3)
+    value = job_value(useful * args.steps, n, total_ms)
 
     # end to end: each step copies the models from pinned host memory into the
     # plan's device buffers, replays the plan and copies every field back
@@ -549,7 +566,7 @@ def run_tomography(args, C, wl_name):
     g_last, _ = grad_of(s0)
     assert torch.equal(g_last, g_ref)       # the gradient is deterministic
     n = args.gpus
-    value = useful * args.steps * n / (total_ms / 1e3)
+    value = job_value(useful * args.steps, n, total_ms)
 
     # the same gradient from per-source solves and adjoints (one problem per call)
     speed = torch.reciprocal(s0)

@@ -299,6 +299,124 @@ __device__ __forceinline__ bool relax(unsigned long long best, const unsigned lo
 }  // namespace eik
 
 namespace eik {
+// Float-float ("double-single") arithmetic on the FP32 pipe: a value is an
+// unevaluated sum hi + lo of two floats, about 48 bits.  Error-free
+// transformations: Knuth's TwoSum, Dekker's FastTwoSum (|a| >= |b|) and the
+// FMA-based TwoProduct; square root by one Newton correction of sqrtf
+// (Karp and Markstein).  Used only for starting points of d-bar, whose exact
+// test decides the result.
+namespace ffa {
+
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return F2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return F2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return F2{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ F2 add(F2 x, F2 y) {
+  const F2 s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ F2 neg(F2 x) { return F2{-x.hi, -x.lo}; }
+__device__ __forceinline__ F2 mul(F2 x, F2 y) {
+  const F2 p = two_prod(x.hi, y.hi);
+  return fast_two_sum(p.hi, __fadd_rn(p.lo, __fadd_rn(__fmul_rn(x.hi, y.lo), __fmul_rn(x.lo, y.hi))));
+}
+__device__ __forceinline__ F2 scale2(F2 x, float k) {   // k a power of two: exact
+  return F2{__fmul_rn(x.hi, k), __fmul_rn(x.lo, k)};
+}
+__device__ __forceinline__ F2 sqrt(F2 x) {
+  if (!(x.hi > 0.0f)) return F2{0.0f, 0.0f};
+  const float y = sqrtf(x.hi);
+  const F2 p = two_prod(y, y);
+  const float e = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);   // x - y^2
+  return fast_two_sum(y, __fdividef(e, __fadd_rn(y, y)));
+}
+// A non-negative finite double (bit pattern) as hi + lo without the FP64
+// pipe: hi keeps the leading 24 bits of the significand (xf::to_f truncates),
+// lo the remaining 29 bits rounded to a float.
+__device__ __forceinline__ F2 split(unsigned long long u) {
+  const float hi = xf::to_f(u);
+  const int se = static_cast<int>((u >> 52) & 0x7ffu) - 1075 + 127;   // 2^(E - 1075) as a float
+  const unsigned rem = static_cast<unsigned>(u & ((1ull << 29) - 1ull));
+  float lo = 0.0f;
+  if (se > 0 && se < 255) lo = __fmul_rn(__uint2float_rn(rem), __int_as_float(se << 23));
+  return F2{hi, lo};
+}
+
+}  // namespace ffa
+
+namespace hw {
+
+// Starting point of d-bar from float-float arithmetic: u = tau - s0 is the
+// root of the active-set quadratic over the sorted minima s0 <= s1 (<= s2)
+// (one-sided: u = sqrt(c); two axes: u = (b1 + sqrt(2c - b1^2)) / 2, the
+// rearranged root d-hat of the Mitigation Strategies section; three axes:
+// u = (S + sqrt(S^2 - 3 (Q - c))) / 3), with b_k = s_k - s0 (exact FP64
+// differences of close values).  About 3 (2D) / 4 (3D) FP64 instructions;
+// u carries about 47 bits, so tau = s0 + u lands within an ulp of d-bar when
+// u is small against tau (cells farther than a few dozen cells from a
+// source), else within a few.  Only speed depends on this.
+template <int D>
+__device__ __forceinline__ unsigned long long ffguess(const unsigned long long (&a)[D],
+                                                      unsigned long long cb) {
+  unsigned long long s0 = a[0], s1 = D > 1 ? a[1] : xf::kInf, s2 = D > 2 ? a[2] : xf::kInf;
+  {
+    const unsigned long long lo = xf::umin(s0, s1), hi = xf::umax(s0, s1);
+    s0 = lo;
+    s1 = hi;
+    if (D > 2) {
+      const unsigned long long l2 = xf::umin(s1, s2), h2 = xf::umax(s1, s2);
+      s2 = h2;
+      s1 = xf::umax(s0, l2);
+      s0 = xf::umin(s0, l2);
+    }
+  }
+  const ffa::F2 c = ffa::split(cb);
+  ffa::F2 u = ffa::sqrt(c);                                      // one-sided
+  if (s1 < xf::kInf) {
+    const ffa::F2 b1 = ffa::split(xf::as_u(__dsub_rn(xf::as_d(s1), xf::as_d(s0))));
+    if (b1.hi < u.hi) {                                          // two axes
+      const ffa::F2 X = ffa::add(ffa::scale2(c, 2.0f), ffa::neg(ffa::mul(b1, b1)));
+      u = ffa::scale2(ffa::add(b1, ffa::sqrt(X)), 0.5f);
+      if (D > 2 && s2 < xf::kInf) {
+        const ffa::F2 b2 = ffa::split(xf::as_u(__dsub_rn(xf::as_d(s2), xf::as_d(s0))));
+        if (b2.hi < u.hi) {                                      // three axes
+          const ffa::F2 S = ffa::add(b1, b2);
+          const ffa::F2 Q = ffa::add(ffa::mul(b1, b1), ffa::mul(b2, b2));
+          const ffa::F2 disc = ffa::add(ffa::mul(S, S),
+                                        ffa::mul(ffa::F2{-3.0f, 0.0f}, ffa::add(Q, ffa::neg(c))));
+          if (disc.hi > 0.0f) {
+            const ffa::F2 third{__int_as_float(0x3eaaaaab),
+                                __int_as_float(static_cast<int>(0xb22aaaabu))};
+            u = ffa::mul(ffa::add(S, ffa::sqrt(disc)), third);
+          }
+        }
+      }
+    }
+  }
+  // tau = s0 + hi + lo on the FP64 unit (two additions)
+  double t = __dadd_rn(xf::as_d(s0), xf::as_d(xf::from_f(u.hi)));
+  const unsigned long long lob = xf::from_f(fabsf(u.lo));
+  t = u.lo < 0.0f ? __dsub_rn(t, xf::as_d(lob)) : __dadd_rn(t, xf::as_d(lob));
+  unsigned long long tau = xf::as_u(t);
+  if (!(tau > s0) || tau >= xf::kInf) tau = s0 + 1ull;
+  return tau;
+}
+
+}  // namespace hw
+
 namespace hw {
 
 // The same update on the hardware FP64 unit: every operation of G an explicit
@@ -342,11 +460,10 @@ __device__ __forceinline__ unsigned long long G_slope(unsigned long long tau,
   return as_u(g);
 }
 
-// d-bar with the exact G on the FP64 unit: fp32 starting guess (one-sided
-// root, else the quadratic root of the smallest two (three) minima), Newton
-// steps on G(tau) - c, then the exact test G(tau) >= c > G(prev(tau)) with a
-// few ulp steps and bisection as the last resort.  About 20 FP64
-// instructions in the common case.
+// d-bar with the exact G on the FP64 unit: float-float starting point
+// (ffguess), then the exact test G(tau) >= c > G(prev(tau)) with a few ulp
+// steps and bisection as the last resort.  About 13 (2D) FP64 instructions in
+// the common case.
 template <int D>
 __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned long long cb,
                                    unsigned *path = nullptr) {
@@ -364,67 +481,50 @@ __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned lo
       s0 = xf::umin(s0, l2);
     }
   }
-  const float cf = xf::to_f(cb);
-  const float rf = sqrtf(cf);
-  float w = rf;
-  if (s1 != kInf) {
-    const float u1 = xf::to_f(as_u(__dsub_rn(as_d(s1), as_d(s0))));
-    if (u1 < rf) {
-      w = 0.5f * (u1 + sqrtf(fmaxf(2.0f * cf - u1 * u1, 0.0f)));
-      if (D > 2 && s2 != kInf) {
-        const float u2 = xf::to_f(as_u(__dsub_rn(as_d(s2), as_d(s0))));
-        if (w > u2) {
-          const float s = u1 + u2;
-          const float disc = s * s - 3.0f * (u1 * u1 + u2 * u2 - cf);
-          if (disc >= 0.0f) w = (s + sqrtf(disc)) * (1.0f / 3.0f);
-        }
+  unsigned long long tau = ffguess<D>(a, cb);
+  bool above = G<D>(tau, a) >= cb;
+  // walk a few ulps; if the root is farther (float-float carries ~47 bits, too
+  // few when tau - s0 is large against tau), one Newton step on G(tau) - c on
+  // the FP64 unit, walk again, then bracket and bisect
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    if (above) {
+#pragma unroll 1
+      for (int i = 0; i < 4; ++i) {
+        if (path) path[1] += 1u;
+        if (tau - 1ull <= s0) return tau;                  // G(a_0) = 0 < c
+        if (G<D>(tau - 1ull, a) < cb) return tau;
+        --tau;
+      }
+    } else {
+#pragma unroll 1
+      for (int i = 0; i < 4; ++i) {
+        if (path) path[1] += 1u;
+        ++tau;
+        if (G<D>(tau, a) >= cb) return tau;
       }
     }
-  }
-  unsigned long long tau = as_u(__dadd_rn(as_d(s0), as_d(xf::from_f(w))));
-  if (tau <= s0 || tau >= kInf) tau = s0 + 1ull;
-  unsigned long long g = kInf;
-  bool have_g = false;
-#pragma unroll 1
-  for (int it = 0; it < 3; ++it) {
-    float msum;
-    g = G_slope<D>(tau, a, msum);
-    have_g = true;
+    if (pass == 1) break;
     if (path) path[0] += 1u;
-    if (!(msum > 0.0f) || g >= kInf) break;
-    const float alpha = g >= cb ? xf::to_f(as_u(__dsub_rn(as_d(g), as_d(cb))))
-                                : -xf::to_f(as_u(__dsub_rn(as_d(cb), as_d(g))));
+    float msum;
+    const unsigned long long gs = G_slope<D>(tau, a, msum);
+    if (!(msum > 0.0f) || gs >= kInf) break;
+    const float alpha = gs >= cb ? xf::to_f(as_u(__dsub_rn(as_d(gs), as_d(cb))))
+                                 : -xf::to_f(as_u(__dsub_rn(as_d(cb), as_d(gs))));
     const float step = __fdividef(alpha, 2.0f * msum);
-    if (fabsf(step) <= 0.25f * xf::ulp_f(tau)) break;   // the root is within this ulp
     unsigned long long sb = xf::from_f(fabsf(step));
-    if (step < 0.0f) sb |= 1ull << 63;                 // tau - step, sign set on the bits
+    if (step < 0.0f) sb |= 1ull << 63;                   // tau - step, sign set on the bits
     unsigned long long nt = as_u(__dsub_rn(as_d(tau), as_d(sb)));
     if (nt <= s0 || nt >= kInf) nt = s0 + 1ull;
-    if (nt == tau) break;
     tau = nt;
-    have_g = false;
+    above = G<D>(tau, a) >= cb;
   }
-  if (!have_g) g = G<D>(tau, a);
   unsigned long long lo, hi;
-  if (g >= cb) {
-#pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-      if (path) path[1] += 1u;
-      if (tau - 1ull <= s0) return tau;
-      if (G<D>(tau - 1ull, a) < cb) return tau;
-      --tau;
-    }
+  if (above) {
     hi = tau;
     lo = s0;
   } else {
     lo = tau;
-#pragma unroll 1
-    for (int i = 0; i < 4; ++i) {
-      if (path) path[1] += 1u;
-      ++tau;
-      if (G<D>(tau, a) >= cb) return tau;
-      lo = tau;
-    }
     unsigned long long step = 1ull;
     hi = lo + 1ull;
 #pragma unroll 1
@@ -463,77 +563,6 @@ __device__ __forceinline__ bool relax(unsigned long long best, const unsigned lo
 namespace eik {
 namespace hw {
 
-// Starting point for d-bar in about 9 (2D) / 15 (3D) FP64 instructions and
-// no branches on the data: the root of the active-set quadratic
-//   A w^2 - 2 B w + C = 0,  A = |S|,  B = sum_S u_k,  C = sum_S u_k^2 - c,
-// with u_k = a_k - a_0 over the sorted minima; the active set S is picked
-// in fp32 (one-sided, two axes, three axes: Algorithm 1's case split and the
-// rearranged root d-hat of the Mitigation Strategies section).  The square
-// root is an fp32 reciprocal-square-root seed refined by two DFMA Newton
-// steps.  tau = a_0 + w lands within about an ulp of d-bar; only speed
-// depends on this.  a are the minima in axis order, s0 their minimum.
-template <int D>
-__device__ __forceinline__ unsigned long long guess(const unsigned long long (&a)[D],
-                                                    unsigned long long cb) {
-  unsigned long long s0 = a[0], s1 = D > 1 ? a[1] : kInf, s2 = D > 2 ? a[2] : kInf;
-  {
-    const unsigned long long lo = xf::umin(s0, s1), hi = xf::umax(s0, s1);
-    s0 = lo;
-    s1 = hi;
-    if (D > 2) {
-      const unsigned long long l2 = xf::umin(s1, s2), h2 = xf::umax(s1, s2);
-      s2 = h2;
-      s1 = xf::umax(s0, l2);
-      s0 = xf::umin(s0, l2);
-    }
-  }
-  const double c = as_d(cb);
-  const double a0 = as_d(s0);
-  double u1 = s1 < kInf ? __dsub_rn(as_d(s1), a0) : 0.0;
-  double u2 = 0.0;
-  if (D > 2) u2 = s2 < kInf ? __dsub_rn(as_d(s2), a0) : 0.0;
-  // active set in fp32
-  const float cf = xf::to_f(cb);
-  const float rf = sqrtf(cf);
-  const float u1f = xf::to_f(as_u(u1)), u2f = xf::to_f(as_u(u2));
-  int A = 1;
-  float wf = rf;
-  if (s1 < kInf && u1f < rf) {
-    A = 2;
-    wf = 0.5f * (u1f + sqrtf(fmaxf(2.0f * cf - u1f * u1f, 0.0f)));
-    if (D > 2 && s2 < kInf && u2f < wf) A = 3;
-  }
-  if (A < 2) u1 = 0.0;
-  if (A < 3) u2 = 0.0;
-  double w;
-  if (D == 2) {
-    // 2D: w = (u1 + sqrt(X - u1^2)) / 2 with X = 2c (two axes) or X = 4c, u1 = 0 (one axis)
-    const double X = as_d(cb + (static_cast<unsigned long long>(A == 2 ? 1 : 2) << 52));  // exact 2c / 4c
-    const double x = fma(-u1, u1, X);
-    const float xf32 = fmaxf(xf::to_f(as_u(x)), 1e-30f);
-    const float y0 = rsqrtf(xf32);
-    const double hy = as_d(xf::from_f(0.5f * y0));
-    double sq = x * as_d(xf::from_f(y0));
-    sq = fma(fma(-sq, sq, x), hy, sq);
-    sq = fma(fma(-sq, sq, x), hy, sq);
-    w = as_d(as_u(u1 + sq) - (1ull << 52));                                  // halve exactly
-  } else {
-    const double B = u1 + u2;
-    const double C = fma(u1, u1, fma(u2, u2, -c));
-    const double x = fma(B, B, -static_cast<double>(A) * C);
-    const float xf32 = fmaxf(xf::to_f(as_u(x)), 1e-30f);
-    const float y0 = rsqrtf(xf32);
-    const double hy = as_d(xf::from_f(0.5f * y0));
-    double sq = x * as_d(xf::from_f(y0));
-    sq = fma(fma(-sq, sq, x), hy, sq);
-    sq = fma(fma(-sq, sq, x), hy, sq);
-    w = (B + sq) * (A == 1 ? 1.0 : (A == 2 ? 0.5 : (1.0 / 3.0)));
-  }
-  unsigned long long t = as_u(a0 + w);
-  if (!(t > s0) || t >= kInf) t = s0 + 1ull;
-  return t;
-}
-
 // The update for one cell, evaluated by a group of L lanes (L = 4 or 8,
 // aligned within the warp).  Every lane computes the same starting point;
 // lane 0 of the group evaluates G(prev(best)) (is a decrease possible?), the
@@ -548,7 +577,7 @@ __device__ __forceinline__ bool relax_group(unsigned long long best, const unsig
                                             unsigned long long &out) {
   const unsigned lane = threadIdx.x & 31u;
   const unsigned j = lane & (L - 1u);
-  const unsigned long long tg = valid ? guess<D>(a, cb) : 1ull;
+  const unsigned long long tg = valid ? ffguess<D>(a, cb) : 1ull;
   unsigned long long amin = a[0];
 #pragma unroll
   for (int k = 1; k < D; ++k) amin = xf::umin(amin, a[k]);
