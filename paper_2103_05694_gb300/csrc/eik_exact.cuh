@@ -420,9 +420,10 @@ __device__ __forceinline__ unsigned long long ffguess(const unsigned long long (
 namespace hw {
 
 // The same update on the hardware FP64 unit: every operation of G an explicit
-// round-to-nearest intrinsic (never contracted into an FMA); the guess uses
-// the d-hat form of the quadratic root with a hardware sqrt; the finish is the
-// exact ulp test.  Same interface as xf::relax (bit patterns in and out).
+// round-to-nearest intrinsic (never contracted into an FMA); the starting
+// point is ffguess (float-float, the d-hat form of the quadratic root for two
+// axes); the finish is the exact ulp test.  Same interface as xf::relax (bit
+// patterns in and out).
 using xf::as_d;
 using xf::as_u;
 using xf::kInf;
