@@ -483,7 +483,11 @@ __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned lo
     }
   }
   unsigned long long tau = ffguess<D>(a, cb);
-  bool above = G<D>(tau, a) >= cb;
+  // the exact test at the starting point: two independent G evaluations
+  const unsigned long long g_prev = G<D>(tau - 1ull, a);
+  const unsigned long long g_here = G<D>(tau, a);
+  if (g_here >= cb && g_prev < cb) return tau;
+  bool above = g_here >= cb;
   // walk a few ulps; if the root is farther (float-float carries ~47 bits, too
   // few when tau - s0 is large against tau), one Newton step on G(tau) - c on
   // the FP64 unit, walk again, then bracket and bisect
@@ -552,10 +556,10 @@ __device__ __forceinline__ bool relax(unsigned long long best, const unsigned lo
 #pragma unroll
   for (int k = 1; k < D; ++k) amin = xf::umin(amin, a[k]);
   if (amin >= kInf || best <= amin) return false;
-  if (best < kInf && G<D>(best - 1ull, a) < cb) return false;
   if (path) path[3] += 1u;
+  // d-bar directly (no separate G(prev(best)) test): a decrease iff d-bar < best
   out = dbar<D>(a, cb, path);
-  return true;
+  return out < best;
 }
 
 }  // namespace hw
