@@ -406,10 +406,12 @@ __device__ __forceinline__ unsigned long long ffguess(const unsigned long long (
       }
     }
   }
-  // tau = s0 + hi + lo on the FP64 unit (two additions)
+  // tau = s0 + hi + lo on the FP64 unit (two additions, the second rounded
+  // upward: d-bar is the double just above the real root, so rounding up
+  // lands on it far more often than rounding to nearest)
   double t = __dadd_rn(xf::as_d(s0), xf::as_d(xf::from_f(u.hi)));
   const unsigned long long lob = xf::from_f(fabsf(u.lo));
-  t = u.lo < 0.0f ? __dsub_rn(t, xf::as_d(lob)) : __dadd_rn(t, xf::as_d(lob));
+  t = u.lo < 0.0f ? __dsub_ru(t, xf::as_d(lob)) : __dadd_ru(t, xf::as_d(lob));
   unsigned long long tau = xf::as_u(t);
   if (!(tau > s0) || tau >= xf::kInf) tau = s0 + 1ull;
   return tau;
