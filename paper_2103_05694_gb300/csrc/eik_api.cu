@@ -291,6 +291,19 @@ eik_status update_form(const eik_opts *opts, int ndim, int &form) {
   return EIK_OK;
 }
 
+// Lane-group d-bar (several lanes per listed cell) pays when a solve is
+// latency-bound, i.e. has few tiles per persistent CTA; with many tiles per
+// CTA the FP64 pipe is better spent on one lane per cell.  sched_flags bits
+// 1-2 override: 1 = never, 2 = lists of up to a quarter of the tile, 3 = an
+// eighth.
+int lane_group_cells(const eik_opts *opts, int64_t tile_cells, int64_t total_tiles, int64_t grid) {
+  const int mode = opts ? (opts->sched_flags >> 1) & 3 : 0;
+  if (mode == 1) return 0;
+  if (mode == 2) return (int)(tile_cells / 4);
+  if (mode == 3) return (int)(tile_cells / 8);
+  return total_tiles < 8 * grid ? (int)(tile_cells / 4) : 0;
+}
+
 // Default persistent CTAs per SM: the per-dimension default for 256-cell
 // tiles, scaled up for smaller tiles.
 int default_ctas_per_sm(int di, int64_t tile_cells) {
@@ -617,6 +630,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   int64_t grid = (int64_t)dev_sms * per_sm;
   if (grid > total_tiles) grid = total_tiles;
   if (grid < 1) grid = 1;
+  sp.lane_group_cells = lane_group_cells(opts, tx * ty * tz, total_tiles, grid);
 
   eik_stats acc;
   std::memset(&acc, 0, sizeof(acc));
@@ -1172,6 +1186,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   int64_t grid = (int64_t)sms * per_sm;
   if (grid > pl.total_tiles) grid = pl.total_tiles;
   pl.grid = (int)std::max<int64_t>(grid, 1);
+  sp.lane_group_cells = lane_group_cells(opts, tx * ty * tz, pl.total_tiles, pl.grid);
   return EIK_OK;
 }
 

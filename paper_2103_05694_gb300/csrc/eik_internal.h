@@ -85,6 +85,7 @@ struct SolveParams {
   int gate_pending_only;          // window follows pending entries only, not running tiles
   int tile_shape;                 // index into tile_shape_of (0: default)
   int update;                     // 0: d-bar; 2D ablation: 1 = d-tilde, 2 = d-hat (c holds r)
+  int lane_group_cells;           // lists of at most this many cells use lane groups (0: never)
   struct TraceRec *trace;         // optional visit trace (device), NULL when off
   unsigned long long trace_cap;
 };

@@ -260,6 +260,8 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
   int64_t grid = static_cast<int64_t>(sms) * per_sm;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
+  // lane-group d-bar when the solve has few tiles per CTA (as the main path)
+  sp.lane_group_cells = ntiles < 8 * grid ? static_cast<int>(tx * ty * tz / 4) : 0;
   if (launch_persistent(sp, static_cast<int>(grid), s) != cudaSuccess) return EIK_ECUDA;
 
   unsigned long long *count = reinterpret_cast<unsigned long long *>(base + na::kOffCount);

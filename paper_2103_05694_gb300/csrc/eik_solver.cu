@@ -609,14 +609,15 @@ __global__ void __launch_bounds__(TX * TY * TZ, 512 / (TX * TY * TZ)) persistent
       }
       __syncthreads();                                              // barrier 1
       if (timing) { const long long c1 = clock64(); cyc[1] += c1 - c0; c0 = c1; }
-      // (B) dense arithmetic phase.  Few cells: a group of 8 (or 4) lanes per
-      //     cell evaluates d-bar (guess + one G pass over a window of points);
-      //     many cells: one lane per cell.  Only warps holding work take part.
+      // (B) dense arithmetic phase.  Few cells (at most p.lane_group_cells): a
+      //     group of 8 (or 4) lanes per cell evaluates d-bar (guess + one G
+      //     pass over a window of points); else one lane per cell.  Only warps
+      //     holding work take part.
       {
         const int cnt = s_cnt[R & 1u];
         unsigned long long nv = kInfBits;
         bool part = false;
-        if (ARITH == kArithFp64 && cnt * 4 <= NT && !p.update) {
+        if (ARITH == kArithFp64 && cnt <= p.lane_group_cells && cnt * 4 <= NT && !p.update) {
           const int L = cnt * 8 <= NT ? 8 : 4;
           if (warp < (cnt * L + 31) / 32) {
             part = true;
