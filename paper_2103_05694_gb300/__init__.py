@@ -192,6 +192,10 @@ def eik_kernel_launches() -> int:
 def _make_opts(opts: dict | None) -> EikOpts | None:
     if not opts:
         return None
+    names = {n for n, _ in EikOpts._fields_}
+    unknown = sorted(set(opts) - names)
+    if unknown:
+        raise KeyError(f"unknown eik_opts fields {unknown}; known: {sorted(names)}")
     o = EikOpts()
     for k, v in opts.items():
         setattr(o, k, v)

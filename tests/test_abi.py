@@ -76,3 +76,10 @@ def test_kernel_launch_counter_without_gpu(lib):
 def test_tune_trial_layout():
     # eik_tune_trial: eik_opts, double, int, int
     assert ctypes.sizeof(eik.EikTuneTrial) == 96 + 8 + 4 + 4
+
+
+def test_unknown_option_names_are_rejected():
+    with pytest.raises(KeyError):
+        eik._make_opts({"bnd": 4.0})
+    o = eik._make_opts({"band": 4.0, "tile": 1, "schedule": 2})
+    assert o.band == 4.0 and o.tile == 1 and o.schedule == 2
