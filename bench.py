@@ -451,7 +451,8 @@ def run_single(args, C, wl_name):
     line["roofline"] = roofline(useful, statistics.mean(solve_ms), traffic,
                                 ["persistent_kernel (tile relaxation + bucket scheduler)",
                                  "fim_kernel (Algorithm 3 rounds)",
-                                 "topo_kernel (Algorithm 4 iterations)"][args.schedule])
+                                 "topo_kernel (Algorithm 4 iterations)",
+                                 "fsm_kernel (Algorithm 5 sweeps)"][args.schedule])
     line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(prob.speed.nbytes + h_src.nbytes),
                    "d2h_bytes_per_step": int(prob.speed.nbytes)}
@@ -643,7 +644,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--schedule", type=int, default=0,
                     help="single grids: 1 = fast iterative method (Algorithm 3), 2 = "
-                         "topology-driven (Algorithm 4); 0: asynchronous tiles (Algorithm 6)")
+                         "topology-driven (Algorithm 4), 3 = fast sweeping (Algorithm 5); "
+                         "0: asynchronous tiles (Algorithm 6)")
     ap.add_argument("--update", type=int, default=0,
                     help="2D ablation: 1 = Algorithm 1 with d-tilde, 2 = with d-hat (0: d-bar)")
     ap.add_argument("--autotune", action="store_true",

@@ -101,9 +101,11 @@ typedef struct {
     int schedule;          /* 0 = asynchronous bucketed tiles (Algorithm 6), the default;
                               single problems only, device pointers, for comparison:
                               1 = fast iterative method (Algorithm 3, epsilon = 0, rounds),
-                              2 = topology-driven (Algorithm 4, every cell every iteration).
-                              Same bits (Theorem 1), different work and time.  Options other
-                              than timeout_ms and counters do not apply to 1 and 2. */
+                              2 = topology-driven (Algorithm 4, every cell every iteration),
+                              3 = fast sweeping method (Algorithm 5, 2^ndim sweep directions,
+                              each sweep in hyperplane order).  Same bits (Theorem 1),
+                              different work and time.  Options other than timeout_ms and
+                              counters do not apply to 1-3. */
     int reserved;          /* keep 0 */
 } eik_opts;
 

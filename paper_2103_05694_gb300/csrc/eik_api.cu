@@ -327,17 +327,18 @@ eik_status ensure_device() {
   return EIK_OK;
 }
 
-// A single problem with one of the comparison schedules (Algorithm 3 or 4).
+// A single problem with one of the comparison schedules (Algorithm 3, 4 or 5).
 eik_status run_schedule(HostProblem &hp, const eik_opts *opts, eik_stats *stats,
                         cudaStream_t stream) {
   const int schedule = opts->schedule;
-  if (schedule != eik::kScheduleFim && schedule != eik::kScheduleTopo) {
-    set_err("opts.schedule must be 0, 1 or 2");
+  if (schedule != eik::kScheduleFim && schedule != eik::kScheduleTopo &&
+      schedule != eik::kScheduleFsm) {
+    set_err("opts.schedule must be 0, 1, 2 or 3");
     return EIK_EINVAL;
   }
-  if (!hp.speed_dev || !hp.out_dev) { set_err("opts.schedule 1, 2 take device pointers only"); return EIK_EINVAL; }
+  if (!hp.speed_dev || !hp.out_dev) { set_err("opts.schedule 1-3 take device pointers only"); return EIK_EINVAL; }
   if (opts->update != 0 || opts->arith == 2) {
-    set_err("opts.schedule 1, 2 run the exact update on the FP64 unit only");
+    set_err("opts.schedule 1-3 run the exact update on the FP64 unit only");
     return EIK_EINVAL;
   }
   {
@@ -446,7 +447,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     if (hp.ndim != ndim) { set_err("all problems of a batch must have the same ndim"); return EIK_EINVAL; }
   }
   if (opts && opts->schedule != 0) {
-    if (hps.size() != 1) { set_err("opts.schedule 1, 2 solve single problems only"); return EIK_EINVAL; }
+    if (hps.size() != 1) { set_err("opts.schedule 1-3 solve single problems only"); return EIK_EINVAL; }
     return run_schedule(hps[0], opts, stats, stream);
   }
   int64_t tx, ty, tz;

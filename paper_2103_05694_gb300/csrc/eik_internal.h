@@ -160,10 +160,10 @@ unsigned long long kernel_launches();
 int persistent_blocks_per_sm(int ndim, int arith, int tile_shape);
 
 // Other schedules of the same update (eik_schedules.cu): opts.schedule.
-constexpr int kScheduleAmm = 0, kScheduleFim = 1, kScheduleTopo = 2;
+constexpr int kScheduleAmm = 0, kScheduleFim = 1, kScheduleTopo = 2, kScheduleFsm = 3;
 
 struct BspCtl {
-  unsigned long long nfront[3];   // worklist sizes (FIM) / changes per iteration (topology)
+  unsigned long long nfront[3];   // worklist sizes (FIM) / changes per iteration (topology, FSM)
   unsigned long long pad0[13];
   unsigned bar_count, bar_gen;
   unsigned pad1[30];

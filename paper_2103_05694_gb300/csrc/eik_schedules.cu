@@ -10,6 +10,11 @@
 //    ones that decreased onto w'; a cell that decreased is pushed onto w'.
 //  * Topology-driven schedule, Algorithm 4: every cell is updated in every
 //    iteration until an iteration changes nothing.
+//  * Fast sweeping method, Algorithm 5: sweeps in the 2^D axis directions,
+//    each sweep's cells in hyperplane order (the cells of one hyperplane
+//    x' + y' (+ z') = k in sweep coordinates are independent and run in
+//    parallel; hyperplanes follow one another), until a full set of sweeps
+//    changes nothing.
 //
 // One cooperative persistent launch per solve; rounds are separated by a grid
 // barrier bounded by %globaltimer.  One thread per cell update, no tiles: the
@@ -169,6 +174,55 @@ __global__ void topo_kernel(BspParams p) {
   add_counts(p.ctl, evals, decs);
 }
 
+template <int D>
+__global__ void fsm_kernel(BspParams p) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t gtid = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t nx = p.nx, ny = p.ny, nz = D == 3 ? p.nz : 1;
+  const int64_t planes = nx + ny + nz - 2;
+  unsigned long long evals = 0, decs = 0;
+  for (unsigned it = 0;; ++it) {
+    if (gtid == 0) p.ctl->nfront[(it + 1u) % 3u] = 0ull;   // change count of the next iteration
+    unsigned long long changed = 0;
+    bool ok = true;
+    for (int d = 0; d < (1 << D) && ok; ++d) {
+      for (int64_t k = 0; k < planes; ++k) {
+        if (D == 2) {
+          const int64_t lo = k - (ny - 1) > 0 ? k - (ny - 1) : 0;
+          const int64_t hi = k < nx - 1 ? k : nx - 1;
+          for (int64_t xs = lo + gtid; xs <= hi; xs += stride) {
+            const int64_t ys = k - xs;
+            const int64_t x = (d & 1) ? nx - 1 - xs : xs, y = (d & 2) ? ny - 1 - ys : ys;
+            changed += update_cell<D>(p, y * nx + x, evals, decs) ? 1u : 0u;
+          }
+        } else {
+          for (int64_t q = gtid; q < nx * ny; q += stride) {
+            const int64_t xs = q % nx, ys = q / nx, zs = k - xs - ys;
+            if (zs < 0 || zs >= nz) continue;
+            const int64_t x = (d & 1) ? nx - 1 - xs : xs, y = (d & 2) ? ny - 1 - ys : ys;
+            const int64_t z = (d & 4) ? nz - 1 - zs : zs;
+            changed += update_cell<D>(p, (z * ny + y) * nx + x, evals, decs) ? 1u : 0u;
+          }
+        }
+        if (!grid::barrier(&p.ctl->bar_count, &p.ctl->bar_gen, &p.ctl->status, p.timeout_ns)) {
+          ok = false;
+          break;
+        }
+      }
+    }
+    if (!ok) break;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) changed += __shfl_xor_sync(kFullMask, changed, o);
+    if ((threadIdx.x & 31) == 0 && changed) atomicAdd(&p.ctl->nfront[it % 3u], changed);
+    if (!grid::barrier(&p.ctl->bar_count, &p.ctl->bar_gen, &p.ctl->status, p.timeout_ns)) break;
+    if (ld_rlx_u64(&p.ctl->nfront[it % 3u]) == 0) {
+      if (gtid == 0) p.ctl->rounds = it + 1u;
+      break;
+    }
+  }
+  add_counts(p.ctl, evals, decs);
+}
+
 int sm_count() {
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
@@ -177,11 +231,11 @@ int sm_count() {
 }
 
 template <typename K>
-cudaError_t launch_coop(K kernel, BspParams &p, cudaStream_t stream) {
+cudaError_t launch_coop(K kernel, BspParams &p, cudaStream_t stream, int max_per_sm = 4) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
   if (e != cudaSuccess) return e;
-  if (per_sm > 4) per_sm = 4;
+  if (per_sm > max_per_sm) per_sm = max_per_sm;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   void *args[] = {&p};
   e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kernel), dim3(sm_count() * per_sm),
@@ -207,6 +261,8 @@ cudaError_t launch_schedule(int schedule, BspParams p, cudaStream_t stream) {
     return p.ndim == 3 ? launch_coop(fim_kernel<3>, p, stream) : launch_coop(fim_kernel<2>, p, stream);
   if (schedule == kScheduleTopo)
     return p.ndim == 3 ? launch_coop(topo_kernel<3>, p, stream) : launch_coop(topo_kernel<2>, p, stream);
+  if (schedule == kScheduleFsm)   // short hyperplanes, many barriers: one block per SM
+    return p.ndim == 3 ? launch_coop(fsm_kernel<3>, p, stream, 1) : launch_coop(fsm_kernel<2>, p, stream, 1);
   return cudaErrorInvalidValue;
 }
 

@@ -1,6 +1,7 @@
 """The comparison schedules of the same exact update (opts.schedule: the fast
-iterative method, Algorithm 3 with epsilon = 0, and the topology-driven
-schedule, Algorithm 4) reach the oracle's fixed point bit for bit (Theorem 1);
+iterative method, Algorithm 3 with epsilon = 0, the topology-driven schedule,
+Algorithm 4, and the fast sweeping method, Algorithm 5) reach the oracle's
+fixed point bit for bit (Theorem 1);
 their work counters are consistent; misuse is EIK_EINVAL."""
 import numpy as np
 import pytest
@@ -33,7 +34,7 @@ def _solve(p, opts):
     return r.t.cpu().numpy(), r.stats
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 @pytest.mark.parametrize("shape", [(1, 1), (1, 50), (37, 45), (120, 90), (5, 5, 5), (17, 9, 23)])
 def test_schedules_bit_exact(schedule, shape):
     p = synth.random_problem(900 + len(shape) + shape[-1], shape, n_src=2, contrast=8.0,
@@ -47,7 +48,7 @@ def test_schedules_bit_exact(schedule, shape):
     assert st["rounds"] >= 1
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 def test_schedules_on_the_layered_section_quarter(schedule):
     nx, nz = 575, 188
     speed = synth.layered_section(nx, nz, 4.0, seed=2)
@@ -62,7 +63,7 @@ def test_schedules_on_the_layered_section_quarter(schedule):
 
 def test_schedule_misuse_is_einval():
     speed = torch.ones((10, 12), dtype=torch.float64, device=DEV)
-    for opts in ({"schedule": 3}, {"schedule": 1, "update": 1}, {"schedule": 2, "arith": 2}):
+    for opts in ({"schedule": 4}, {"schedule": 1, "update": 1}, {"schedule": 2, "arith": 2}):
         with pytest.raises(eik.EikError) as e:
             eik.solve(speed, 1.0, [0], opts=opts)
         assert e.value.status == eik.EIK_EINVAL
