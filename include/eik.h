@@ -165,16 +165,17 @@ typedef struct {
 eik_status eik_solve_batched(const eik_problem *probs, int nprob, const eik_opts *opts,
                              eik_stats *stats, void *stream);
 
-/* Self-test of the exact arithmetic.  The solver evaluates d-bar with exact
+/* Self-test of the exact arithmetic.  d-bar can be evaluated with exact
  * round-to-nearest binary64 operations emulated on the integer pipes (FP64 is
- * scarce on GB300); this runs n random and tie-heavy trials on the current
- * device, comparing each emulated result with the hardware FP64 unit (and
- * d-bar with a plain bisection over G built from the hardware operations), bit
- * for bit, and the solver's lane-group update (FP64 guess + one G pass over a
- * window of points) against the same reference.  mismatches[32] receives:
- * [0] x-y, [1] m*m, [2] x+y, [3] G 2D, [4] G 3D, [5] d-bar 2D, [6] d-bar 3D,
- * [7] lane-group update 2D x8, [8] 3D x8, [9] 2D x4 mismatch counts,
- * [10] trials run, [16 + k] the first failing trial of check k (-1 if none).
+ * scarce on GB300, opts.arith = 2) or on the FP64 unit (the default, with a
+ * float-float starting point and an exact test); this runs n random and
+ * tie-heavy trials on the current device, comparing each emulated operation
+ * with the hardware FP64 unit, and each d-bar with a plain bisection over G
+ * built from the hardware operations, bit for bit.  mismatches[32] receives:
+ * [0] x-y, [1] m*m, [2] x+y, [3] G 2D, [4] G 3D, [5] integer d-bar 2D,
+ * [6] integer d-bar 3D, [7] lane-group update 2D x8, [8] 3D x8, [9] 2D x4,
+ * [10] FP64-unit d-bar 2D, [11] FP64-unit d-bar 3D mismatch counts,
+ * [15] trials run, [16 + k] the first failing trial of check k (-1 if none).
  * Allocates and frees a small device buffer; synchronises `stream`. */
 eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches, void *stream);
 

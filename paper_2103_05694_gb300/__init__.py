@@ -152,18 +152,19 @@ EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "
             "eik_kernel_launches", "eik_autotune", "eik_eval_update", "eik_residual"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3", "group2x8", "group3x8",
-                   "group2x4"]
+                   "group2x4", "dbar2_fp64", "dbar3_fp64"]
 
 
 def eik_selftest(n: int = 1 << 20, seed: int = 1, stream=None) -> dict:
-    """Bit-exact check of the integer-pipe arithmetic against the FP64 unit."""
+    """Bit-exact check of the integer-pipe arithmetic against the FP64 unit, and
+    of both d-bar paths against a bisection over the hardware G."""
     L = load_library()
     out = (ctypes.c_int64 * 32)()
     rc = L.eik_selftest(int(n), int(seed) & ((1 << 64) - 1), out, _stream_handle(stream))
     if rc != EIK_OK:
         raise EikError(rc, "selftest failed to run")
     res = {k: int(out[i]) for i, k in enumerate(SELFTEST_CHECKS)}
-    res["trials"] = int(out[10])
+    res["trials"] = int(out[15])
     res["first"] = {k: int(out[16 + i]) for i, k in enumerate(SELFTEST_CHECKS)}
     return res
 

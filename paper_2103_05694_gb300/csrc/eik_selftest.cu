@@ -106,7 +106,7 @@ __global__ void selftest_kernel(int64_t n, unsigned long long seed, unsigned lon
     const bool live = i < n;
     const unsigned long long h0 = mix(seed ^ mix(static_cast<unsigned long long>(i)));
     const unsigned long long h1 = mix(h0), h2 = mix(h1), h3 = mix(h2), h4 = mix(h3), h5 = mix(h4);
-    unsigned long long nb[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long nb[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     // sub and add: x >= y > 0 with exponent gaps 0..70
     {
       unsigned long long x = rand_double(h1, 900, 250);
@@ -147,19 +147,21 @@ __global__ void selftest_kernel(int64_t n, unsigned long long seed, unsigned lon
       if (xf::G<3>(tau, a3) != G_hw<3>(tau, a3)) nb[4] = 1;
       if (xf::dbar<2>(a2, cb) != dbar_ref<2>(a2, cb)) nb[5] = 1;
       if (xf::dbar<3>(a3, cb) != dbar_ref<3>(a3, cb)) nb[6] = 1;
+      if (hw::dbar<2>(a2, cb) != dbar_ref<2>(a2, cb)) nb[10] = 1;
+      if (hw::dbar<3>(a3, cb) != dbar_ref<3>(a3, cb)) nb[11] = 1;
       const unsigned long long hg = mix(h5 ^ 3);
       if (!group_ok<2, 8>(a2, cb, hg)) nb[7] = 1;
       if (!group_ok<3, 8>(a3, cb, hg)) nb[8] = 1;
       if (!group_ok<2, 4>(a2, cb, hg ^ 1)) nb[9] = 1;
     }
-    for (int k = 0; k < 10; ++k) {
+    for (int k = 0; k < 12; ++k) {
       if (live && nb[k]) {
         atomicAdd(&bad[k], 1ull);
         atomicCAS(&first[k], ~0ull, static_cast<unsigned long long>(i));
       }
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&bad[10], static_cast<unsigned long long>(n));
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&bad[15], static_cast<unsigned long long>(n));
 }
 
 }  // namespace
