@@ -370,8 +370,14 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 // + 1) * delta are deferred: recorded in the tile's pending mask and the tile
 // re-queued at their bucket.  Only accepted values are written to memory.
 // ---------------------------------------------------------------------------
+// Register budget: at least this many 256-thread CTAs per SM (scaled for
+// other tile sizes).
+#ifndef EIK_MIN_CTAS_256
+#define EIK_MIN_CTAS_256 2
+#endif
 template <int D, int TX, int TY, int TZ, int ARITH>
-__global__ void __launch_bounds__(TX * TY * TZ, 512 / (TX * TY * TZ)) persistent_kernel(SolveParams p) {
+__global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * TY * TZ))
+    persistent_kernel(SolveParams p) {
   constexpr int NT = TX * TY * TZ;
   static_assert(NT % 32 == 0 && NT <= 32 * kPendWords, "whole warps, one pending bit per cell");
   constexpr int HZ = (D == 3) ? 1 : 0;
