@@ -217,7 +217,7 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
  * Every operation is separately rounded in that order, so results are
  * reproducible bit for bit.  Device pointers only.  A parallel set-up pass
  * evaluates every weight; then one cooperative launch processes the cells in
- * dependency order, its blocks meeting at a grid barrier between frontiers
+ * dependency order, its blocks meeting at a grid barrier between levels
  * (the wait is bounded by opts->timeout_ms: EIK_ETIMEOUT).  Workspace: about
  * 53 bytes per cell of the batch, kept for the next call (eik_release frees
  * it).  Synchronises `stream`.  stats (optional): good = cells processed,

@@ -1292,6 +1292,7 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
   std::lock_guard<std::mutex> lk(g_mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (nprob <= 0 || !probs || !dL_dslowness) { set_err("bad adjoint arguments"); return EIK_EINVAL; }
+  if (nprob >= (1 << 23)) { set_err("adjoint: too many problems"); return EIK_EINVAL; }
   std::vector<HostProblem> hps((size_t)nprob);
   int64_t total = 0, total_src = 0;
   for (int i = 0; i < nprob; ++i) {
