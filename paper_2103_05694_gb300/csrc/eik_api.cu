@@ -38,8 +38,8 @@ constexpr uint64_t kMaxCapEntries = uint64_t(1) << 30;   // whole ring storage l
 // window in buckets, in-tile acceptance band, persistent CTAs per SM.
 // Defaults per dimension (2D, 3D), from sweeps over the 2D layered, constant
 // and tomography workloads and the 3D checkerboard and batched workloads.
-constexpr double kDefaultKDelta[2] = {16.0, 4.0};
-constexpr int kDefaultWindow[2] = {8, 16};
+constexpr double kDefaultKDelta[2] = {16.0, 2.0};
+constexpr int kDefaultWindow[2] = {16, 16};
 constexpr double kDefaultBand[2] = {16.0, 8.0};
 constexpr int kDefaultCtasPerSm[2] = {1, 2};
 constexpr int kMaxRetries = 4;

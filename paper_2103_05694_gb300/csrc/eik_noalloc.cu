@@ -240,13 +240,13 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
   sp.timeout_ns = (opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000) * 1000000ll;
   sp.counters = opts ? opts->counters : 0;
   sp.test_stall = 0;
-  sp.window = static_cast<unsigned>(opts && opts->window > 0 ? opts->window : (ndim == 3 ? 16 : 8));
+  sp.window = static_cast<unsigned>(opts && opts->window > 0 ? opts->window : 16);
   sp.band = opts && opts->band > 0 ? opts->band : (ndim == 3 ? 8.0 : 16.0);
   sp.arith = opts && opts->arith == 2 ? kArithInt : kArithFp64;
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
   sp.trace = nullptr;
   sp.trace_cap = 0;
-  const double k_delta = opts && opts->k_delta > 0 ? opts->k_delta : (ndim == 3 ? 4.0 : 16.0);
+  const double k_delta = opts && opts->k_delta > 0 ? opts->k_delta : (ndim == 3 ? 2.0 : 16.0);
   const double delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
   if (launch_seed(sp, reinterpret_cast<const SeedItem *>(base + na::kOffSeeds), nsrc, k_delta,
                   delta_fixed, s) != cudaSuccess) {
