@@ -65,13 +65,15 @@ typedef enum {
     EIK_ECUDA = 5       /* a CUDA runtime call failed (message: eik_last_error()) */
 } eik_status;
 
-/* Tuning knobs.  Zero (or a NULL pointer) selects the default / autotuned value. */
+/* Tuning knobs.  Zero (or a NULL pointer) selects the default; eik_autotune picks
+ * them for a given batch.  Defaults: 2D k_delta 16, window 16, band 16, 1 CTA per SM
+ * (2 when the batch has >= 8 sources); 3D k_delta 2, window 16, band 8, 2 CTAs per SM. */
 typedef struct {
     double delta;          /* bucket width in time units; <= 0: auto (k_delta * mean h/v) */
     double k_delta;        /* auto bucket width in cell travel times; <= 0: default */
     int64_t capacity;      /* initial frontier ring capacity per bucket slot; 0: auto */
     int64_t timeout_ms;    /* limit of any single device wait; 0: 60000 */
-    int ctas_per_sm;       /* persistent CTAs per SM; 0: occupancy-derived default */
+    int ctas_per_sm;       /* persistent CTAs per SM (capped by occupancy); 0: default */
     int counters;          /* nonzero: collect eik_stats counters (small cost) */
     int test_stall;        /* testing aid, keep 0: the solve first waits on a device flag
                               that nothing sets, so the wait reaches timeout_ms and the
@@ -83,7 +85,10 @@ typedef struct {
     int arith;             /* arithmetic of d-bar: 1 = FP64 unit, 2 = exact emulation on the
                               integer pipes (same results bit for bit); 0: default */
     int sched_flags;       /* bit 0: the look-ahead window follows the lowest bucket holding
-                              queued entries only (tiles still running do not hold it) */
+                              queued entries only (tiles still running do not hold it);
+                              bits 1-2: lane-group d-bar, 0 = automatic (when the batch has
+                              fewer than 8 tiles per persistent CTA), 1 = never, 2 = for
+                              lists of up to a quarter of the tile, 3 = an eighth */
     void *trace;           /* optional device buffer of trace_cap 32-byte visit records
                               {int64 t_claim_ns, t_end_ns; uint32 tile, lowest bucket,
                               rounds, flags}; NULL: no trace */
