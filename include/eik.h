@@ -88,7 +88,10 @@ typedef struct {
                               queued entries only (tiles still running do not hold it);
                               bits 1-2: lane-group d-bar, 0 = automatic (when the batch has
                               fewer than 8 tiles per persistent CTA), 1 = never, 2 = for
-                              lists of up to a quarter of the tile, 3 = an eighth */
+                              lists of up to a quarter of the tile, 3 = an eighth;
+                              bits 3-4 (eik_adjoint only): schedule, 0 = default (tiles when
+                              every problem has the same ndim, else levels), 1 = levels,
+                              2 = tiles */
     void *trace;           /* optional device buffer of trace_cap 32-byte visit records
                               {int64 t_claim_ns, t_end_ns; uint32 tile, lowest bucket,
                               rounds, flags}; NULL: no trace */
@@ -221,13 +224,23 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
  *   the order x-, x+, y-, y+, z-, z+;  dL/ds_n = lambda_n (h^2 s_n) / S_n.
  * Every operation is separately rounded in that order, so results are
  * reproducible bit for bit.  Device pointers only.  A parallel set-up pass
- * evaluates every weight; then one cooperative launch processes the cells in
- * dependency order, its blocks meeting at a grid barrier between levels
- * (the wait is bounded by opts->timeout_ms: EIK_ETIMEOUT).  Workspace: about
- * 53 bytes per cell of the batch, kept for the next call (eik_release frees
- * it).  Synchronises `stream`.  stats (optional): good = cells processed,
- * visits = reached cells, rounds = frontiers, solve_ms = device time of the
- * adjoint launches. */
+ * evaluates every weight; then the cells are processed in dependency order by
+ * one of two schedules (opts->sched_flags bits 3-4), with the same results:
+ *   tiles (default): persistent CTAs take tiles of 16x16 (2D) or 8x8x4 (3D)
+ *     cells from a queue and run the dependency order inside a tile in shared
+ *     memory; a tile is queued when a cell of it may have become ready;
+ *   levels: one cooperative launch processes the cells level by level, its
+ *     blocks meeting at a grid barrier between levels.
+ * Every device wait is bounded by opts->timeout_ms (EIK_ETIMEOUT); opts->
+ * ctas_per_sm caps the CTAs of the tile schedule.  Workspace: about 34 (tiles)
+ * or 53 (levels) bytes per cell of the batch, kept for the next call
+ * (eik_release frees it).
+ * Synchronises `stream`.  stats (optional): good = cells processed, evals =
+ * reached cells, solve_ms = device time of the adjoint launches; tiles: visits
+ * = tile visits, rounds = in-tile rounds summed over visits, visit_ns /
+ * idle_ns = CTA time in visits / waiting for a tile, ctas, detail[0..3] = SM
+ * cycles (thread 0 of each CTA, summed) waiting, loading, in rounds, storing;
+ * levels: rounds = levels. */
 eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
                        double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,
                        void *stream);

@@ -423,6 +423,12 @@ class Plan:
             pass
 
 
+# eik_adjoint schedule (opts["sched_flags"] bits 3-4): cells level by level
+# between grid barriers, or tiles in shared memory handed over through a queue
+ADJ_LEVELS = 1 << 3
+ADJ_TILES = 2 << 3
+
+
 def eik_adjoint(problems: list[dict], dL_dt: list, dL_ds: list, opts: dict | None = None,
                 stream=None) -> dict:
     """d(loss)/d(slowness) through the solved fields ``problems[i]["out"]``.

@@ -38,6 +38,8 @@ constexpr uint64_t kMaxCapEntries = uint64_t(1) << 30;   // whole ring storage l
 // window in buckets, in-tile acceptance band, persistent CTAs per SM.
 // Defaults per dimension (2D, 3D), from sweeps over the 2D layered, constant
 // and tomography workloads and the 3D checkerboard and batched workloads.
+// adjoint schedule by default: the tile schedule (else level-synchronous)
+constexpr bool kAdjTilesDefault = true;
 constexpr double kDefaultKDelta[2] = {16.0, 2.0};
 constexpr int kDefaultWindow[2] = {16, 16};
 constexpr double kDefaultBand[2] = {16.0, 8.0};
@@ -105,10 +107,11 @@ Workspace g_ws;
 
 struct AdjWorkspace {
   int device = -1;
-  DevBuf<int> cnt;
+  DevBuf<int> cnt, cnt_out;
   DevBuf<double> W, lam;
-  DevBuf<unsigned char> mask;
-  DevBuf<unsigned long long> front;
+  DevBuf<unsigned char> mask, status;
+  DevBuf<unsigned long long> front, ring;
+  DevBuf<unsigned> tile_state;
   DevBuf<eik::AdjProb> probs;
   DevBuf<eik::AdjCtl> ctl;
   DevBuf<int64_t> src;
@@ -116,7 +119,8 @@ struct AdjWorkspace {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   void release_all() {
-    cnt.release(); W.release(); lam.release(); mask.release(); front.release();
+    cnt.release(); cnt_out.release(); W.release(); lam.release(); mask.release();
+    status.release(); front.release(); ring.release(); tile_state.release();
     probs.release(); ctl.release(); src.release();
     if (ctl_host) cudaFreeHost(ctl_host);
     ctl_host = nullptr;
@@ -1017,7 +1021,7 @@ const char *eik_status_str(eik_status s) {
 
 const char *eik_last_error(void) { return g_err; }
 
-int eik_abi_version(void) { return 104; }
+int eik_abi_version(void) { return 105; }
 
 uint64_t eik_kernel_launches(void) { return (uint64_t)eik::kernel_launches(); }
 
@@ -1316,26 +1320,62 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
       g_adj.device = dev;
     }
   }
+  // schedule: sched_flags bits 3-4, 1 = levels, 2 = tiles, 0 = default (tiles
+  // when every problem has the same ndim)
+  const int adj_mode = opts ? (opts->sched_flags >> 3) & 3 : 0;
+  if (adj_mode == 3) { set_err("adjoint: bad schedule flags"); return EIK_EINVAL; }
+  bool same_ndim = true;
+  for (int i = 1; i < nprob; ++i) same_ndim = same_ndim && hps[(size_t)i].ndim == hps[0].ndim;
+  if (adj_mode == 2 && !same_ndim) {
+    set_err("adjoint: the tile schedule needs one ndim per batch");
+    return EIK_EINVAL;
+  }
+  const bool tiles = adj_mode == 2 || (adj_mode == 0 && same_ndim && kAdjTilesDefault);
+  const int *tsh = hps[0].ndim == 3 ? eik::kAdjTile3 : eik::kAdjTile2;
+  int64_t total_tiles = 0;
+  std::vector<int64_t> ntile((size_t)nprob * 3);
+  for (int i = 0; i < nprob; ++i) {
+    const HostProblem &hp = hps[(size_t)i];
+    const int64_t ext[3] = {hp.dims[2], hp.dims[1], hp.dims[0]};   // x, y, z
+    for (int k = 0; k < 3; ++k) ntile[(size_t)i * 3 + k] = (ext[k] + tsh[k] - 1) / tsh[k];
+    total_tiles += ntile[(size_t)i * 3] * ntile[(size_t)i * 3 + 1] * ntile[(size_t)i * 3 + 2];
+  }
+  if (tiles && total_tiles >= (int64_t(1) << 31)) { set_err("adjoint: too many tiles"); return EIK_EINVAL; }
+  const uint64_t qcap = next_pow2((uint64_t)std::max<int64_t>(total_tiles, 2));
   if (!g_adj.ctl_host) CK(cudaMallocHost(&g_adj.ctl_host, sizeof(eik::AdjCtl)), "adjoint: pinned");
   CK(g_adj.cnt.ensure((size_t)total), "adjoint: alloc counts");
+  if (tiles) {
+    CK(g_adj.cnt_out.ensure((size_t)total), "adjoint: alloc counts");
+    CK(g_adj.status.ensure((size_t)total), "adjoint: alloc status");
+    CK(g_adj.tile_state.ensure((size_t)total_tiles), "adjoint: alloc tile states");
+    CK(g_adj.ring.ensure((size_t)qcap), "adjoint: alloc tile queue");
+  } else {
+    CK(g_adj.front.ensure((size_t)total * 2), "adjoint: alloc frontiers");
+  }
   CK(g_adj.W.ensure((size_t)total * 3), "adjoint: alloc weights");
   CK(g_adj.mask.ensure((size_t)total), "adjoint: alloc masks");
-  CK(g_adj.lam.ensure((size_t)total), "adjoint: alloc lambda");
-  CK(g_adj.front.ensure((size_t)total * 2), "adjoint: alloc frontiers");
+  if (!tiles) CK(g_adj.lam.ensure((size_t)total), "adjoint: alloc lambda");
   CK(g_adj.probs.ensure((size_t)nprob), "adjoint: alloc problems");
   CK(g_adj.ctl.ensure(1), "adjoint: alloc control");
   CK(g_adj.src.ensure((size_t)std::max<int64_t>(total_src, 1)), "adjoint: alloc sources");
   std::vector<eik::AdjProb> ap((size_t)nprob);
   std::vector<int64_t> all_src;
-  int64_t base = 0;
+  int64_t base = 0, tile_base = 0;
   for (int i = 0; i < nprob; ++i) {
     const HostProblem &hp = hps[(size_t)i];
     eik::AdjProb &A = ap[(size_t)i];
+    A.cnt_out = tiles ? g_adj.cnt_out.p + base : nullptr;
+    A.status = tiles ? g_adj.status.p + base : nullptr;
+    A.ntx = ntile[(size_t)i * 3];
+    A.nty = ntile[(size_t)i * 3 + 1];
+    A.ntz = ntile[(size_t)i * 3 + 2];
+    A.tile_base = tile_base;
+    tile_base += A.ntx * A.nty * A.ntz;
     A.t = hp.out;
     A.v = hp.speed;
     A.g = dL_dt ? dL_dt[i] : nullptr;
     A.grad = dL_dslowness[i];
-    A.lam = g_adj.lam.p + base;
+    A.lam = tiles ? nullptr : g_adj.lam.p + base;
     for (int k = 0; k < 3; ++k) A.W[k] = g_adj.W.p + (size_t)k * (size_t)total + base;
     A.mask = g_adj.mask.p + base;
     A.cnt = g_adj.cnt.p + base;
@@ -1356,6 +1396,11 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
   CK(cudaMemcpyAsync(g_adj.probs.p, ap.data(), ap.size() * sizeof(eik::AdjProb),
                      cudaMemcpyHostToDevice, s), "adjoint: upload problems");
   CK(cudaMemsetAsync(g_adj.cnt.p, 0, (size_t)total * sizeof(int), s), "adjoint: clear counts");
+  if (tiles) {
+    CK(cudaMemsetAsync(g_adj.cnt_out.p, 0, (size_t)total * sizeof(int), s), "adjoint: clear counts");
+    CK(cudaMemsetAsync(g_adj.tile_state.p, 0, (size_t)total_tiles * sizeof(unsigned), s),
+       "adjoint: clear tile states");
+  }
   CK(cudaMemsetAsync(g_adj.ctl.p, 0, sizeof(eik::AdjCtl), s), "adjoint: clear control");
   const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
   if (!g_adj.ev0) {
@@ -1363,8 +1408,14 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
     CK(cudaEventCreate(&g_adj.ev1), "adjoint: event");
   }
   CK(cudaEventRecord(g_adj.ev0, s), "adjoint: event record");
-  CK(eik::launch_adjoint(g_adj.probs.p, nprob, total, g_adj.ctl.p, g_adj.front.p,
-                         tmo_ms * 1000000ll, s), "adjoint launch");
+  if (tiles)
+    CK(eik::launch_adjoint_tiles(g_adj.probs.p, nprob, total, total_tiles, hps[0].ndim, g_adj.ctl.p,
+                                 g_adj.tile_state.p, g_adj.ring.p, qcap,
+                                 opts ? opts->ctas_per_sm : 0, tmo_ms * 1000000ll, s),
+       "adjoint launch");
+  else
+    CK(eik::launch_adjoint(g_adj.probs.p, nprob, total, g_adj.ctl.p, g_adj.front.p,
+                           tmo_ms * 1000000ll, s), "adjoint launch");
   CK(cudaEventRecord(g_adj.ev1, s), "adjoint: event record");
   CK(cudaMemcpyAsync(g_adj.ctl_host, g_adj.ctl.p, sizeof(eik::AdjCtl), cudaMemcpyDeviceToHost, s),
      "adjoint: read status");
@@ -1373,8 +1424,13 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->good = (int64_t)c.done;
-    stats->visits = (int64_t)c.reached;
-    stats->rounds = (int64_t)c.levels;
+    stats->evals = (int64_t)c.reached;
+    stats->visits = (int64_t)c.visits;
+    stats->rounds = tiles ? (int64_t)c.rounds : (int64_t)c.levels;
+    stats->visit_ns = (int64_t)c.visit_ns;
+    stats->idle_ns = (int64_t)c.idle_ns;
+    stats->ctas = (int64_t)c.ctas;
+    for (int i = 0; i < 4; ++i) stats->detail[i] = (int64_t)c.cycles[i];
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, g_adj.ev0, g_adj.ev1) == cudaSuccess) stats->solve_ms = ms;
   }

@@ -202,21 +202,27 @@ struct AdjProb {
   const double *v;          // speed
   const double *g;          // dL/dt (NULL: 0)
   double *grad;             // dL/ds output
-  double *lam;              // adjoint variable (workspace)
-  double *W[3];             // per axis: weight of the axis' upwind side(s) (workspace)
+  double *lam;              // adjoint variable (workspace; NULL in the tile schedule)
+  double *W[3];             // per axis: weight of the axis' upwind side(s) (workspace); in
+                            // the tile schedule lambda * weight once the cell is processed
   unsigned char *mask;      // upwind sides (bit 2k + side) of each cell (workspace)
-  int *cnt;                 // downwind users not yet processed (workspace)
+  int *cnt;                 // downwind users not yet processed (workspace); with tiles:
+                            // the users inside the cell's own tile
+  int *cnt_out;             // with tiles: the users in other tiles (workspace)
+  unsigned char *status;    // with tiles: 0 unreached, 1 pending, 2 processed (workspace)
   const int64_t *src_idx;   // sorted unique sources
   int64_t nsrc;
   int64_t nx, ny, nz;
   int ndim;
   int64_t base;             // first global cell index of this problem
   double hh;                // fl(h * h)
+  int64_t ntx, nty, ntz;    // tiles per axis (tile schedule)
+  int64_t tile_base;        // first global tile index of this problem
 };
 
-// Control block of the adjoint's level-synchronous schedule.  Frontier counts
+// Control block of the adjoint.  Level-synchronous schedule: frontier counts
 // rotate over three slots: level L reads slot L % 3, appends to (L + 1) % 3 and
-// clears (L + 2) % 3.
+// clears (L + 2) % 3.  Tile schedule: queue counters and visit statistics.
 struct AdjCtl {
   unsigned long long reached;        // cells with a finite time
   unsigned long long pad0[15];
@@ -229,6 +235,18 @@ struct AdjCtl {
   unsigned pad3[30];
   unsigned long long levels;
   unsigned status;
+  unsigned pad4[13];
+  unsigned long long head;           // tile schedule: queue tickets taken and pushed
+  unsigned long long pad5[15];
+  unsigned long long tail;
+  unsigned long long pad6[15];
+  unsigned long long visits;         // tile visits
+  unsigned long long rounds;         // rounds summed over tile visits
+  unsigned long long visit_ns;       // visit time summed over CTAs
+  unsigned long long idle_ns;        // time CTAs spent waiting for a tile
+  unsigned long long ctas;           // persistent CTAs of the tile launch
+  unsigned long long cycles[4];      // SM cycles of thread 0 per CTA: waiting for a tile,
+                                     // visit loads, rounds, stores and releases
 };
 
 // set-up (masks, weights, coefficients, counts), first frontier, and one
@@ -236,5 +254,17 @@ struct AdjCtl {
 // entries.
 cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, AdjCtl *ctl,
                            unsigned long long *front, long long timeout_ns, cudaStream_t stream);
+// The tile schedule: set-up with counts split by tile, the initial queue, and a
+// persistent launch that relaxes ready tiles in shared memory.  tile_state
+// holds total_tiles words, zero on entry; queue holds qcap slots (a power of two
+// >= total_tiles, set up by the launch).  ndim: of every problem (one tile shape
+// per launch).  The tiles are kAdjTile2 in 2D and kAdjTile3 in 3D.  ctas_per_sm
+// caps the persistent CTAs per SM (0: occupancy).
+constexpr int kAdjTile2[3] = {16, 16, 1};
+constexpr int kAdjTile3[3] = {8, 8, 4};
+cudaError_t launch_adjoint_tiles(const AdjProb *probs_dev, int nprob, int64_t total,
+                                 int64_t total_tiles, int ndim, AdjCtl *ctl, unsigned *tile_state,
+                                 unsigned long long *queue, unsigned long long qcap,
+                                 int ctas_per_sm, long long timeout_ns, cudaStream_t stream);
 
 }  // namespace eik

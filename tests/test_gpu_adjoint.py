@@ -24,14 +24,20 @@ def _built():
     eik.load_library()
 
 
-@pytest.mark.parametrize("shape", [(40, 70), (3, 300), (12, 15, 17)])
-def test_adjoint_bit_exact_vs_oracle(shape):
+SCHEDULES = {"levels": eik.ADJ_LEVELS, "tiles": eik.ADJ_TILES}
+
+
+@pytest.mark.parametrize("sched", sorted(SCHEDULES))
+@pytest.mark.parametrize("shape", [(40, 70), (3, 300), (12, 15, 17), (1, 1), (33, 1), (5, 9, 1),
+                                   (17, 16, 9)])
+def test_adjoint_bit_exact_vs_oracle(shape, sched):
     rng = np.random.Generator(np.random.PCG64(5))
     probs, ref = [], []
     base = synth.random_problem(21, shape, n_src=1, contrast=6.0, smooth_sigma=1.0, h=0.5)
     speed = torch.from_numpy(base.speed).to(DEV)
     for k in range(4):
-        src = rng.choice(base.speed.size, size=1 + k % 3, replace=False).astype(np.int64)
+        src = rng.choice(base.speed.size, size=min(1 + k % 3, base.speed.size),
+                         replace=False).astype(np.int64)
         t = oracle.fmm(base.speed, base.h, src).t
         g = np.where(rng.random(shape) < 0.05, rng.standard_normal(shape), 0.0)
         lam, gs = oracle.adjoint(base.speed, base.h, src, t, g)
@@ -40,12 +46,16 @@ def test_adjoint_bit_exact_vs_oracle(shape):
         probs.append(dict(speed=speed, h=base.h, sources=torch.from_numpy(src).to(DEV), out=out,
                           g=torch.from_numpy(g).to(DEV), grad=torch.full_like(out, np.nan)))
     st = eik.eik_adjoint([{k: p[k] for k in ("speed", "h", "sources", "out")} for p in probs],
-                         [p["g"] for p in probs], [p["grad"] for p in probs])
+                         [p["g"] for p in probs], [p["grad"] for p in probs],
+                         opts={"sched_flags": SCHEDULES[sched], "timeout_ms": 10000})
     torch.cuda.synchronize()
     for p, r in zip(probs, ref):
         got = p["grad"].cpu().numpy()
         assert np.array_equal(got.view(np.uint64), r.view(np.uint64))
-    assert st["good"] == st["visits"]
+    assert st["good"] == st["evals"] == sum(int(np.isfinite(p["out"].cpu().numpy()).sum())
+                                            for p in probs)
+    if sched == "tiles":
+        assert st["visits"] >= 1 and st["ctas"] >= 1
 
 
 def test_autograd_function_matches_oracle_adjoint():
@@ -69,7 +79,8 @@ def test_autograd_function_matches_oracle_adjoint():
     del speed
 
 
-def test_adjoint_bit_exact_vs_oracle_tomography_grid():
+@pytest.mark.parametrize("sched", sorted(SCHEDULES))
+def test_adjoint_bit_exact_vs_oracle_tomography_grid(sched):
     """The 1024^2 tomography layout, two surface sources in one batch: forward
     times and the adjoint gradient both equal the oracle's bit for bit."""
     cfg = synth.tomography_2d_1024()
@@ -89,7 +100,8 @@ def test_adjoint_bit_exact_vs_oracle_tomography_grid():
                           g=torch.from_numpy(g).to(DEV), grad=torch.full_like(out, np.nan)))
     eik.eik_solve_batched([{k: p[k] for k in ("speed", "h", "sources", "out")} for p in probs])
     eik.eik_adjoint([{k: p[k] for k in ("speed", "h", "sources", "out")} for p in probs],
-                    [p["g"] for p in probs], [p["grad"] for p in probs])
+                    [p["g"] for p in probs], [p["grad"] for p in probs],
+                    opts={"sched_flags": SCHEDULES[sched], "timeout_ms": 10000})
     torch.cuda.synchronize()
     for p, (t, gs) in zip(probs, ref):
         assert np.array_equal(p["out"].cpu().numpy().view(np.uint64), t.view(np.uint64))
