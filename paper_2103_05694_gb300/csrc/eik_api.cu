@@ -76,6 +76,7 @@ struct Workspace {
   DevBuf<unsigned char> tile_src;
   DevBuf<unsigned> pend;
   DevBuf<unsigned long long> slots;
+  DevBuf<unsigned> seq;
   DevBuf<int64_t> src_idx;
   DevBuf<double> src_t;
   DevBuf<SeedItem> seeds;
@@ -84,20 +85,18 @@ struct Workspace {
   DevBuf<unsigned long long> count;
   Ctl *ctl_host = nullptr;     // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  bool slots_dirty = true;
   uint64_t cap = 0;            // entries per slot
 
   void release_all() {
     r.release(); t_stage.release(); v_stage.release(); state.release(); tile_src.release();
     pend.release();
-    slots.release(); src_idx.release(); src_t.release(); seeds.release(); probs.release();
-    ctl.release(); count.release();
+    slots.release(); seq.release(); src_idx.release(); src_t.release(); seeds.release();
+    probs.release(); ctl.release(); count.release();
     if (ctl_host) cudaFreeHost(ctl_host);
     ctl_host = nullptr;
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     ev0 = ev1 = nullptr;
-    slots_dirty = true;
     cap = 0;
     device = -1;
   }
@@ -551,12 +550,10 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
                                                  : (uint64_t)total_tiles / 4 + 4096;
   want_cap = next_pow2(std::max<uint64_t>(want_cap, opts && opts->capacity > 0 ? 16 : 1024));
   while (want_cap * eik::kNumSlots > kMaxCapEntries && want_cap > 1024) want_cap >>= 1;
-  // the ring layout depends on cap; storage only grows.  A clean solve leaves
-  // every entry EMPTY, so changing cap needs no clearing unless dirty.
-  if (g_ws.slots.n < want_cap * eik::kNumSlots) {
-    CK(g_ws.slots.ensure((size_t)(want_cap * eik::kNumSlots)), "alloc frontier");
-    g_ws.slots_dirty = true;
-  }
+  // the ring layout depends on cap; storage only grows.  Entries need no
+  // clearing: the sequence words (zeroed below) say which positions hold one.
+  CK(g_ws.slots.ensure((size_t)(want_cap * eik::kNumSlots)), "alloc frontier");
+  CK(g_ws.seq.ensure((size_t)(want_cap * eik::kNumSlots)), "alloc frontier sequence");
   g_ws.cap = want_cap;
 
   // uploads
@@ -576,11 +573,8 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   CK(cudaMemsetAsync(g_ws.tile_src.p, 0, (size_t)total_tiles, stream), "clear tile flags");
   CK(cudaMemsetAsync(g_ws.pend.p, 0, (size_t)total_tiles * eik::kPendWords * sizeof(unsigned),
                      stream), "clear pending masks");
-  if (g_ws.slots_dirty) {
-    CK(cudaMemsetAsync(g_ws.slots.p, 0xff, g_ws.slots.n * sizeof(unsigned long long), stream),
-       "clear frontier");
-    g_ws.slots_dirty = false;
-  }
+  CK(cudaMemsetAsync(g_ws.seq.p, 0, (size_t)(want_cap * eik::kNumSlots) * sizeof(unsigned), stream),
+     "clear frontier sequence");
 
   // r = h / v (staging host speeds first)
   int64_t v_off = 0;
@@ -620,6 +614,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
                                                         : nullptr;
   sp.trace_cap = sp.trace ? (unsigned long long)opts->trace_cap : 0ull;
   sp.slots = g_ws.slots.p;
+  sp.seq = g_ws.seq.p;
   sp.cap_mask = (unsigned)(g_ws.cap - 1);
   sp.ctl = g_ws.ctl.p;
   const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
@@ -672,15 +667,15 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     if (status != eik::kEcapacity || attempt >= kMaxRetries ||
         g_ws.cap * 4 * eik::kNumSlots > kMaxCapEntries) break;
     // grow the frontier, clear the scheduler (keep delta) and resume
-    g_ws.slots_dirty = true;
     const uint64_t ncap = g_ws.cap * 4;
     CK(g_ws.slots.ensure((size_t)(ncap * eik::kNumSlots)), "grow frontier");
+    CK(g_ws.seq.ensure((size_t)(ncap * eik::kNumSlots)), "grow frontier sequence");
     g_ws.cap = ncap;
     sp.slots = g_ws.slots.p;
+    sp.seq = g_ws.seq.p;
     sp.cap_mask = (unsigned)(ncap - 1);
-    CK(cudaMemsetAsync(g_ws.slots.p, 0xff, g_ws.slots.n * sizeof(unsigned long long), stream),
-       "clear frontier");
-    g_ws.slots_dirty = false;
+    CK(cudaMemsetAsync(g_ws.seq.p, 0, (size_t)(ncap * eik::kNumSlots) * sizeof(unsigned), stream),
+       "clear frontier sequence");
     CK(cudaMemsetAsync(g_ws.ctl.p, 0, offsetof(Ctl, rsum), stream), "clear scheduler");
     CK(cudaMemsetAsync(&g_ws.ctl.p->stats[0], 0, sizeof(Ctl) - offsetof(Ctl, stats), stream),
        "clear counters");
@@ -690,7 +685,6 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     acc.retries++;
   }
   if (status != 0) {
-    g_ws.slots_dirty = true;
     const Ctl &c = *g_ws.ctl_host;
     if (status == eik::kEinval) {
       set_err("invalid input data (cell %llu: speed must be finite and > 0, h/v finite and > 0)",
@@ -1046,6 +1040,7 @@ struct eik_plan {
   DevBuf<unsigned char> tile_src;
   DevBuf<unsigned> pend;
   DevBuf<unsigned long long> slots;
+  DevBuf<unsigned> seq;
   DevBuf<int64_t> src_idx;
   DevBuf<double> src_t;
   DevBuf<SeedItem> seeds;
@@ -1060,7 +1055,7 @@ struct eik_plan {
 
   ~eik_plan() {
     c.release(); state.release(); tile_src.release(); pend.release(); slots.release();
-    src_idx.release(); src_t.release(); seeds.release(); probs_d.release(); ctl.release();
+    seq.release(); src_idx.release(); src_t.release(); seeds.release(); probs_d.release(); ctl.release();
     count.release();
     if (ctl_host) cudaFreeHost(ctl_host);
   }
@@ -1149,6 +1144,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   while (want_cap * eik::kNumSlots > kMaxCapEntries && want_cap > 1024) want_cap >>= 1;
   pl.cap = want_cap;
   CK(pl.slots.ensure((size_t)(want_cap * eik::kNumSlots)), "plan: alloc frontier");
+  CK(pl.seq.ensure((size_t)(want_cap * eik::kNumSlots)), "plan: alloc frontier sequence");
   if (!all_src.empty()) {
     CK(cudaMemcpyAsync(pl.src_idx.p, all_src.data(), all_src.size() * sizeof(int64_t),
                        cudaMemcpyHostToDevice, stream), "plan: upload sources");
@@ -1170,6 +1166,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   sp.tile_src = pl.tile_src.p;
   sp.pend = pl.pend.p;
   sp.slots = pl.slots.p;
+  sp.seq = pl.seq.p;
   sp.cap_mask = (unsigned)(pl.cap - 1);
   sp.ctl = pl.ctl.p;
   const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
@@ -1236,7 +1233,8 @@ eik_status eik_plan_enqueue(eik_plan *pl, void *stream) {
   CK(cudaMemsetAsync(pl->tile_src.p, 0, (size_t)pl->total_tiles, s), "clear tile flags");
   CK(cudaMemsetAsync(pl->pend.p, 0, (size_t)pl->total_tiles * eik::kPendWords * sizeof(unsigned), s),
      "clear pending masks");
-  CK(cudaMemsetAsync(pl->slots.p, 0xff, pl->slots.n * sizeof(unsigned long long), s), "clear frontier");
+  CK(cudaMemsetAsync(pl->seq.p, 0, (size_t)(pl->cap * eik::kNumSlots) * sizeof(unsigned), s),
+     "clear frontier sequence");
   for (size_t j = 0; j < pl->speeds.size(); ++j) {
     CK(eik::launch_init_c(pl->speeds[j], pl->speed_h[j], pl->c.p + pl->speed_off[j], pl->speed_n[j],
                           pl->ctl.p, s, pl->sp.update != 0), "init_c launch");

@@ -8,7 +8,11 @@
 namespace eik {
 
 // Bucket ring: NB slots; bucket b lives in slot b & (NB - 1).  Each slot is a
-// ring of `cap` 64-bit entries (cap a power of two), EMPTY when free.
+// ring of `cap` 64-bit entries (cap a power of two) with one sequence word per
+// position.  For the entry of index i (position i & (cap - 1)) the word reads
+// i & ~(cap - 1) while the position is free for it and that + 1 once the entry
+// is written; the entry's taker moves it on by cap (free for the next lap).
+// Sequence words are zero before every solve.
 constexpr uint32_t kNumSlots = 128;
 constexpr uint64_t kEmpty = ~0ull;
 constexpr uint32_t kMaxBucket = (1u << 30) - 1;
@@ -51,6 +55,9 @@ struct Ctl {
   unsigned push[kNumSlots * kCounterPad];
   unsigned pop[kNumSlots * kCounterPad];
   unsigned run[kNumSlots * kCounterPad];   // tiles claimed from the slot and still running
+  int avail[kNumSlots * kCounterPad];      // entries written and not yet reserved by a popper
+                                           // (may dip below 0 while a failed reservation
+                                           // is being undone)
 };
 
 // One grid of a (possibly batched) solve, as the kernels see it.
@@ -74,6 +81,7 @@ struct SolveParams {
   unsigned *pend;                 // per global tile, kPendWords words: cells deferred by
                                   // the last visit (to evaluate at the next one)
   unsigned long long *slots;      // kNumSlots * cap
+  unsigned *seq;                  // kNumSlots * cap sequence words (see the bucket ring)
   unsigned cap_mask;              // cap - 1
   Ctl *ctl;
   long long timeout_ns;

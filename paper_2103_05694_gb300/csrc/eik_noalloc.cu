@@ -38,7 +38,8 @@ constexpr size_t kOffState = up256(kOffC + sizeof(double) * kMaxCells);
 constexpr size_t kOffTileSrc = up256(kOffState + sizeof(unsigned long long) * kMaxTiles);
 constexpr size_t kOffPend = up256(kOffTileSrc + kMaxTiles);
 constexpr size_t kOffSlots = up256(kOffPend + sizeof(unsigned) * kPendWords * kMaxTiles);
-constexpr size_t kOffSrcIdx = up256(kOffSlots + sizeof(unsigned long long) * kNumSlots * kCap);
+constexpr size_t kOffSeq = up256(kOffSlots + sizeof(unsigned long long) * kNumSlots * kCap);
+constexpr size_t kOffSrcIdx = up256(kOffSeq + sizeof(unsigned) * kNumSlots * kCap);
 constexpr size_t kOffSrcT = up256(kOffSrcIdx + sizeof(int64_t) * kMaxSources);
 constexpr size_t kOffSeeds = up256(kOffSrcT + sizeof(double) * kMaxSources);
 constexpr size_t kBytes = up256(kOffSeeds + sizeof(SeedItem) * kMaxSources);
@@ -199,7 +200,7 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
       cudaMemsetAsync(base + na::kOffState, 0, sizeof(unsigned long long) * ntiles, s) != cudaSuccess ||
       cudaMemsetAsync(base + na::kOffTileSrc, 0, ntiles, s) != cudaSuccess ||
       cudaMemsetAsync(base + na::kOffPend, 0, sizeof(unsigned) * kPendWords * ntiles, s) != cudaSuccess ||
-      cudaMemsetAsync(base + na::kOffSlots, 0xff, sizeof(unsigned long long) * kNumSlots * na::kCap, s) !=
+      cudaMemsetAsync(base + na::kOffSeq, 0, sizeof(unsigned) * kNumSlots * na::kCap, s) !=
           cudaSuccess) {
     return EIK_ECUDA;
   }
@@ -235,6 +236,7 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
   sp.tile_src = base + na::kOffTileSrc;
   sp.pend = reinterpret_cast<unsigned *>(base + na::kOffPend);
   sp.slots = reinterpret_cast<unsigned long long *>(base + na::kOffSlots);
+  sp.seq = reinterpret_cast<unsigned *>(base + na::kOffSeq);
   sp.cap_mask = static_cast<unsigned>(na::kCap - 1);
   sp.ctl = ctl;
   sp.timeout_ns = (opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000) * 1000000ll;

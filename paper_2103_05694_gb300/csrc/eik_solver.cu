@@ -18,11 +18,13 @@
 //    arrival time; the minimum committed time on each tile face activates the
 //    neighbour tile across that face (one aggregated push per face).
 //  * Scheduler: persistent kernel; kNumSlots bucket slots, each a ring of
-//    64-bit entries (tile | bucket << 32); warp 0 of a CTA scans 32 slots per
-//    step from the lowest-bucket hint, claims an entry with a CAS on the
-//    slot's pop counter and then claims the tile through its state word
-//    (idle / queued(b) / running / dirty(b)); a stale entry is dropped.
-//    Termination: the count of unfinished entries reaches zero.
+//    64-bit entries (tile | bucket << 32) with a sequence word per position;
+//    warp 0 of a CTA scans 32 slots per step from the lowest-bucket hint,
+//    reserves a written entry of a slot and takes the slot's next index (two
+//    fetch-and-adds: hundreds of idle CTAs never serialise on a retried CAS),
+//    then claims the tile through its state word (idle / queued(b) / running
+//    / dirty(b)); a stale entry is dropped.  Termination: the count of
+//    unfinished entries reaches zero.
 //  * FP64 is scarce on this part (about 1.6 DFMA per SM per clock), so every
 //    comparison, min, max and sign test runs on integer bit patterns, and a
 //    cell is evaluated only when a neighbour changed.
@@ -90,6 +92,14 @@ __device__ __forceinline__ void st_rlx(unsigned long long *p, unsigned long long
 __device__ __forceinline__ void st_rlx(unsigned *p, unsigned v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ unsigned ld_acq(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_rel(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ long long now_ns() {
   long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -137,16 +147,21 @@ __device__ bool push_entry(const SolveParams &p, unsigned long long tile, unsign
     raise_status(ctl, kEcapacity, (static_cast<unsigned long long>(s) << 32) | idx);
     return false;
   }
-  unsigned long long *slot = p.slots + static_cast<size_t>(s) * cap + (idx & p.cap_mask);
+  const size_t pos = static_cast<size_t>(s) * cap + (idx & p.cap_mask);
+  const unsigned lap = idx & ~p.cap_mask;
   const unsigned long long e = (static_cast<unsigned long long>(b) << 32) | tile;
   long long t0 = 0;
-  while (atomicCAS(slot, kEmpty, e) != kEmpty) {  // previous lap not consumed yet
+  while (ld_acq(p.seq + pos) != lap) {   // the previous lap's entry not taken yet
     const long long now = now_ns();
     if (t0 == 0) t0 = now;
     else if (now - t0 > p.timeout_ns) { raise_status(ctl, kEcapacity, 1ull << 63); return false; }
     if (ld_rlx(&ctl->status)) return false;
     __nanosleep(64);
   }
+  st_rlx(p.slots + pos, e);
+  st_rel(p.seq + pos, lap + 1u);
+  // the entry is written: one more for poppers to reserve
+  atomicAdd(&ctl->avail[s * kCounterPad], 1);
   // A scanner may have moved the lowest-bucket hint past this slot between
   // the caller's read of the hint and the push: pull the hint back.  A
   // scanner's forward CAS from a stale value then fails.
@@ -230,16 +245,17 @@ __device__ void finish_tile(const SolveParams &p, unsigned long long tile) {
   raise_status(p.ctl, kEtimeout, 5);
 }
 
-// Wait for the entry at ring position q of slot s, take it, free the slot.
+// The entry of index q of slot s (reserved by the caller): wait until its
+// pusher has written it, take it and free the position for the next lap.
 __device__ unsigned long long take_slot(const SolveParams &p, unsigned s, unsigned q) {
-  unsigned long long *slot =
-      p.slots + static_cast<size_t>(s) * (p.cap_mask + 1u) + (q & p.cap_mask);
+  const size_t pos = static_cast<size_t>(s) * (p.cap_mask + 1u) + (q & p.cap_mask);
+  const unsigned lap = q & ~p.cap_mask;
   long long t0 = 0;
 #pragma unroll 1
   for (;;) {
-    const unsigned long long e = ld_rlx(slot);
-    if (e != kEmpty) {
-      st_rlx(slot, kEmpty);
+    if (ld_acq(p.seq + pos) == lap + 1u) {
+      const unsigned long long e = ld_rlx(p.slots + pos);
+      st_rel(p.seq + pos, lap + p.cap_mask + 1u);     // after the read of the entry
       return e;
     }
     const long long now = now_ns();
@@ -309,15 +325,21 @@ __device__ unsigned long long pop_entry(const SolveParams &p, long long &idle_si
         int got = 0;
         if (lane == static_cast<unsigned>(l)) {
           atomicAdd(&ctl->run[s * kCounterPad], 1u);   // keep the slot active meanwhile
-#pragma unroll 1
-          while (static_cast<int>(pp - q) > 0) {
-            const unsigned prev = atomicCAS(&ctl->pop[s * kCounterPad], q, q + 1u);
-            if (prev == q) { got = 1; break; }
-            q = prev;
-            pp = ld_rlx(&ctl->push[s * kCounterPad]);
+          // reserve one written entry, then take the next index: two
+          // fetch-and-adds, so many idle CTAs never serialise on a retried CAS.
+          // Reservations never exceed the entries written, so pop <= push.  Only
+          // a popper that has just seen an entry to reserve tries (a failed try
+          // holds the count down until it is undone).
+          int *av = &ctl->avail[s * kCounterPad];
+          if (ld_rlx(av) > 0) {
+            if (atomicAdd(av, -1) > 0) {
+              got = 1;
+              e = take_slot(p, s, atomicAdd(&ctl->pop[s * kCounterPad], 1u));
+            } else {
+              atomicAdd(av, 1);                           // nothing left: undo the try
+            }
           }
-          if (got) e = take_slot(p, s, q);
-          else atomicAdd(&ctl->run[s * kCounterPad], 0xffffffffu);
+          if (!got) atomicAdd(&ctl->run[s * kCounterPad], 0xffffffffu);
         }
         got = __shfl_sync(kFull, got, l);
         if (got) {
