@@ -641,7 +641,8 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--band", type=float, default=0.0)
-    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0,
+                    help="tile shape 1-4 (see eik_opts.tile); 0: automatic")
     ap.add_argument("--schedule", type=int, default=0,
                     help="single grids: 1 = fast iterative method (Algorithm 3), 2 = "
                          "topology-driven (Algorithm 4), 3 = fast sweeping (Algorithm 5); "

@@ -66,11 +66,17 @@ typedef enum {
 } eik_status;
 
 /* Tuning knobs.  Zero (or a NULL pointer) selects the default; eik_autotune picks
- * them for a given batch.  Defaults: 2D k_delta 16, window 16, band 16, 1 CTA per SM
- * (2 when the batch has >= 8 sources); 3D k_delta 2, window 16, band 8, 2 CTAs per SM. */
+ * them for a given batch.  Defaults depend on how many independent wavefronts the
+ * batch has:
+ *   2D, fewer than 8 sources in the batch: 16x16 tiles, k_delta 16, window 16,
+ *     band 16, 1 CTA per SM (latency-bound: one front);
+ *   2D, 8 or more sources: 16x8 tiles, k_delta 2, window 16, band 16, 4 CTAs of
+ *     128 threads per SM;
+ *   3D: 8x4x4 tiles, k_delta 1, window 16, band 8, 4 CTAs of 128 threads per SM.
+ * With arith = 2 the first shape (16x16, 8x8x4) and k_delta 16 (2D) / 2 (3D). */
 typedef struct {
     double delta;          /* bucket width in time units; <= 0: auto (k_delta * mean h/v) */
-    double k_delta;        /* auto bucket width in cell travel times; <= 0: default */
+    double k_delta;        /* auto bucket width in cell travel times; <= 0: default (above) */
     int64_t capacity;      /* initial frontier ring capacity per bucket slot; 0: auto */
     int64_t timeout_ms;    /* limit of any single device wait; 0: 60000 */
     int ctas_per_sm;       /* persistent CTAs per SM (capped by occupancy); 0: default */
@@ -96,10 +102,10 @@ typedef struct {
                               {int64 t_claim_ns, t_end_ns; uint32 tile, lowest bucket,
                               rounds, flags}; NULL: no trace */
     int64_t trace_cap;
-    int tile;              /* tile shape, cells x*y(*z), one CTA thread per cell; 0: default.
-                              2D: 0 = 16x16, 1 = 32x8, 2 = 32x4, 3 = 16x8;
-                              3D: 0 = 8x8x4, 1 = 16x4x4, 2 = 32x4x2, 3 = 8x4x4.
-                              Shapes 1-3 need arith 0/1 (EIK_EINVAL otherwise). */
+    int tile;              /* tile shape, cells x*y(*z), one CTA thread per cell; 0: default
+                              (above).  2D: 1 = 16x16, 2 = 32x8, 3 = 32x4, 4 = 16x8;
+                              3D: 1 = 8x8x4, 2 = 16x4x4, 3 = 32x4x2, 4 = 8x4x4.
+                              Shapes 2-4 need arith 0/1 (EIK_EINVAL otherwise). */
     int update;            /* the local update: 0 = d-bar, exactly monotone (section "Achieving
                               Exact Monotonicity"), the default; for the ablation of the
                               Mitigation Strategies section, 2D only: 1 = Algorithm 1 with the
@@ -198,8 +204,10 @@ eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches, void *str
  *     2048 sources; larger inputs return EIK_EINVAL before anything runs;
  *   - no capacity retry: a frontier overflow returns EIK_ECAPACITY;
  *   - stats->solve_ms, max_queue and the timing details stay 0;
- *     opts->trace and opts->test_stall are ignored.
- * Scratch memory is one fixed file-scope device array of about 17 MB, present
+ *     opts->trace and opts->test_stall are ignored;
+ *   - the first tile shape (16x16, 8x8x4) whatever the dimension, k_delta 16 (2D) /
+ *     2 (3D) unless opts->k_delta is set; opts->tile must be 0.
+ * Scratch memory is one fixed file-scope device array of about 21 MB, present
  * on every GPU that loads the library until the process exits.  The first
  * call on a device looks up that array's device address (once per device);
  * make that first call before any stream capture.  Every call shares the

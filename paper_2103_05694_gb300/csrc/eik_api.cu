@@ -266,16 +266,42 @@ eik_status check_problem(const double *speed, double h, int ndim, const int64_t 
   return EIK_OK;
 }
 
-// Tile shape of opts (validated): shape index and cells per axis.
-eik_status tile_shape(const eik_opts *opts, int ndim, int &shape, int64_t &tx, int64_t &ty,
-                      int64_t &tz) {
-  shape = opts ? opts->tile : 0;
-  if (shape < 0 || shape >= eik::kNumTileShapes) {
-    set_err("opts.tile must be in 0..%d", eik::kNumTileShapes - 1);
+// Automatic tile shape and bucket width.  With many independent wavefronts
+// (3D grids, 2D batches of at least 8 sources) every CTA has work and smaller
+// tiles with narrower buckets finish sooner; a single 2D front is latency-bound
+// and wants large tiles and wide buckets.  (Chosen with the autotuner on the
+// layered, tomography, checkerboard and batched workloads.)  The integer-pipe
+// arithmetic has the first shape only.
+struct AutoCfg {
+  int shape;
+  double k_delta;
+};
+AutoCfg auto_config(int ndim, int64_t total_sources, bool int_arith) {
+  if (int_arith) return {0, kDefaultKDelta[ndim == 3 ? 1 : 0]};
+  if (ndim == 3) return {3, 1.0};
+  if (total_sources >= 8) return {3, 2.0};
+  return {0, kDefaultKDelta[0]};
+}
+
+int64_t count_sources(const std::vector<HostProblem> &hps) {
+  int64_t n = 0;
+  for (const HostProblem &hp : hps) n += (int64_t)hp.src.size();
+  return n;
+}
+
+// Tile shape of opts (validated): shape index and cells per axis.  opts.tile 0
+// is automatic; 1..kNumTileShapes name shape tile - 1.
+eik_status tile_shape(const eik_opts *opts, int ndim, int64_t total_sources, int &shape,
+                      int64_t &tx, int64_t &ty, int64_t &tz) {
+  const int t = opts ? opts->tile : 0;
+  const bool int_arith = opts && opts->arith == 2;
+  if (t < 0 || t > eik::kNumTileShapes) {
+    set_err("opts.tile must be in 0..%d", eik::kNumTileShapes);
     return EIK_EINVAL;
   }
-  if (shape != 0 && opts->arith == 2) {
-    set_err("integer-pipe arithmetic (arith 2) runs the default tile shape only");
+  shape = t == 0 ? auto_config(ndim, total_sources, int_arith).shape : t - 1;
+  if (shape != 0 && int_arith) {
+    set_err("integer-pipe arithmetic (arith 2) runs the first tile shape only (opts.tile 0 or 1)");
     return EIK_EINVAL;
   }
   const eik::TileShape ts = eik::tile_shape_of(ndim, shape);
@@ -460,7 +486,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   }
   int64_t tx, ty, tz;
   int shape = 0;
-  st = tile_shape(opts, ndim, shape, tx, ty, tz);
+  st = tile_shape(opts, ndim, count_sources(hps), shape, tx, ty, tz);
   if (st != EIK_OK) return st;
   int form = 0;
   st = update_form(opts, ndim, form);
@@ -621,7 +647,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.timeout_ns = tmo_ms * 1000000ll;
   sp.counters = opts ? opts->counters : 0;
   sp.test_stall = opts ? opts->test_stall : 0;
-  const double k_delta = opts && opts->k_delta > 0 ? opts->k_delta : kDefaultKDelta[di];
+  const double k_delta = opts && opts->k_delta > 0
+                             ? opts->k_delta
+                             : auto_config(ndim, total_src, sp.arith == eik::kArithInt).k_delta;
   const double delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
 
   CK(eik::launch_seed(sp, g_ws.seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
@@ -802,10 +830,15 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
   cur.test_stall = 0;
   cur.trace = nullptr;
   cur.trace_cap = 0;
-  if (cur.k_delta <= 0) cur.k_delta = kDefaultKDelta[di];
+  const bool int_arith = cur.arith == 2;
+  {
+    // start from the automatic choice, named explicitly
+    const AutoCfg ac = auto_config(ndim, count_sources(hps), int_arith);
+    if (cur.tile <= 0) cur.tile = ac.shape + 1;
+    if (cur.k_delta <= 0) cur.k_delta = ac.k_delta;
+  }
   if (cur.window <= 0) cur.window = kDefaultWindow[di];
   if (cur.band <= 0) cur.band = kDefaultBand[di];
-  const bool int_arith = cur.arith == 2;
 
   unsigned long long ref[2] = {0, 0};
   bool have_ref = false;
@@ -865,7 +898,7 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
     const eik_opts start = cur;
     if (!int_arith) {
       const int t0 = cur.tile;
-      for (int t = 0; t < eik::kNumTileShapes; ++t) {
+      for (int t = 1; t <= eik::kNumTileShapes; ++t) {
         if (t == t0) continue;
         eik_opts o = cur;
         o.tile = t;
@@ -906,7 +939,7 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
     }
     {
       const int occ = eik::persistent_blocks_per_sm(ndim, int_arith ? eik::kArithInt : eik::kArithFp64,
-                                                    cur.tile);
+                                                    cur.tile - 1);
       const int c0 = cur.ctas_per_sm;
       for (int c = 1; c <= occ; ++c) {
         if (c == c0) continue;
@@ -1015,7 +1048,7 @@ const char *eik_status_str(eik_status s) {
 
 const char *eik_last_error(void) { return g_err; }
 
-int eik_abi_version(void) { return 105; }
+int eik_abi_version(void) { return 106; }
 
 uint64_t eik_kernel_launches(void) { return (uint64_t)eik::kernel_launches(); }
 
@@ -1073,7 +1106,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   }
   int64_t tx, ty, tz;
   int shape = 0;
-  eik_status tst = tile_shape(opts, pl.ndim, shape, tx, ty, tz);
+  eik_status tst = tile_shape(opts, pl.ndim, count_sources(hps), shape, tx, ty, tz);
   if (tst != EIK_OK) return tst;
   int form = 0;
   tst = update_form(opts, pl.ndim, form);
@@ -1182,7 +1215,9 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   sp.update = form;
   sp.trace = nullptr;
   sp.trace_cap = 0;
-  pl.k_delta = opts && opts->k_delta > 0 ? opts->k_delta : kDefaultKDelta[di];
+  pl.k_delta = opts && opts->k_delta > 0
+                   ? opts->k_delta
+                   : auto_config(pl.ndim, count_sources(hps), opts && opts->arith == 2).k_delta;
   pl.delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm
                                              : default_ctas_per_sm(di, tx * ty * tz, pl.nseeds);

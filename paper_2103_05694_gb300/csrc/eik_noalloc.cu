@@ -8,7 +8,7 @@
 // scratch area that is a file-scope __device__ array, so it calls no
 // cudaMalloc, cudaFree, cudaMallocHost or other allocating routine.
 //
-// The array (about 17 MB) exists on every GPU that loads this library, for
+// The array (about 21 MB) exists on every GPU that loads this library, for
 // as long as the library stays loaded.  Every call shares it: the call clears
 // what must start at zero itself, and calls whose work overlaps on the GPU
 // (different streams, or different host threads without ordering) race on it.

@@ -40,7 +40,7 @@ def test_autotune_bits_and_choice(shape):
     best, trials = eik.eik_autotune(probs, repeats=1)
     assert len(trials) >= 10
     assert all(t["status"] == eik.EIK_OK and t["ms"] > 0 for t in trials)
-    assert 0 <= best["tile"] < 4 and best["k_delta"] > 0 and best["window"] > 0
+    assert 1 <= best["tile"] <= 4 and best["k_delta"] > 0 and best["window"] > 0
     cap = best["capacity"]
     assert cap >= 64 and cap & (cap - 1) == 0
     # the chosen configuration is no slower than the starting one (same run)
