@@ -17,9 +17,10 @@ Functions and the passages they follow:
   method, Algorithm 5 (mode 1).
 * ``relax_order`` -- relaxation in a caller-given order (Theorem 1).
 * ``residual`` -- the fixed-point residual of Table 3 (d-bar, or in 2D Algorithm 1
-  with the explicit roots d-tilde / d-hat: ``form`` 1 / 2).
+  with the explicit roots d-tilde / d-hat / d-hat then Newton: ``form`` 1 / 2 / 3).
 * ``update_form`` -- one application of Algorithm 1 with d-tilde (form 1), d-hat
-  (form 2) or d-bar (form 0) (Mitigation Strategies section).
+  (form 2), d-hat followed by Newton's method on alpha = 0 (form 3) or d-bar
+  (form 0) (Mitigation Strategies and Achieving Exact Monotonicity sections).
 * ``adjoint`` -- d(loss)/d(slowness) through the fixed point (not in the paper:
   implicit differentiation of the real-arithmetic local equations).
 """
@@ -177,13 +178,13 @@ def relax_order(speed: np.ndarray, h: float, sources, perm, src_t=None) -> Oracl
 
 
 def update_form(form: int, v: float, h: float, tH: float, tV: float) -> float:
-    """Algorithm 1 with root d-tilde (1), d-hat (2) or d-bar (0)."""
+    """Algorithm 1 with root d-tilde (1), d-hat (2), d-hat then Newton (3) or d-bar (0)."""
     return lib().orc_update_form(int(form), v, h, tH, tV)
 
 
 def residual(speed: np.ndarray, h: float, sources, t: np.ndarray, src_t=None, form: int = 0):
     """Table 3 residual of a field: (number of cells that are not fixed under the
-    operator, largest relative difference).  ``form`` as in update_form (1, 2:
+    operator, largest relative difference).  ``form`` as in update_form (1-3:
     2D only)."""
     speed, dims, src, st = _grid_args(speed, sources, src_t)
     t = np.ascontiguousarray(t, dtype=np.float64)

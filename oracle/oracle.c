@@ -69,6 +69,31 @@ double orc_dhat(double v, double h, double tH, double tV)
     return 0.5 * (tH + tV + sqrt(disc));
 }
 
+/* d-hat followed by Newton's method on alpha(tau) = (tau - tH)^2 + (tau - tV)^2
+ * - c = 0: the variant the Achieving Exact Monotonicity section reports as
+ * deterministic in its tests although it does not follow d-bar's rounding
+ * semantics.  The paper gives no stopping rule.  This reading stops when an
+ * iterate repeats the previous one, when the derivative 2 (mH + mV) is not
+ * positive, or after ORC_NEWTON_ITERS steps. */
+#define ORC_NEWTON_ITERS 4
+double orc_newton(double v, double h, double tH, double tV)
+{
+    double r = h / v;
+    double c = r * r;
+    double tau = orc_dhat(v, h, tH, tV);
+    for (int k = 0; k < ORC_NEWTON_ITERS; ++k) {
+        double mH = tau - tH;
+        double mV = tau - tV;
+        double alpha = (mH * mH + mV * mV) - c;
+        double slope = 2.0 * (mH + mV);
+        if (!(slope > 0.0)) break;
+        double next = tau - alpha / slope;
+        if (next == tau) break;
+        tau = next;
+    }
+    return tau;
+}
+
 /* Per-cell constant of the update: c = fl(fl(h/v)^2) (Eq. difference_as_root
  * with the (h/v)^2 reading; Table 2 pins the two roundings). */
 double orc_cell_c(double v, double h)
@@ -164,9 +189,9 @@ double orc_dbar_bisect(const double *a, int D, double c)
 /* One application of Algorithm 1 (the Eikonal update operator) with an
  * explicit root in place of Eq. difference_as_root, for the ablation of the
  * Mitigation Strategies section (2D): form 1 = d-tilde (the classical root, "no
- * mitigation"), form 2 = d-hat (the rearranged root).  One-sided when
- * |tH - tV| >= h/v or one minimum is +inf: min(tH, tV) + h/v.  form 0 = d-bar.
- * +inf when both minima are +inf. */
+ * mitigation"), form 2 = d-hat (the rearranged root), form 3 = d-hat then
+ * Newton's method (orc_newton).  One-sided when |tH - tV| >= h/v or one minimum
+ * is +inf: min(tH, tV) + h/v.  form 0 = d-bar.  +inf when both minima are +inf. */
 double orc_update_form(int form, double v, double h, double tH, double tV)
 {
     double r = h / v;
@@ -179,7 +204,9 @@ double orc_update_form(int form, double v, double h, double tH, double tV)
     if (tH == ORC_INF || tV == ORC_INF) return lo + r;
     double d = tH - tV;
     if (fabs(d) >= r) return lo + r;
-    return form == 1 ? orc_dtilde(v, h, tH, tV) : orc_dhat(v, h, tH, tV);
+    if (form == 1) return orc_dtilde(v, h, tH, tV);
+    if (form == 2) return orc_dhat(v, h, tH, tV);
+    return orc_newton(v, h, tH, tV);
 }
 
 /* ---------------------------------------------------------------------------

@@ -124,3 +124,59 @@ def test_residual_form_rejects_3d():
     t = np.zeros((3, 3, 3))
     with pytest.raises(RuntimeError):
         oracle.residual(speed, 1.0, [0], t, form=1)
+
+
+def _ulp_scale(tau, tH, tV):
+    # the update rounds tau - tH and tau - tV: its error is relative to the
+    # largest magnitude among tau, the minima and those differences
+    return math.ulp(max(abs(tau), abs(tH), abs(tV), abs(tau - tH), abs(tau - tV)))
+
+
+def test_newton_variant_close_to_the_exact_root():
+    """Form 3 (d-hat, then Newton's method on alpha = 0) lands within 2 ulps (of
+    the largest magnitude in the update) of the exact root of the quadratic with
+    the same c, over scales from 1e-3 to 1e3 and minima of either sign."""
+    getcontext().prec = 80
+    rng = np.random.Generator(np.random.PCG64(7))
+    n = 0
+    for _ in range(4000):
+        v = float(rng.uniform(0.5, 4.0))
+        h = float(rng.choice([1.0, 0.25, 4.0]))
+        r = h / v
+        tH = float(rng.uniform(0.0, 50.0)) * float(rng.choice([1e-3, 1.0, 1e3]))
+        tV = tH + float(rng.uniform(-0.95, 0.95)) * r
+        if abs(tH - tV) >= r:
+            continue
+        c = Decimal(r * r)
+        a, b = Decimal(tH), Decimal(tV)
+        root = (a + b + (2 * c - (a - b) ** 2).sqrt()) / 2
+        got = oracle.update_form(3, v, h, tH, tV)
+        assert abs(Decimal(got) - root) <= 2 * Decimal(_ulp_scale(got, tH, tV)), (v, h, tH, tV, got)
+        n += 1
+    assert n > 3000
+
+
+@pytest.mark.parametrize("table,broken", [("table1_dtilde.txt", 1), ("table2_dhat.txt", 2)])
+def test_newton_variant_orders_the_table_pairs(table, broken):
+    """The paper reports the Newton variant deterministic in its tests: on the two
+    input pairs of Tables 1 and 2, where d-tilde and d-hat respectively lose
+    monotonicity, form 3 keeps the order of its inputs."""
+    (_, v, h, tH, tVa, _), (_, _, _, _, tVb, _) = _rows(table)
+    assert tVb < tVa
+    assert oracle.update_form(broken, v, h, tH, tVb) > oracle.update_form(broken, v, h, tH, tVa)
+    assert oracle.update_form(3, v, h, tH, tVb) <= oracle.update_form(3, v, h, tH, tVa)
+
+
+def test_newton_variant_one_sided_and_symmetric():
+    rng = np.random.Generator(np.random.PCG64(8))
+    for _ in range(500):
+        v = float(rng.uniform(0.5, 4.0))
+        h = float(rng.choice([1.0, 0.5, 2.0]))
+        r = h / v
+        tH = float(rng.uniform(0.0, 20.0))
+        tV = tH + float(rng.choice([-1.0, 1.0])) * float(rng.uniform(1.0, 3.0)) * r
+        assert oracle.update_form(3, v, h, tH, tV) == min(tH, tV) + r      # one-sided
+        tV2 = tH + float(rng.uniform(-0.9, 0.9)) * r
+        assert oracle.update_form(3, v, h, tH, tV2) == oracle.update_form(3, v, h, tV2, tH)
+    assert oracle.update_form(3, 1.0, 1.0, INF, 2.0) == 3.0
+    assert oracle.update_form(3, 1.0, 1.0, INF, INF) == INF
