@@ -366,6 +366,9 @@ def make_opts(args):
         opts["tile"] = args.tile
     if args.update > 0:
         opts["update"] = args.update
+    if args.track_changes:
+        from paper_2103_05694_gb300 import TRACK_CHANGES
+        opts["sched_flags"] = opts.get("sched_flags", 0) | TRACK_CHANGES
     if args.schedule > 0:
         opts["schedule"] = args.schedule
     return opts
@@ -388,6 +391,11 @@ def run_single(args, C, wl_name):
         else SINGLE[args.workload]()
     if args.scale != 1.0:
         wl_name = prob.name + "_scaled"
+    if args.upsample > 1:
+        if prob.speed.ndim != 2:
+            raise SystemExit("--upsample applies to the 2D workloads")
+        prob = synth.upsampled(prob, args.upsample)
+        wl_name = f"{wl_name}_upsampled_x{args.upsample}"
     useful = useful_of(prob)
     opts = make_opts(args)
     speed = torch.from_numpy(prob.speed).to(C.dev)
@@ -443,10 +451,11 @@ def run_single(args, C, wl_name):
                                                 "stale_pops", "rounds")}
     line["work_per_step"].update(empty=st["evals"] - st["decreases"],
                                  bad=st["decreases"] - st["good"])
-    line["residual"] = {"update": ["d-bar", "d-tilde", "d-hat"][args.update], "cells": bad,
+    line["residual"] = {"update": ["d-bar", "d-tilde", "d-hat", "d-hat+Newton"][args.update]
+                        + (" (change tracking)" if args.track_changes else ""), "cells": bad,
                         "max_rel": max_rel, "same_bits_every_step": same_bits}
     traffic = args.traffic_bytes
-    if traffic is None and not opts and args.scale == 1.0 and not args.autotune:
+    if traffic is None and not opts and args.scale == 1.0 and args.upsample == 1 and not args.autotune:
         traffic = MEASURED_TRAFFIC.get(args.workload)
     line["roofline"] = roofline(useful, statistics.mean(solve_ms), traffic,
                                 ["persistent_kernel (tile relaxation + bucket scheduler)",
@@ -635,6 +644,9 @@ def main():
     ap.add_argument("--workload", default="layered_2d", choices=sorted(WORKLOADS))
     ap.add_argument("--scale", type=float, default=1.0,
                     help="layered_2d only: fraction of the extent per axis (profiling)")
+    ap.add_argument("--upsample", type=int, default=1,
+                    help="2D single grids: nearest-neighbour upsampling by this factor per axis, "
+                         "spacing h / factor (Table 3's input scale)")
     ap.add_argument("--sources", type=int, default=0,
                     help="tomography_2d only: use the first N sources (profiling cases)")
     ap.add_argument("--k-delta", type=float, default=0.0)
@@ -648,7 +660,10 @@ def main():
                          "topology-driven (Algorithm 4), 3 = fast sweeping (Algorithm 5); "
                          "0: asynchronous tiles (Algorithm 6)")
     ap.add_argument("--update", type=int, default=0,
-                    help="2D ablation: 1 = Algorithm 1 with d-tilde, 2 = with d-hat (0: d-bar)")
+                    help="2D ablation: 1 = Algorithm 1 with d-tilde, 2 = with d-hat, 3 = d-hat "
+                         "then Newton (0: d-bar)")
+    ap.add_argument("--track-changes", action="store_true",
+                    help="with --update 1-3: conservative work tracking (activate on any change)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the scheduling options with eik_autotune on the workload first")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -97,7 +97,13 @@ typedef struct {
                               lists of up to a quarter of the tile, 3 = an eighth;
                               bits 3-4 (eik_adjoint only): schedule, 0 = default (tiles when
                               every problem has the same ndim, else levels), 1 = levels,
-                              2 = tiles */
+                              2 = tiles;
+                              bit 5 (update 1-3 only, EIK_EINVAL otherwise): change tracking,
+                              the conservative work tracking of the Mitigation Strategies
+                              section: a recomputed value that differs from the cell's, up or
+                              down, replaces it and re-activates the neighbours (termination
+                              is no longer guaranteed: after 256 tile visits per tile the
+                              solve stops with EIK_ETIMEOUT) */
     void *trace;           /* optional device buffer of trace_cap 32-byte visit records
                               {int64 t_claim_ns, t_end_ns; uint32 tile, lowest bucket,
                               rounds, flags}; NULL: no trace */
@@ -110,8 +116,11 @@ typedef struct {
                               Exact Monotonicity"), the default; for the ablation of the
                               Mitigation Strategies section, 2D only: 1 = Algorithm 1 with the
                               classical explicit root d-tilde, 2 = with the rearranged root
-                              d-hat.  1 and 2 are not monotone: their results may depend on the
-                              schedule and are not a fixed point (Table 3). */
+                              d-hat, 3 = d-hat refined by Newton's method on the root problem
+                              (the variant of the Achieving Exact Monotonicity section; stops
+                              when an iterate repeats or after 4 steps).  1-3 are not proven
+                              monotone: results may depend on the schedule and need not be a
+                              fixed point (Table 3). */
     int schedule;          /* 0 = asynchronous bucketed tiles (Algorithm 6), the default;
                               single problems only, device pointers, for comparison:
                               1 = fast iterative method (Algorithm 3, epsilon = 0, rounds),
@@ -256,15 +265,16 @@ eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const 
 /* Update-form ablation (Mitigation Strategies section, Tables 1 and 2): for
  * i < n, out[i] = one application of Algorithm 1 at a cell of speed v = speed[i]
  * with axis minima t_h[i], t_v[i] (2D): form 1 = classical root d-tilde,
- * form 2 = rearranged root d-hat (one-sided min + h/v when |t_h - t_v| >= h/v
- * or one minimum is +inf), form 0 = d-bar.  +inf when both minima are +inf.
+ * form 2 = rearranged root d-hat, form 3 = d-hat then Newton (as eik_opts.update;
+ * all three one-sided min + h/v when |t_h - t_v| >= h/v or one minimum is +inf),
+ * form 0 = d-bar.  +inf when both minima are +inf.
  * Device pointers only; EIK_EINVAL otherwise.  Synchronises `stream`.  The
  * paper has no interface of this kind: it exposes the update for testing. */
 eik_status eik_eval_update(int form, const double *speed, double h, const double *t_h,
                            const double *t_v, int64_t n, double *out, void *stream);
 
 /* The fixed-point residual of Table 3: re-applies the update (form as in
- * eik_eval_update; 1 and 2: 2D only) at every cell of prob->out_t using the
+ * eik_eval_update; 1-3: 2D only) at every cell of prob->out_t using the
  * final values of its neighbours.  *bad = cells whose value changes (sources:
  * value != their smallest t0), *max_rel = the largest |t - tau| / t over cells
  * where both are finite and t > 0 (+inf if a changing cell is not), 0 for a

@@ -472,7 +472,10 @@ def eik_autotune(problems: list[dict], base: dict | None = None, repeats: int = 
     return opts_dict(best), trials
 
 
-UPDATE_FORMS = {"dbar": 0, "dtilde": 1, "dhat": 2}
+UPDATE_FORMS = {"dbar": 0, "dtilde": 1, "dhat": 2, "newton": 3}
+# opts["sched_flags"] bit 5: with an explicit form, a recomputed value that differs
+# (up or down) replaces the cell's and re-activates its neighbours
+TRACK_CHANGES = 1 << 5
 
 
 def eik_eval_update(form: int, speed, h: float, t_h, t_v, out=None, stream=None):

@@ -314,9 +314,13 @@ eik_status tile_shape(const eik_opts *opts, int ndim, int64_t total_sources, int
 // Update form of opts (validated): 0 = d-bar; 1 = d-tilde, 2 = d-hat (2D).
 eik_status update_form(const eik_opts *opts, int ndim, int &form) {
   form = opts ? opts->update : 0;
+  if (opts && (opts->sched_flags & 32) && form == 0) {
+    set_err("change tracking (sched_flags bit 5) applies to the explicit update forms only");
+    return EIK_EINVAL;
+  }
   if (form == 0) return EIK_OK;
-  if (form < 0 || form > 2) { set_err("opts.update must be 0, 1 or 2"); return EIK_EINVAL; }
-  if (ndim != 2) { set_err("the explicit update forms (opts.update 1, 2) are 2D only"); return EIK_EINVAL; }
+  if (form < 0 || form > 3) { set_err("opts.update must be 0, 1, 2 or 3"); return EIK_EINVAL; }
+  if (ndim != 2) { set_err("the explicit update forms (opts.update 1-3) are 2D only"); return EIK_EINVAL; }
   return EIK_OK;
 }
 
@@ -636,6 +640,8 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
   sp.tile_shape = shape;
   sp.update = form;
+  sp.track_changes = opts && (opts->sched_flags & 32) ? 1 : 0;
+  sp.visit_budget = sp.track_changes ? (unsigned long long)total_tiles * 256ull + 4096ull : 0ull;
   sp.trace = opts && opts->trace && opts->trace_cap > 0 ? static_cast<eik::TraceRec *>(opts->trace)
                                                         : nullptr;
   sp.trace_cap = sp.trace ? (unsigned long long)opts->trace_cap : 0ull;
@@ -972,7 +978,7 @@ eik_status eik_eval_update(int form, const double *speed, double h, const double
                            const double *t_v, int64_t n, double *out, void *stream) {
   std::lock_guard<std::mutex> lk(g_mu);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (form < 0 || form > 2 || n < 0 || !(h > 0.0) || (n > 0 && (!speed || !t_h || !t_v || !out))) {
+  if (form < 0 || form > 3 || n < 0 || !(h > 0.0) || (n > 0 && (!speed || !t_h || !t_v || !out))) {
     set_err("bad eik_eval_update arguments");
     return EIK_EINVAL;
   }
@@ -1048,7 +1054,7 @@ const char *eik_status_str(eik_status s) {
 
 const char *eik_last_error(void) { return g_err; }
 
-int eik_abi_version(void) { return 106; }
+int eik_abi_version(void) { return 107; }
 
 uint64_t eik_kernel_launches(void) { return (uint64_t)eik::kernel_launches(); }
 
@@ -1213,6 +1219,8 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
   sp.tile_shape = shape;
   sp.update = form;
+  sp.track_changes = opts && (opts->sched_flags & 32) ? 1 : 0;
+  sp.visit_budget = sp.track_changes ? (unsigned long long)pl.total_tiles * 256ull + 4096ull : 0ull;
   sp.trace = nullptr;
   sp.trace_cap = 0;
   pl.k_delta = opts && opts->k_delta > 0

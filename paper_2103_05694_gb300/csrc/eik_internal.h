@@ -58,6 +58,7 @@ struct Ctl {
   int avail[kNumSlots * kCounterPad];      // entries written and not yet reserved by a popper
                                            // (may dip below 0 while a failed reservation
                                            // is being undone)
+  unsigned long long visits_total;         // tile visits claimed (checked against visit_budget)
 };
 
 // One grid of a (possibly batched) solve, as the kernels see it.
@@ -92,7 +93,14 @@ struct SolveParams {
   int arith;                      // kArithFp64 or kArithInt
   int gate_pending_only;          // window follows pending entries only, not running tiles
   int tile_shape;                 // index into tile_shape_of (0: default)
-  int update;                     // 0: d-bar; 2D ablation: 1 = d-tilde, 2 = d-hat (c holds r)
+  int update;                     // 0: d-bar; 2D ablation: 1 = d-tilde, 2 = d-hat, 3 = d-hat
+                                  // then Newton (c holds r)
+  unsigned long long visit_budget;  // 0: none; else the solve stops with EIK_ETIMEOUT after
+                                    // this many tile visits (change tracking, which may not
+                                    // terminate, runs with one)
+  int track_changes;              // explicit forms only: a cell whose recomputed value differs
+                                  // from its value (up or down) takes it and re-activates its
+                                  // neighbours (the paper's conservative work tracking)
   int lane_group_cells;           // lists of at most this many cells use lane groups (0: never)
   struct TraceRec *trace;         // optional visit trace (device), NULL when off
   unsigned long long trace_cap;

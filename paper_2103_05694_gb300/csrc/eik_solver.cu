@@ -483,6 +483,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         if (tile >= 0) {
           __threadfence();  // the claim is ordered before the tile's loads
           prob = find_prob(p, static_cast<unsigned long long>(tile));
+          if (p.visit_budget && atomicAdd(&p.ctl->visits_total, 1ull) >= p.visit_budget)
+            raise_status(p.ctl, kEtimeout, 9);   // this visit runs; then every CTA stops
           const double vlim = static_cast<double>(lo + p.window + 1u) * delta;
           s_vlim = bits_of(vlim);
         }
@@ -612,8 +614,10 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         unsigned long long amin = a[0];
 #pragma unroll
         for (int k = 1; k < D; ++k) amin = umin64(amin, a[k]);
-        const unsigned long long best = umin64(bits_of(tv), s_pv[tid]);
-        go = amin < kInfBits && best > amin;
+        // change tracking compares with the cell's value (a recomputed value may
+        // also be larger); otherwise a candidate must beat value and pending
+        const unsigned long long best = p.track_changes ? bits_of(tv) : umin64(bits_of(tv), s_pv[tid]);
+        go = amin < kInfBits && (p.track_changes || best > amin);
         if (go) {
 #pragma unroll
           for (int k = 0; k < D; ++k) s_a[k][tid] = a[k];
@@ -675,7 +679,12 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
             bool dec;
             if (D == 2 && p.update) {   // explicit roots: s_c holds r = fl(h/v)
               nv = forms::explicit_update(p.update, a[0], a[D - 1], from_bits(s_c[c]));
-              dec = nv < s_best[c];
+              if (p.track_changes) {    // the latest value replaces any pending one
+                dec = nv != s_best[c];
+                if (!dec) s_pv[c] = kInfBits;
+              } else {
+                dec = nv < s_best[c];
+              }
             } else {
               dec = ARITH == kArithInt ? xf::relax<D>(s_best[c], a, s_c[c], nv)
                                        : hw::relax<D>(s_best[c], a, s_c[c], nv,
@@ -733,19 +742,24 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
     ++R;
 
     // commit and collect the smallest committed time per tile face
-    if (bits_of(tv) < bits_of(tv0)) {
+    const bool track = p.track_changes != 0;
+    if (track ? bits_of(tv) != bits_of(tv0) : bits_of(tv) < bits_of(tv0)) {
       const unsigned long long tb = bits_of(tv);
-      atomicMin(reinterpret_cast<unsigned long long *>(T + gidx), tb);
+      if (track)   // a value may rise: only this tile's visit writes its cells
+        st_rlx(reinterpret_cast<unsigned long long *>(T + gidx), tb);
+      else
+        atomicMin(reinterpret_cast<unsigned long long *>(T + gidx), tb);
       ++n_commits;
       // a face value can change the cell across the face only if it is below
-      // that cell's value (causality; the loaded halo value is an upper bound)
-      if (lx == 0 && tb < bits_of(s_t[zc][yc][xc - 1])) atomicMin(&s_facemin[0], tb);
-      if (lx == TX - 1 && tb < bits_of(s_t[zc][yc][xc + 1])) atomicMin(&s_facemin[1], tb);
-      if (ly == 0 && tb < bits_of(s_t[zc][yc - 1][xc])) atomicMin(&s_facemin[2], tb);
-      if (ly == TY - 1 && tb < bits_of(s_t[zc][yc + 1][xc])) atomicMin(&s_facemin[3], tb);
+      // that cell's value (causality; the loaded halo value is an upper bound).
+      // Change tracking activates on any change.
+      if (lx == 0 && (track || tb < bits_of(s_t[zc][yc][xc - 1]))) atomicMin(&s_facemin[0], tb);
+      if (lx == TX - 1 && (track || tb < bits_of(s_t[zc][yc][xc + 1]))) atomicMin(&s_facemin[1], tb);
+      if (ly == 0 && (track || tb < bits_of(s_t[zc][yc - 1][xc]))) atomicMin(&s_facemin[2], tb);
+      if (ly == TY - 1 && (track || tb < bits_of(s_t[zc][yc + 1][xc]))) atomicMin(&s_facemin[3], tb);
       if constexpr (D == 3) {
-        if (lz == 0 && tb < bits_of(s_t[zc - 1][yc][xc])) atomicMin(&s_facemin[4], tb);
-        if (lz == TZ - 1 && tb < bits_of(s_t[zc + 1][yc][xc])) atomicMin(&s_facemin[5], tb);
+        if (lz == 0 && (track || tb < bits_of(s_t[zc - 1][yc][xc]))) atomicMin(&s_facemin[4], tb);
+        if (lz == TZ - 1 && (track || tb < bits_of(s_t[zc + 1][yc][xc]))) atomicMin(&s_facemin[5], tb);
       }
     }
     __threadfence();

@@ -104,6 +104,20 @@ def layered_2d_2301x751() -> Problem:
     return Problem("2d_2301x751_layered", speed, h, src, np.zeros(1), {})
 
 
+def upsampled(p: Problem, k: int) -> Problem:
+    """A 2D problem upsampled by k on each axis with nearest-neighbour
+    interpolation (spacing h / k), its sources at the same physical points: the
+    paper's x4 input scale (Methods: Marmousi upsampled by 4 per axis)."""
+    if k == 1:
+        return p
+    nz, nx = p.speed.shape
+    speed = np.repeat(np.repeat(p.speed, k, axis=0), k, axis=1)
+    z, x = np.divmod(p.sources, nx)
+    src = (z * k) * (nx * k) + x * k
+    return Problem(f"{p.name}_up{k}", speed, p.h / k, src.astype(np.int64), p.src_t.copy(),
+                   dict(p.meta, upsample=k))
+
+
 def smooth_random_volume(n: int, seed: int, vmin: float, vmax: float,
                          sigma: float = 8.0) -> np.ndarray:
     """White noise, Gaussian-filtered, affinely mapped from its min/max to

@@ -1,5 +1,6 @@
 """The update-form ablation through the C ABI: the device evaluation of
-Algorithm 1 with d-tilde / d-hat (and of d-bar) equals the oracle bit for bit
+Algorithm 1 with d-tilde / d-hat / d-hat then Newton (and of d-bar) equals the
+oracle bit for bit
 and reproduces Tables 1 and 2; the device Table 3 residual equals the oracle's;
 solves with the explicit forms stay within rounding of the exact field and are
 not fixed points in general, while d-bar's residual is exactly 0."""
@@ -51,7 +52,7 @@ def test_device_update_reproduces_tables(form, table):
     assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
 
 
-@pytest.mark.parametrize("form", [0, 1, 2])
+@pytest.mark.parametrize("form", [0, 1, 2, 3])
 def test_device_update_equals_oracle(form):
     rng = np.random.Generator(np.random.PCG64(40 + form))
     n = 4000
@@ -80,10 +81,10 @@ def _gpu_field(p, opts):
 @pytest.mark.parametrize("shape", [(60, 80), (9, 300)])
 def test_device_residual_equals_oracle(shape):
     p = synth.random_problem(12, shape, n_src=2, contrast=6.0, smooth_sigma=2.0, h=0.5)
-    for upd in (0, 1, 2):
+    for upd in (0, 1, 2, 3):
         prob = _gpu_field(p, {"update": upd})
         t = prob["out"].cpu().numpy()
-        for form in (0, 1, 2):
+        for form in (0, 1, 2, 3):
             got = eik.eik_residual(prob, form)
             want = oracle.residual(p.speed, p.h, p.sources, t, form=form)
             assert got == want, (upd, form, got, want)
@@ -114,7 +115,7 @@ def test_explicit_forms_rejected_where_undefined():
         eik.eik_autotune(probs, base={"update": 2})
     assert e.value.status == eik.EIK_EINVAL
     with pytest.raises(eik.EikError) as e:
-        eik.solve(speed2, 1.0, [0], opts={"update": 3})
+        eik.solve(speed2, 1.0, [0], opts={"update": 4})
     assert e.value.status == eik.EIK_EINVAL
 
 
@@ -127,3 +128,25 @@ def test_dbar_bits_do_not_depend_on_the_schedule():
         if ref is None:
             ref = t
         assert np.array_equal(t.view(np.uint64), ref.view(np.uint64)), opts
+
+
+@pytest.mark.parametrize("form", [1, 2, 3])
+def test_change_tracking_solves_stay_within_rounding(form):
+    """Change tracking (a recomputed value that differs, up or down, replaces the
+    cell's value and re-activates its neighbours): the field stays within
+    rounding of the exact one, and the device residual equals the oracle's."""
+    p = synth.random_problem(14, (160, 230), n_src=2, contrast=8.0, smooth_sigma=1.5, h=0.5)
+    exact = _gpu_field(p, {})["out"].cpu().numpy()
+    prob = _gpu_field(p, {"update": form, "sched_flags": eik.TRACK_CHANGES})
+    t = prob["out"].cpu().numpy()
+    rel = np.max(np.abs(t - exact) / np.maximum(exact, 1e-300))
+    assert rel < 1e-9, rel
+    got = eik.eik_residual(prob, form)
+    assert got == oracle.residual(p.speed, p.h, p.sources, t, form=form)
+
+
+def test_change_tracking_needs_an_explicit_form():
+    speed = torch.ones((16, 16), dtype=torch.float64, device=DEV)
+    with pytest.raises(eik.EikError) as e:
+        eik.solve(speed, 1.0, [0], opts={"sched_flags": eik.TRACK_CHANGES})
+    assert e.value.status == eik.EIK_EINVAL

@@ -180,3 +180,15 @@ def test_newton_variant_one_sided_and_symmetric():
         assert oracle.update_form(3, v, h, tH, tV2) == oracle.update_form(3, v, h, tV2, tH)
     assert oracle.update_form(3, 1.0, 1.0, INF, 2.0) == 3.0
     assert oracle.update_form(3, 1.0, 1.0, INF, INF) == INF
+
+
+def test_upsampled_input_keeps_the_physical_problem():
+    """Table 3's x4 input (nearest-neighbour upsampling by 4 per axis, h / 4): on a
+    constant-speed grid with one source the upsampled solve's axis values are the
+    original ones at the same physical points, k h exactly along the source row."""
+    p = synth.Problem("c", np.ones((6, 9)), 1.0, np.array([4], dtype=np.int64), np.zeros(1))
+    q = synth.upsampled(p, 4)
+    assert q.speed.shape == (24, 36) and q.h == 0.25 and list(q.sources) == [16]
+    t = oracle.fmm(q.speed, q.h, q.sources).t
+    assert np.array_equal(t[0], np.abs(np.arange(36) - 16) * 0.25)
+    assert np.array_equal(synth.upsampled(p, 4).speed[::4, ::4], p.speed)
