@@ -148,9 +148,11 @@ typedef struct {
     int64_t ctas;          /* persistent CTAs launched */
     int64_t trace_n;       /* visit records produced (only the first trace_cap are stored) */
     int64_t detail[9];     /* counters >= 2 only: SM cycles of one thread per CTA spent in
-                              [0] tile load, [1] round phase A, [2] phase B, [3] phase C,
-                              [4] commit and activation; [5] Newton steps, [6] ulp-walk
-                              steps, [7] bisection fallbacks, [8] d-bar evaluations */
+                              [0] tile load, [1] round phase A (acceptance of the previous
+                              round's candidates and evaluation), [2] phase B (d-bar),
+                              [3] 0 (no separate acceptance phase), [4] commit and
+                              activation; [5] Newton steps, [6] ulp-walk steps,
+                              [7] bisection fallbacks, [8] d-bar evaluations */
     double solve_ms;       /* device time of the persistent solve kernel(s), CUDA events
                               recorded on `stream` around each launch */
 } eik_stats;

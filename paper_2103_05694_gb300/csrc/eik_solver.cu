@@ -9,11 +9,12 @@
 // (Theorem 1).
 //
 // GB300 design:
-//  * Work item = a tile of cells (default 2D 16x16, 3D 8x8x4; other shapes by
-//    option), one CTA (one thread per cell) relaxes it in shared memory: tile plus a one-cell
+//  * Work item = a tile of cells (by default 16x16 for one 2D front, 16x8 for 2D
+//    batches of 8 or more sources, 8x4x4 in 3D; other shapes by option), one CTA
+//    (one thread per cell) relaxes it in shared memory: tile plus a one-cell
 //    halo staged with coalesced relaxed loads, x-neighbours by warp shuffles,
 //    y/z neighbours from shared memory, rounds of Jacobi relaxation driven by
-//    per-cell change stamps until the tile is locally converged.
+//    double-buffered tile values until the tile is locally converged.
 //  * Commits are 64-bit atomicMin on the bit pattern of the (non-negative)
 //    arrival time; the minimum committed time on each tile face activates the
 //    neighbour tile across that face (one aggregated push per face).
@@ -63,6 +64,12 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
   const unsigned lo = __reduce_min_sync(
       0xffffffffu, static_cast<unsigned>(v >> 32) == hi ? static_cast<unsigned>(v) : 0xffffffffu);
   return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+
+// A cell's candidate is pending while it differs from the cell's value
+// (+inf: none); accepting it sets the value to it.
+__device__ __forceinline__ bool is_pending(unsigned long long pv, unsigned long long t) {
+  return pv != t && pv != kInfBits;
 }
 
 // Relaxed, GPU-scope accesses (never served from a stale L1 line).
@@ -405,8 +412,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
   constexpr int HZ = (D == 3) ? 1 : 0;
   constexpr int SX = TX + 2, SY = TY + 2, SZ = TZ + 2 * HZ;
   static_assert(32 % TX == 0 || TX == 32, "a tile row must not straddle warps");
-  __shared__ double s_t[SZ][SY][SX];
-  __shared__ unsigned s_stamp[SZ][SY][SX];
+  __shared__ double s_t[2][SZ][SY][SX];     // values at the start of round R: s_t[R & 1]
   __shared__ unsigned long long s_a[D][NT];  // axis minima of the cells on the list
   __shared__ unsigned long long s_c[NT];     // c = fl(fl(h/v)^2) of each cell of the tile
   __shared__ unsigned long long s_best[NT];  // value a candidate must beat
@@ -428,7 +434,6 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
   const int warp = tid >> 5;
   const int lx = tid % TX, ly = (tid / TX) % TY, lz = tid / (TX * TY);
   const int xc = lx + 1, yc = ly + 1, zc = lz + HZ;
-  for (int i = tid; i < SZ * SY * SX; i += NT) (&s_stamp[0][0][0])[i] = 0u;
   s_pv[tid] = kInfBits;
   if (tid == 0) { s_cmin = kInfBits; s_min[0] = s_min[1] = s_min[2] = kInfBits; s_cnt[0] = s_cnt[1] = 0; }
   const double delta = p.ctl->delta;
@@ -518,7 +523,6 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
                 : kInfBits;
     bool active = present;
     if (p.tile_src[tile] && present && is_source(P, gidx)) active = false;
-    s_t[zc][yc][xc] = tv;
     s_c[tid] = cv;
     unsigned pword = 0;
     if (lane == 0) pword = ld_rlx(p.pend + static_cast<size_t>(tile) * kPendWords + warp);
@@ -565,9 +569,12 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
           sx = side ? TX + 1 : 0; sy = iy + 1; sz = iz + HZ;
         }
         const bool in = hx >= 0 && hx < nx && hy >= 0 && hy < ny && hz >= 0 && hz < nz;
-        s_t[sz][sy][sx] = in ? ld_time(T + (hz * ny + hy) * nx + hx) : from_bits(kInfBits);
+        const double hv = in ? ld_time(T + (hz * ny + hy) * nx + hx) : from_bits(kInfBits);
+        s_t[0][sz][sy][sx] = hv;     // the halo is the same in both buffers
+        s_t[1][sz][sy][sx] = hv;
       }
     }
+    s_t[R & 1u][zc][yc][xc] = tv;    // this cell at the start of the pass's first round
     if (tid < 6) s_facemin[tid] = kInfBits;
     if (tid == 0) { s_min[0] = s_min[1] = s_min[2] = kInfBits; s_cnt[0] = 0; s_cnt[1] = 0; }
     __syncthreads();
@@ -583,40 +590,88 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
     const double tv0 = tv;
     bool need = active;
     if (need && !(faces_now & (1 << kFaceFull))) {
-      const bool pend_cell = first ? ((pword >> lane) & 1u) != 0u : s_pv[tid] < kInfBits;
+      const bool pend_cell = first ? ((pword >> lane) & 1u) != 0u : is_pending(s_pv[tid], bits_of(tv));
       need = ((faces_now & 1) && lx == 0) || ((faces_now & 2) && lx == TX - 1) ||
              ((faces_now & 4) && ly == 0) || ((faces_now & 8) && ly == TY - 1) ||
              (D == 3 && (((faces_now & 16) && lz == 0) || ((faces_now & 32) && lz == TZ - 1))) ||
              pend_cell;
     }
-    // Pending candidates live in s_pv (owner-indexed).  The minimum over all
-    // pending candidates of round R accumulates in s_min[R % 3]: the accept
-    // phase of round R-1 adds what stayed pending, the evaluation phase of
-    // round R adds the new candidates.  Three barriers per round.
+    // Pending candidates live in s_pv (owner-indexed); a candidate is pending
+    // while it differs from the cell's value, so accepting it needs no clearing.
+    // The values at the start of round R are in s_t[R & 1].  Accepting round
+    // R-1's candidates and evaluating round R form one phase: each thread
+    // derives its neighbours' acceptance from their candidates and s_t[(R-1) & 1]
+    // (x neighbours by shuffles), and writes its own new value to s_t[R & 1].
+    // Two barriers per round.  The minimum over the candidates pending after
+    // round R accumulates in s_min[R % 3].
     m = kInfBits;
-    unsigned ri = R % 3u;
     unsigned pass_round = 0;
 #pragma unroll 1
     for (;;) {
-      // (A) neighbour minima (x by shuffles) and the exact integer filters; the
-      //     cells that may decrease go on a dense list for the FP64 phase
+      const unsigned b = R & 1u, bo = b ^ 1u;
+      const bool accept = pass_round > 0;
+      unsigned long long lim = 0;
+      if (accept) {
+        // (C) accept round R-1's pending candidates within the band above their minimum
+        m = s_min[(R - 1u) % 3u];
+        ++rounds;
+        if (m >= vlim) break;   // nothing pending below the visit limit (uniform)
+        lim = umin64(bits_of(__dadd_rn(from_bits(m), from_bits(s_band))), vlim - 1);
+      }
+      bool acc = false;
+      const unsigned long long pv = s_pv[tid];
+      if (accept && is_pending(pv, bits_of(tv)) && pv <= lim) {
+        tv = from_bits(pv);
+        acc = true;
+        ++n_dec;
+      }
+      {  // what stays pending takes part in this round's minimum
+        const unsigned long long keep = warp_min64(is_pending(pv, bits_of(tv)) ? pv : kInfBits);
+        if (lane == 0 && keep < kInfBits) atomicMin(&s_min[R % 3u], keep);
+      }
+      if (accept) s_t[b][zc][yc][xc] = tv;
+      // (A) neighbour values after the acceptance, whether they changed, and the
+      //     exact integer filters; the cells that may decrease go on a dense list
+      //     for the FP64 phase
       double xl = __shfl_up_sync(kFull, tv, 1, TX);
       double xr = __shfl_down_sync(kFull, tv, 1, TX);
-      if (lx == 0) xl = s_t[zc][yc][0];
-      if (lx == TX - 1) xr = s_t[zc][yc][TX + 1];
+      const unsigned accbits = __ballot_sync(kFull, acc);
+      bool changed = (lx > 0 && ((accbits >> (lane - 1)) & 1u)) ||
+                     (lx < TX - 1 && ((accbits >> (lane + 1)) & 1u));
+      if (lx == 0) xl = s_t[bo][zc][yc][0];
+      if (lx == TX - 1) xr = s_t[bo][zc][yc][TX + 1];
+      // a neighbour in another warp (or the halo) at offset (dz, dy) and tile
+      // thread offset dt: its value after the acceptance
+      auto across = [&](int dz, int dy, int dt, bool inside) -> double {
+        const double old = s_t[accept ? bo : b][zc + dz][yc + dy][xc];
+        if (!accept || !inside) return old;
+        const unsigned long long q = s_pv[tid + dt];
+        if (is_pending(q, bits_of(old)) && q <= lim) {
+          changed = true;
+          return from_bits(q);
+        }
+        return old;
+      };
+      const double yl = across(0, -1, -TX, ly > 0), yr = across(0, 1, TX, ly < TY - 1);
+      double zl = 0.0, zr = 0.0;
+      if constexpr (D == 3) {
+        zl = across(-1, 0, -TX * TY, lz > 0);
+        zr = across(1, 0, TX * TY, lz < TZ - 1);
+      }
+      if (accept) need = active && changed;
       bool go = false;
       if (need) {
         unsigned long long a[D];
         a[0] = umin64(bits_of(xl), bits_of(xr));
-        a[1] = umin64(bits_of(s_t[zc][yc - 1][xc]), bits_of(s_t[zc][yc + 1][xc]));
-        if constexpr (D == 3)
-          a[D - 1] = umin64(bits_of(s_t[zc - 1][yc][xc]), bits_of(s_t[zc + 1][yc][xc]));
+        a[1] = umin64(bits_of(yl), bits_of(yr));
+        if constexpr (D == 3) a[D - 1] = umin64(bits_of(zl), bits_of(zr));
         unsigned long long amin = a[0];
 #pragma unroll
         for (int k = 1; k < D; ++k) amin = umin64(amin, a[k]);
         // change tracking compares with the cell's value (a recomputed value may
         // also be larger); otherwise a candidate must beat value and pending
-        const unsigned long long best = p.track_changes ? bits_of(tv) : umin64(bits_of(tv), s_pv[tid]);
+        const unsigned long long best =
+            p.track_changes ? bits_of(tv) : umin64(bits_of(tv), is_pending(pv, bits_of(tv)) ? pv : kInfBits);
         go = amin < kInfBits && (p.track_changes || best > amin);
         if (go) {
 #pragma unroll
@@ -625,17 +680,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         }
         ++n_evals;
       }
-      if (pass_round == 0 && !first) {
-        // candidates still pending from the previous pass of this visit take
-        // part in this round's minimum (the buffers were reset for the pass)
-        const unsigned long long keep = warp_min64(s_pv[tid]);
-        if (lane == 0 && keep < kInfBits) atomicMin(&s_min[ri], keep);
-      }
       ++pass_round;
       {
         const unsigned bal = __ballot_sync(kFull, go);
         int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&s_cnt[R & 1u], __popc(bal));
+        if (lane == 0 && bal) base = atomicAdd(&s_cnt[b], __popc(bal));
         base = __shfl_sync(kFull, base, 0);
         if (go) s_list[base + __popc(bal & ((1u << lane) - 1u))] = static_cast<unsigned short>(tid);
       }
@@ -646,7 +695,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
       //     pass over a window of points); else one lane per cell.  Only warps
       //     holding work take part.
       {
-        const int cnt = s_cnt[R & 1u];
+        const int cnt = s_cnt[b];
+        if (tid == 0) {
+          s_cnt[bo] = 0;                          // the list of round R+1
+          s_min[(R + 1u) % 3u] = kInfBits;        // the minimum after round R+1
+        }
         unsigned long long nv = kInfBits;
         bool part = false;
         if (ARITH == kArithFp64 && cnt <= p.lane_group_cells && cnt * 4 <= NT && !p.update) {
@@ -695,45 +748,12 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         }
         if (part) {   // warp-uniform
           nv = warp_min64(nv);
-          if (lane == 0 && nv < kInfBits) atomicMin(&s_min[ri], nv);
+          if (lane == 0 && nv < kInfBits) atomicMin(&s_min[R % 3u], nv);
         }
       }
       __syncthreads();                                              // barrier 2
       if (timing) { const long long c1 = clock64(); cyc[2] += c1 - c0; c0 = c1; }
-      // (C) accept the pending candidates within the band above the minimum
-      m = s_min[ri];
-      const unsigned rn = ri == 2u ? 0u : ri + 1u;
-      if (tid == 0) {
-        s_cnt[(R + 1u) & 1u] = 0;
-        s_min[rn == 2u ? 0u : rn + 1u] = kInfBits;   // the buffer of round R+2
-      }
-      ++rounds;
-      if (m >= vlim) break;   // nothing pending below the visit limit (uniform)
-      const unsigned long long lim =
-          umin64(bits_of(__dadd_rn(from_bits(m), from_bits(s_band))), vlim - 1);
-      {
-        const unsigned long long pv = s_pv[tid];
-        unsigned long long keep = kInfBits;
-        if (pv <= lim) {
-          tv = from_bits(pv);
-          s_pv[tid] = kInfBits;
-          s_t[zc][yc][xc] = tv;
-          s_stamp[zc][yc][xc] = R;
-          ++n_dec;
-        } else {
-          keep = pv;
-        }
-        keep = warp_min64(keep);
-        if (lane == 0 && keep < kInfBits) atomicMin(&s_min[rn], keep);
-      }
-      __syncthreads();                                              // barrier 3
-      if (timing) { const long long c1 = clock64(); cyc[3] += c1 - c0; c0 = c1; }
-      bool nb = s_stamp[zc][yc][xc - 1] == R || s_stamp[zc][yc][xc + 1] == R ||
-                s_stamp[zc][yc - 1][xc] == R || s_stamp[zc][yc + 1][xc] == R;
-      if constexpr (D == 3) nb = nb || s_stamp[zc - 1][yc][xc] == R || s_stamp[zc + 1][yc][xc] == R;
-      need = active && nb;
       ++R;
-      ri = rn;
       if (rounds >= kMaxRounds) {   // uniform across the CTA
         if (tid == 0) raise_status(p.ctl, kEtimeout, 7);
         break;
@@ -753,13 +773,14 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
       // a face value can change the cell across the face only if it is below
       // that cell's value (causality; the loaded halo value is an upper bound).
       // Change tracking activates on any change.
-      if (lx == 0 && (track || tb < bits_of(s_t[zc][yc][xc - 1]))) atomicMin(&s_facemin[0], tb);
-      if (lx == TX - 1 && (track || tb < bits_of(s_t[zc][yc][xc + 1]))) atomicMin(&s_facemin[1], tb);
-      if (ly == 0 && (track || tb < bits_of(s_t[zc][yc - 1][xc]))) atomicMin(&s_facemin[2], tb);
-      if (ly == TY - 1 && (track || tb < bits_of(s_t[zc][yc + 1][xc]))) atomicMin(&s_facemin[3], tb);
+      const auto &H = s_t[0];   // halo entries (both buffers hold them)
+      if (lx == 0 && (track || tb < bits_of(H[zc][yc][xc - 1]))) atomicMin(&s_facemin[0], tb);
+      if (lx == TX - 1 && (track || tb < bits_of(H[zc][yc][xc + 1]))) atomicMin(&s_facemin[1], tb);
+      if (ly == 0 && (track || tb < bits_of(H[zc][yc - 1][xc]))) atomicMin(&s_facemin[2], tb);
+      if (ly == TY - 1 && (track || tb < bits_of(H[zc][yc + 1][xc]))) atomicMin(&s_facemin[3], tb);
       if constexpr (D == 3) {
-        if (lz == 0 && (track || tb < bits_of(s_t[zc - 1][yc][xc]))) atomicMin(&s_facemin[4], tb);
-        if (lz == TZ - 1 && (track || tb < bits_of(s_t[zc + 1][yc][xc]))) atomicMin(&s_facemin[5], tb);
+        if (lz == 0 && (track || tb < bits_of(H[zc - 1][yc][xc]))) atomicMin(&s_facemin[4], tb);
+        if (lz == TZ - 1 && (track || tb < bits_of(H[zc + 1][yc][xc]))) atomicMin(&s_facemin[5], tb);
       }
     }
     __threadfence();
@@ -815,7 +836,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
 
     // cells still pending are deferred to a later visit
     {
-      const bool deferred = s_pv[tid] < kInfBits;
+      const bool deferred = is_pending(s_pv[tid], bits_of(tv));
       s_pv[tid] = kInfBits;
       const unsigned pend_bits = __ballot_sync(kFull, deferred);
       if (lane == 0) {
