@@ -49,7 +49,7 @@ L2_FLUSH_BYTES = 512 << 20
 # ncu DRAM bytes (read + write) per launch of the persistent kernel in its default
 # configuration, from the one-pass captures summarised in profiles/ (refresh them
 # whenever the kernel changes)
-MEASURED_TRAFFIC = {"layered_2d": 28121344 + 678400, "checker_3d": 279772672 + 109199360}
+MEASURED_TRAFFIC = {"layered_2d": 28160000 + 682496, "checker_3d": 280830720 + 109687040}
 
 WORKLOADS = {
     "layered_2d": "2d_2301x751_layered_h4_1src",
