@@ -452,7 +452,8 @@ __global__ void adj_tile_seed_kernel(const AdjProb *probs, int nprob, int64_t to
 #define EIK_ADJ_TILE_MINB 4
 #endif
 template <int D, int TX, int TY, int TZ>
-__global__ void __launch_bounds__(TX * TY * TZ, EIK_ADJ_TILE_MINB) adj_tiles_kernel(
+__global__ void __launch_bounds__(TX * TY * TZ, (EIK_ADJ_TILE_MINB * 256 + TX * TY * TZ - 1) /
+                                                     (TX * TY * TZ)) adj_tiles_kernel(
     const AdjProb *probs, int nprob, TileQueue q) {
   constexpr int NT = TX * TY * TZ;
   constexpr unsigned kClear = 0x40u, kDid = 0x80u;   // s_flags; bits 0..2D-1: halo sides

@@ -276,7 +276,14 @@ cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, A
 // >= total_tiles, set up by the launch).  ndim: of every problem (one tile shape
 // per launch).  The tiles are kAdjTile2 in 2D and kAdjTile3 in 3D.  ctas_per_sm
 // caps the persistent CTAs per SM (0: occupancy).
-constexpr int kAdjTile2[3] = {16, 16, 1};
+// 2D adjoint tile (compile-time; 16x16 measured fastest against 32x16 and 32x8)
+#ifndef EIK_ADJ_TILE2_X
+#define EIK_ADJ_TILE2_X 16
+#endif
+#ifndef EIK_ADJ_TILE2_Y
+#define EIK_ADJ_TILE2_Y 16
+#endif
+constexpr int kAdjTile2[3] = {EIK_ADJ_TILE2_X, EIK_ADJ_TILE2_Y, 1};
 constexpr int kAdjTile3[3] = {8, 8, 4};
 cudaError_t launch_adjoint_tiles(const AdjProb *probs_dev, int nprob, int64_t total,
                                  int64_t total_tiles, int ndim, AdjCtl *ctl, unsigned *tile_state,
