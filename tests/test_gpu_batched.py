@@ -99,3 +99,18 @@ def test_plan_graph_replay_bit_exact(ndim):
         _check(probs)
         assert st["good"] > 0
     plan.close()
+
+
+@pytest.mark.parametrize("shape,k_delta", [((256, 384), 1.0), ((300, 200), 0.5), ((40, 48, 56), 0.5)])
+def test_small_rings_and_narrow_buckets(shape, k_delta):
+    """Rings of 16 entries per bucket slot (grown by the capacity retry when a
+    bucket holds more) and buckets narrow enough that slots serve several
+    buckets in turn: small, contended rings under the reservation protocol and
+    the sequence-tagged positions still give the oracle's bits."""
+    p = synth.random_problem(23, shape, n_src=1, contrast=6.0, smooth_sigma=1.5, h=1.0)
+    r = eik.solve(torch.from_numpy(p.speed).to(DEV), p.h, torch.from_numpy(p.sources).to(DEV),
+                  opts={"capacity": 16, "k_delta": k_delta, "counters": 1})
+    torch.cuda.synchronize()
+    ref = oracle.fmm(p.speed, p.h, p.sources).t
+    assert np.array_equal(r.t.cpu().numpy().view(np.uint64), ref.view(np.uint64))
+    assert r.stats["pushes"] > 1000
