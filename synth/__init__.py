@@ -148,28 +148,33 @@ def smooth_model_3d_128(n: int = 128) -> np.ndarray:
     return smooth_random_volume(n, 4, 1500.0, 4500.0, 8.0)
 
 
+def batched_3d_item(i: int, model: np.ndarray | None = None, n_lattice: int = 8,
+                    model_n: int = 128) -> Problem:
+    """Problem i of batched_3d, generated alone (`model`: the shared lattice
+    model, if already at hand)."""
+    h = 10.0
+    if i < n_lattice * n_lattice:
+        if model is None:
+            model = smooth_model_3d_128(model_n)
+        yy, xx = 8 + 16 * (i // n_lattice), 8 + 16 * (i % n_lattice)
+        src = np.array([_flat(model.shape, 0, yy, xx)], dtype=np.int64)
+        return Problem(f"shared_src_{yy}_{xx}", model, h, src, np.zeros(1), {"shared_model": True})
+    k = i - n_lattice * n_lattice
+    rng = np.random.Generator(np.random.PCG64(400 + k))
+    side = int(rng.integers(64, 193))
+    v = smooth_random_volume(side, 400 + k, 1500.0, 4500.0, 8.0)
+    ns = int(rng.integers(1, 5))
+    src = np.unique(rng.integers(0, side ** 3, ns)).astype(np.int64)
+    return Problem(f"grid_{k}_{side}", v, h, src, np.zeros(src.size), {"shared_model": False})
+
+
 def batched_3d(n_lattice: int = 8, n_grids: int = 24, model_n: int = 128) -> list[Problem]:
     """Batched multi-source work: one solve per source on a lattice of surface
     sources over a shared smooth 128^3 model, plus independent grids of uneven
     size (side uniform in 64..192, own model, 1-4 sources solved together)."""
-    h = 10.0
     model = smooth_model_3d_128(model_n)
-    probs: list[Problem] = []
-    coords = [8 + 16 * i for i in range(n_lattice)]
-    for yy in coords:
-        for xx in coords:
-            src = np.array([_flat(model.shape, 0, yy, xx)], dtype=np.int64)
-            probs.append(Problem(f"shared_src_{yy}_{xx}", model, h, src, np.zeros(1),
-                                 {"shared_model": True}))
-    for k in range(n_grids):
-        rng = np.random.Generator(np.random.PCG64(400 + k))
-        side = int(rng.integers(64, 193))
-        v = smooth_random_volume(side, 400 + k, 1500.0, 4500.0, 8.0)
-        ns = int(rng.integers(1, 5))
-        src = np.unique(rng.integers(0, side ** 3, ns)).astype(np.int64)
-        probs.append(Problem(f"grid_{k}_{side}", v, h, src, np.zeros(src.size),
-                             {"shared_model": False}))
-    return probs
+    return [batched_3d_item(i, model, n_lattice, model_n)
+            for i in range(n_lattice * n_lattice + n_grids)]
 
 
 def tomography_2d_1024(n: int = 1024, n_src: int = 32, n_rcv: int = 512, z_c: float | None = None):
