@@ -259,7 +259,7 @@ def _oracle_core_worker(workload, items, barrier, out):
             s = int(cfg["sources"][i])
             observed = oracle.fmm(cfg["true"], h, [s]).t     # the observed data is input
             work.append(("tomo", (v0, h, s, rcv, observed)))
-    barrier.wait()
+    barrier.wait(timeout=600)       # a worker that failed to start breaks the barrier
     t0 = time.perf_counter()
     useful = 0
     for kind, w in work:
@@ -294,9 +294,13 @@ def cpu_baseline_all_cores(args, per_unit_s: float, seconds: float = 12.0):
              for a in assign]
     for pr in procs:
         pr.start()
-    res = [out.get() for _ in procs]
-    for pr in procs:
-        pr.join()
+    try:
+        res = [out.get(timeout=900 + 20 * seconds) for _ in procs]
+    finally:
+        for pr in procs:
+            pr.join(timeout=60)
+            if pr.is_alive():
+                pr.terminate()
     useful = sum(u for u, _ in res)
     wall = max(t for _, t in res)
     return {"value": useful / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
