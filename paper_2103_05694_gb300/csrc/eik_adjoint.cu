@@ -18,14 +18,19 @@
 // fl(fl(h^2 fl(1 / v)) / S), and counts for every cell the downwind cells that
 // use it.  The dependent part is then one multiply-add per downwind neighbour.
 //
-// Schedule: Kahn order, level by level.  Cells with count 0 form the first
-// frontier.  One cooperative persistent launch processes a frontier (each cell
-// pulls lambda from its downwind cells, writes lambda and dL/ds, decrements its
-// upwind cells' counts and appends those that reach zero to the next
-// frontier), then its blocks meet at a grid barrier bounded by %globaltimer.
-// (Letting a thread follow the cells it releases does not pay on this graph:
-// in 2D most cells have two downwind users, so chains merge after about two
-// steps while the few long chains stretch every frontier.)
+// Two schedules process the cells in dependency (Kahn) order with the same
+// operations in the same order, so their results are identical:
+//  * tiles (the default; see "Tile schedule" below): persistent CTAs take
+//    tiles from a queue and run the order inside a tile in shared memory,
+//    handing cross-tile dependencies over through counts and the queue;
+//  * levels: cells with count 0 form the first frontier; one cooperative
+//    persistent launch processes a frontier (each cell pulls lambda from its
+//    downwind cells, writes lambda and dL/ds, decrements its upwind cells'
+//    counts and appends those that reach zero to the next frontier), then its
+//    blocks meet at a grid barrier bounded by %globaltimer.  (Letting a thread
+//    follow the cells it releases does not pay on this graph: in 2D most cells
+//    have two downwind users, so chains merge after about two steps while the
+//    few long chains stretch every frontier.)
 #include <cstdint>
 #include <cuda_runtime.h>
 
