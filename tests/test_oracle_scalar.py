@@ -86,8 +86,8 @@ def test_dbar_monotone_exhaustive_near_tables(table):
     _, v, h, tH, tV, _ = rows[0]
     r = h / v
     c = oracle.cell_c(v, h)
-    tHs = _neighbourhood(tH, 16)
-    tVs = _neighbourhood(tV, 16)
+    tHs = _neighbourhood(tH, 64)      # every pair within +-64 ulps of the table's inputs
+    tVs = _neighbourhood(tV, 64)
     grid = np.array([[oracle.dbar([x, y], r, c) for y in tVs] for x in tHs])
     assert np.all(np.diff(grid, axis=0) >= 0.0)
     assert np.all(np.diff(grid, axis=1) >= 0.0)
