@@ -391,10 +391,12 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 // Persistent kernel: pop a tile, relax it in shared memory, commit, activate
 // neighbour tiles, repeat until no work is left anywhere.
 //
-// A visit finalises cells in increasing order of time (delta-stepping inside
-// the tile): every round evaluates the cells whose neighbours changed, takes
-// the CTA-wide minimum m of the pending candidates and accepts the candidates
-// within `band` of m (one cell's travel time: those cannot improve each other).
+// A visit relaxes cells in roughly increasing order of time (delta-stepping
+// inside the tile): every round accepts the pending candidates within `band`
+// cell travel times of their CTA-wide minimum m and evaluates the cells whose
+// neighbours changed.  Within one travel time of m candidates cannot improve
+// each other; the default, wider band also accepts provisional values, which
+// later decreases correct (fewer rounds, more updates).
 // Candidates at or above the visit limit V = (lowest active bucket + window
 // + 1) * delta are deferred: recorded in the tile's pending mask and the tile
 // re-queued at their bucket.  Only accepted values are written to memory.
