@@ -92,6 +92,57 @@ def closed_form_axis(n: int = 33, h: float = 2.0 ** -7):
     return speed, h, [m * n + m], m
 
 
+def g_xyz(tau: float, a) -> float:
+    """G(tau) of the definition in Python floats (IEEE binary64, one rounding per
+    operation, no fused multiply-add): m_k = max(tau - a_k, 0), terms added in
+    axis order x, y, z starting from the x term."""
+    g = None
+    for ak in a:
+        m = tau - ak
+        if not m > 0.0:
+            m = 0.0
+        q = m * m
+        g = q if g is None else g + q
+    return g
+
+
+def certified_dbar(tau: float, a, c: float) -> bool:
+    """tau is the smallest double with G(tau) >= c (the definition of d-bar)."""
+    return g_xyz(tau, a) >= c and g_xyz(math.nextafter(tau, -math.inf), a) < c
+
+
+def fixed_point_violations(speed: np.ndarray, h: float, sources, t: np.ndarray) -> int:
+    """Cells of a solved grid where t is not d-bar of its neighbours' values, with
+    c = fl(fl(h / v)^2) and G in x, y, z order, all in Python floats (sources:
+    their time must be finite and unchanged by the check)."""
+    src = set(int(s) for s in np.atleast_1d(sources))
+    tt = np.asarray(t, dtype=np.float64)
+    shape = tt.shape
+    flat = tt.reshape(-1)
+    bad = 0
+    for idx in range(flat.size):
+        if idx in src:
+            continue
+        coord = np.unravel_index(idx, shape)
+        a = []
+        for ax in range(len(shape) - 1, -1, -1):      # x (last axis) first
+            best = math.inf
+            for step in (-1, 1):
+                cc = list(coord)
+                cc[ax] += step
+                if 0 <= cc[ax] < shape[ax]:
+                    best = min(best, float(tt[tuple(cc)]))
+            a.append(best)
+        r = h / float(speed[coord])
+        c = r * r
+        ti = float(flat[idx])
+        if all(x == math.inf for x in a):
+            bad += ti != math.inf
+        elif not certified_dbar(ti, a, c):
+            bad += 1
+    return bad
+
+
 def run_pin_suite(orc) -> list[str]:
     """Run the cheap pins against an oracle module; return the names that fail."""
     import synth
@@ -147,7 +198,34 @@ def run_pin_suite(orc) -> list[str]:
                 return False
         return True
 
+    def dbar_definition():
+        # d-bar against its definition in Python floats: random 2D / 3D minima in
+        # axis order (not sorted), c = fl(fl(h / v)^2) from non-dyadic h and v
+        rng = np.random.Generator(np.random.PCG64(29))
+        for i in range(3000):
+            D = 2 if i % 3 == 0 else 3
+            a, _ = random_minima(rng, D)
+            h = float(rng.uniform(0.1, 20.0))
+            base = min(x for x in a if x != INF)
+            v = h / (float(rng.uniform(0.05, 1.0)) * max(base, 1e-3) * float(rng.choice([1e-3, 0.05, 0.5])))
+            r = h / v
+            if not certified_dbar(orc.dbar(a, r, r * r), a, r * r):
+                return False
+        return True
+
+    def grid_definition():
+        # every cell of small solved grids (2D and 3D, non-dyadic spacing, 10:1
+        # speeds) is d-bar of its neighbours by the Python-float definition
+        for shape, seed in (((1, 40), 5), ((9, 11), 6), ((5, 6, 7), 7)):
+            p = synth.random_problem(seed, shape, n_src=2, contrast=10.0, h=0.37)
+            t = orc.fmm(p.speed, p.h, p.sources).t
+            if fixed_point_violations(p.speed, p.h, p.sources, t):
+                return False
+        return True
+
     pin("tables", tables)
+    pin("dbar_definition", dbar_definition)
+    pin("grid_definition", grid_definition)
     pin("exact_roots", roots)
     pin("axes", axes)
     pin("plane3d", plane3d)

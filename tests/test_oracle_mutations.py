@@ -2,7 +2,8 @@
 
 Each case copies oracle.c, plants one plausible mistake (a dropped term, a wrong
 sign or index, transposed axes, the h^2/v misreading, a missing push, a
-missing upwind max), builds
+missing upwind max, G summed in reverse axis order, c rounded as
+fl(h^2)/fl(v^2)), builds
 the copy with the oracle's own flags and runs the cheap pins of
 tests/oracle_pins.py against it in a child process.  The pins must fail (or the
 child must not finish) for every mutant, and must all pass for the real oracle.
@@ -30,6 +31,12 @@ MUTANTS = {
     "no_push_on_decrease": ("                    if (heap_push(&hp, tau, m)) goto fail;\n",
                             "                    if (k > 0 && heap_push(&hp, tau, m)) goto fail;\n"),
     "dtilde_sign": ("    double disc = s * s - 2.0 * (q - c);\n", "    double disc = s * s - 2.0 * (q + c);\n"),
+    # G summed in the reverse axis order (z, y, x) instead of x, y, z
+    "reversed_G_term_order": ("    for (int k = 0; k < D; ++k) {\n        double m = tau - a[k];\n",
+                              "    for (int k = D - 1; k >= 0; --k) {\n        double m = tau - a[k];\n"),
+    # c rounded as fl(h^2) / fl(v^2) in the grid solvers (consistently in the
+    # residual too) instead of fl(fl(h/v)^2)
+    "c_from_squares": ("        c[i] = r[i] * r[i];\n", "        c[i] = (h * h) / (v[i] * v[i]);\n"),
     "missing_upwind_max": ("        if (!(m > 0.0)) m = 0.0;     /* max(., 0); a_k = +inf gives -inf -> 0 */\n",
                            "        if (!(m > -1e300)) m = 0.0;\n"),
 }
@@ -68,6 +75,10 @@ def test_mutant_is_caught(name, tmp_path):
     old, new = MUTANTS[name]
     assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
     mutated = src.replace(old, new, 1)
+    if name == "c_from_squares":    # the residual's own constant, consistently
+        old2 = "        double r = h / v[i];\n        double c = r * r;\n"
+        assert mutated.count(old2) == 1
+        mutated = mutated.replace(old2, "        double r = h / v[i];\n        double c = (h * h) / (v[i] * v[i]);\n")
     csrc = tmp_path / "mut.c"
     csrc.write_text(mutated)
     lib = tmp_path / "libmut.so"
