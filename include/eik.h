@@ -103,7 +103,17 @@ typedef struct {
                               section: a recomputed value that differs from the cell's, up or
                               down, replaces it and re-activates the neighbours (termination
                               is no longer guaranteed: after 256 tile visits per tile the
-                              solve stops with EIK_ETIMEOUT) */
+                              solve stops with EIK_ETIMEOUT);
+                              bit 6 (eik_solve, eik_solve_batched, eik_solve_noalloc, plans,
+                              eik_autotune, eik_adjoint): the `speed` arrays hold slowness s
+                              instead, and the speed used is v = fl(1/s), correctly rounded, on
+                              the device (the traveltime-tomography parameterisation);
+                              bit 7 (eik_adjoint only): problems whose dL_dslowness pointers
+                              are equal form a group, and that array receives the sum of their
+                              gradients, +0 + g_first + ... + g_last in problem order, each
+                              addition rounded to nearest (deterministic; the per-problem
+                              gradients go to library workspace, 8 bytes per cell of the
+                              batch) */
     void *trace;           /* optional device buffer of trace_cap 32-byte visit records
                               {int64 t_claim_ns, t_end_ns; uint32 tile, lowest bucket,
                               rounds, flags}; NULL: no trace */
@@ -211,7 +221,7 @@ eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches, void *str
  * cudaMalloc / cudaFree would synchronise the device.)
  *   Arguments and results as eik_solve, with these limits:
  *   - speed, src_idx, src_t (if not NULL) and out_t must be device pointers;
- *   - at most 2^20 cells, 2^15 tiles (2D tiles 32x8, 3D tiles 16x4x4) and
+ *   - at most 2^20 cells, 2^15 tiles (2D tiles 16x16, 3D tiles 8x8x4) and
  *     2048 sources; larger inputs return EIK_EINVAL before anything runs;
  *   - no capacity retry: a frontier overflow returns EIK_ECAPACITY;
  *   - stats->solve_ms, max_queue and the timing details stay 0;
@@ -219,12 +229,13 @@ eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches, void *str
  *   - the first tile shape (16x16, 8x8x4) whatever the dimension, k_delta 16 (2D) /
  *     2 (3D) unless opts->k_delta is set; opts->tile must be 0.
  * Scratch memory is one fixed file-scope device array of about 21 MB, present
- * on every GPU that loads the library until the process exits.  The first
- * call on a device looks up that array's device address (once per device);
- * make that first call before any stream capture.  Every call shares the
+ * on every GPU that loads the library until the process exits.  Each call
+ * looks up that array's device address on the current device
+ * (cudaGetSymbolAddress, which allocates nothing).  Every call shares the
  * array and clears what must start at zero; calls whose GPU work overlaps
  * (other streams, other host threads) race on it and must be serialised by
- * the caller.  Synchronises `stream` to read the status. */
+ * the caller.  Every failure leaves its reason for eik_last_error().
+ * Synchronises `stream` to read the status. */
 eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int64_t *dims,
                              const int64_t *src_idx, const double *src_t, int64_t nsrc,
                              double *out_t, const eik_opts *opts, eik_stats *stats,
@@ -236,7 +247,10 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
  * times solved for exactly that problem (speed, h, sources); dL_dt[i] (NULL,
  * or dL_dt == NULL: zero) is d(loss)/d(t) per cell; dL_dslowness[i] receives
  * d(loss)/d(s) with slowness s = 1/v per cell (written, not accumulated; 0 at
- * sources and unreachable cells).  For a reached non-source cell n with axis
+ * sources and unreachable cells; with opts->sched_flags bit 7, problems that
+ * share an output array receive their gradients' sum in problem order; with
+ * bit 6, probs[i].speed holds slowness and v = fl(1/s)).  For a reached
+ * non-source cell n with axis
  * minima a_k and active axes A = {k : a_k < t_n}, S_n = sum_A (t_n - a_k):
  *   lambda_n = dL_dt_n + sum_{downwind m} lambda_m (t_m - t_n) / S_m
  *   (halved where m's two neighbours on that axis tie), downwind neighbours in
@@ -263,6 +277,17 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
 eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
                        double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,
                        void *stream);
+
+/* Fixed-order sum of k arrays of n doubles: dst[i] = (((+0 + src[0][i]) +
+ * src[1][i]) + ...) + src[k-1][i], each addition rounded to nearest in that
+ * order (k = 0 writes +0).  src is a host array of k device pointers; dst a
+ * device pointer (it may alias none of the inputs).  This is the cross-source
+ * gradient sum of eik_adjoint's sched_flags bit 7, exposed for sharded
+ * tomography: ranks that solved different sources gather their per-source
+ * gradients on one device and sum them here in source order, which gives the
+ * bits of the single-device step.  (Not in the paper.)  EIK_EINVAL for
+ * non-device pointers.  Synchronises `stream`. */
+eik_status eik_sum_ordered(const double *const *src, int k, double *dst, int64_t n, void *stream);
 
 /* Update-form ablation (Mitigation Strategies section, Tables 1 and 2): for
  * i < n, out[i] = one application of Algorithm 1 at a cell of speed v = speed[i]

@@ -144,6 +144,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     L.eik_residual.argtypes = [ctypes.POINTER(EikProblem), ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), vp]
     L.eik_residual.restype = ctypes.c_int
+    L.eik_sum_ordered.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, i64, vp]
+    L.eik_sum_ordered.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -151,7 +153,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
 EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "eik_last_error",
             "eik_abi_version", "eik_selftest", "eik_solve_noalloc", "eik_plan_create",
             "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy", "eik_adjoint",
-            "eik_kernel_launches", "eik_autotune", "eik_eval_update", "eik_residual"]
+            "eik_kernel_launches", "eik_autotune", "eik_eval_update", "eik_residual",
+            "eik_sum_ordered"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3", "group2x8", "group3x8",
                    "group2x4", "dbar2_fp64", "dbar3_fp64"]
@@ -248,7 +251,7 @@ def eik_solve_noalloc(speed_ptr: int, h: float, ndim: int, dims, src_ptr: int | 
                              out_ptr, ctypes.byref(o) if o is not None else None, ctypes.byref(st),
                              stream)
     if rc != EIK_OK:
-        raise EikError(rc, "eik_solve_noalloc")
+        raise EikError(rc, eik_last_error())
     return st.as_dict()
 
 
@@ -300,23 +303,12 @@ def solve(speed, h: float, sources, src_t=None, out=None, opts: dict | None = No
 
 
 def eik_solve_batched(problems: list[dict], opts: dict | None = None, stream=None) -> dict:
-    """Batched call.  Each problem dict holds torch CUDA tensors: speed, sources,
-    optional src_t, out, and h.  All problems run in one persistent launch."""
+    """Batched call.  Each problem dict holds speed, sources, optional src_t, out
+    (torch tensors on the device or in host memory, or numpy arrays; host
+    buffers are staged inside the call) and h.  All problems run in one
+    persistent launch."""
     L = load_library()
-    arr = (EikProblem * len(problems))()
-    keep = []
-    for i, p in enumerate(problems):
-        sp = p["speed"]
-        arr[i].speed = _ptr(sp)
-        arr[i].h = float(p["h"])
-        arr[i].ndim = sp.ndim
-        for k in range(3):
-            arr[i].dims[k] = int(sp.shape[k]) if k < sp.ndim else 1
-        arr[i].src_idx = _ptr(p["sources"])
-        arr[i].src_t = _ptr(p.get("src_t"))
-        arr[i].nsrc = int(p["sources"].numel())
-        arr[i].out_t = _ptr(p["out"])
-        keep.append(p)
+    arr = _problem_array(problems)
     st = EikStats()
     o = _make_opts(opts)
     rc = L.eik_solve_batched(arr, len(problems), ctypes.byref(o) if o is not None else None,
@@ -429,6 +421,11 @@ class Plan:
 # between grid barriers, or tiles in shared memory handed over through a queue
 ADJ_LEVELS = 1 << 3
 ADJ_TILES = 2 << 3
+# opts["sched_flags"] bit 6: the "speed" arrays hold slowness s (v = fl(1/s) on the
+# device); bit 7 (eik_adjoint): problems sharing a gradient array receive the sum of
+# their gradients in problem order
+SLOWNESS_INPUT = 1 << 6
+SUM_SHARED_GRADIENTS = 1 << 7
 
 
 def eik_adjoint(problems: list[dict], dL_dt: list, dL_ds: list, opts: dict | None = None,
@@ -506,6 +503,18 @@ def eik_residual(problem: dict, form: int = 0, stream=None) -> tuple[int, float]
     return int(bad.value), float(rel.value)
 
 
+def eik_sum_ordered(srcs: list, out, stream=None):
+    """out = +0 + srcs[0] + srcs[1] + ... in list order, each addition rounded to
+    nearest (torch CUDA float64 tensors of out's size; the library's kernel)."""
+    n = len(srcs)
+    ptrs = (ctypes.c_void_p * max(n, 1))(*[_ptr(x) for x in srcs])
+    rc = load_library().eik_sum_ordered(ptrs, n, _ptr(out), int(out.numel()),
+                                        _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    return out
+
+
 def _make_eikonal_fn():
     import torch
 
@@ -515,37 +524,36 @@ def _make_eikonal_fn():
 
         forward(slowness, h, sources): slowness (float64 CUDA tensor, 2D or 3D),
         sources a list of int64 tensors (flat indices), one solve per entry, all
-        in one persistent launch.  Returns t with shape (len(sources), *grid).
-        backward: d(loss)/d(slowness) summed over the solves."""
+        in one persistent launch; the library converts slowness to speed
+        (v = fl(1/s)) on the device.  Returns t with shape (len(sources), *grid).
+        backward: d(loss)/d(slowness) summed over the solves in source order by
+        the library (eik_adjoint with SUM_SHARED_GRADIENTS).  The binding only
+        allocates and passes pointers."""
 
         @staticmethod
         def forward(ctx, slowness, h, sources):
-            speed = torch.reciprocal(slowness).contiguous()
-            outs = []
-            probs = []
-            for src in sources:
-                out = torch.empty_like(speed)
-                probs.append({"speed": speed, "h": h, "sources": src, "out": out})
-                outs.append(out)
-            eik_solve_batched(probs)
-            t = torch.stack(outs)
-            ctx.save_for_backward(speed, t)
+            if slowness.dtype != torch.float64 or not slowness.is_contiguous():
+                raise ValueError("slowness must be a contiguous float64 tensor")
+            t = torch.empty((len(sources),) + tuple(slowness.shape), dtype=slowness.dtype,
+                            device=slowness.device)
+            probs = [{"speed": slowness, "h": h, "sources": src, "out": t[i]}
+                     for i, src in enumerate(sources)]
+            eik_solve_batched(probs, {"sched_flags": SLOWNESS_INPUT})
+            ctx.save_for_backward(slowness, t)
             ctx.h = h
             ctx.sources = sources
             return t
 
         @staticmethod
         def backward(ctx, grad_t):
-            speed, t = ctx.saved_tensors
-            probs = []
-            grads = []
-            gts = []
-            for i, src in enumerate(ctx.sources):
-                probs.append({"speed": speed, "h": ctx.h, "sources": src, "out": t[i].contiguous()})
-                grads.append(torch.empty_like(speed))
-                gts.append(grad_t[i].contiguous())
-            eik_adjoint(probs, gts, grads)
-            return torch.stack(grads).sum(dim=0), None, None
+            slowness, t = ctx.saved_tensors
+            grad_t = grad_t.contiguous()
+            grad = torch.empty_like(slowness)
+            probs = [{"speed": slowness, "h": ctx.h, "sources": src, "out": t[i]}
+                     for i, src in enumerate(ctx.sources)]
+            eik_adjoint(probs, [grad_t[i] for i in range(len(probs))], [grad] * len(probs),
+                        {"sched_flags": SLOWNESS_INPUT | SUM_SHARED_GRADIENTS})
+            return grad, None, None
 
     return EikonalFn
 

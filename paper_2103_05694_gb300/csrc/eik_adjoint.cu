@@ -176,7 +176,9 @@ __global__ void adj_setup_kernel(const AdjProb *probs, int nprob, int64_t total,
       }
     }
     P.mask[n] = mask;
-    const double s = __ddiv_rn(1.0, P.v[n]);
+    // slowness input: v = fl(1/s_in) as the forward used, then s = fl(1/v)
+    const double vn = P.v_is_slowness ? __ddiv_rn(1.0, P.v[n]) : P.v[n];
+    const double s = __ddiv_rn(1.0, vn);
     P.grad[n] = __ddiv_rn(__dmul_rn(P.hh, s), S);
   }
 #pragma unroll

@@ -45,6 +45,10 @@ constexpr int kDefaultWindow[2] = {16, 16};
 constexpr double kDefaultBand[2] = {16.0, 8.0};
 constexpr int kDefaultCtasPerSm[2] = {1, 2};
 constexpr int kMaxRetries = 4;
+// eik_opts.sched_flags bits of the tomography interface
+constexpr int kFlagSlowness = 1 << 6;     // speed arrays hold slowness s; v = fl(1/s) is used
+constexpr int kFlagSumShared = 1 << 7;    // eik_adjoint: equal outputs receive the ordered sum
+int from_slowness(const eik_opts *opts) { return opts && (opts->sched_flags & kFlagSlowness) ? 1 : 0; }
 
 // Grow-only device buffer.
 template <class T>
@@ -83,6 +87,7 @@ struct Workspace {
   DevBuf<Prob> probs;
   DevBuf<Ctl> ctl;
   DevBuf<unsigned long long> count;
+  DevBuf<const double *> sum_ptr;   // eik_sum_ordered's pointer table
   Ctl *ctl_host = nullptr;     // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   uint64_t cap = 0;            // entries per slot
@@ -91,7 +96,7 @@ struct Workspace {
     r.release(); t_stage.release(); v_stage.release(); state.release(); tile_src.release();
     pend.release();
     slots.release(); seq.release(); src_idx.release(); src_t.release(); seeds.release();
-    probs.release(); ctl.release(); count.release();
+    probs.release(); ctl.release(); count.release(); sum_ptr.release();
     if (ctl_host) cudaFreeHost(ctl_host);
     ctl_host = nullptr;
     if (ev0) cudaEventDestroy(ev0);
@@ -102,7 +107,12 @@ struct Workspace {
   }
 };
 
-Workspace g_ws;
+// Workspaces are kept per device (indexed by the CUDA device ordinal); g_dev
+// is the device of the call in progress, set under the API lock.
+constexpr int kMaxDevices = 64;
+int g_dev = 0;
+Workspace g_ws_dev[kMaxDevices];
+Workspace &ws() { return g_ws_dev[g_dev]; }
 
 struct AdjWorkspace {
   int device = -1;
@@ -114,13 +124,15 @@ struct AdjWorkspace {
   DevBuf<eik::AdjProb> probs;
   DevBuf<eik::AdjCtl> ctl;
   DevBuf<int64_t> src;
+  DevBuf<double> gsum;                   // per-problem gradients summed into shared outputs
+  DevBuf<const double *> gptr;           // their addresses, grouped by output
   eik::AdjCtl *ctl_host = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   void release_all() {
     cnt.release(); cnt_out.release(); W.release(); lam.release(); mask.release();
     status.release(); front.release(); ring.release(); tile_state.release();
-    probs.release(); ctl.release(); src.release();
+    probs.release(); ctl.release(); src.release(); gsum.release(); gptr.release();
     if (ctl_host) cudaFreeHost(ctl_host);
     ctl_host = nullptr;
     if (ev0) cudaEventDestroy(ev0);
@@ -129,7 +141,8 @@ struct AdjWorkspace {
     device = -1;
   }
 };
-AdjWorkspace g_adj;
+AdjWorkspace g_adj_dev[kMaxDevices];
+AdjWorkspace &adj() { return g_adj_dev[g_dev]; }
 
 // Workspace of the comparison schedules (opts.schedule 1, 2).
 struct BspWorkspace {
@@ -155,7 +168,22 @@ struct BspWorkspace {
     device = -1;
   }
 };
-BspWorkspace g_bsp;
+BspWorkspace g_bsp_dev[kMaxDevices];
+BspWorkspace &bsp() { return g_bsp_dev[g_dev]; }
+
+}  // namespace
+
+namespace eik {
+std::mutex &api_mutex() { return g_mu; }
+void set_last_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+}  // namespace eik
+
+namespace {
 
 eik_status cuda_fail(cudaError_t e, const char *what) {
   set_err("%s: %s", what, cudaGetErrorString(e));
@@ -184,6 +212,19 @@ bool is_device_ptr(const void *p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Page-locked (pinned or registered) host memory: copies from and to it can
+// be enqueued asynchronously and captured in a CUDA graph.
+bool is_pinned_host(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
 }
 
 uint64_t next_pow2(uint64_t x) {
@@ -231,9 +272,11 @@ eik_status check_problem(const double *speed, double h, int ndim, const int64_t 
   std::vector<int64_t> idx(static_cast<size_t>(nsrc));
   std::vector<double> tt(static_cast<size_t>(nsrc), 0.0);
   if (nsrc > 0) {
+    bool copied = false;
     if (is_device_ptr(src_idx)) {
       CK(cudaMemcpyAsync(idx.data(), src_idx, nsrc * sizeof(int64_t), cudaMemcpyDeviceToHost, stream),
          "copy src_idx");
+      copied = true;
     } else {
       std::memcpy(idx.data(), src_idx, nsrc * sizeof(int64_t));
     }
@@ -241,11 +284,12 @@ eik_status check_problem(const double *speed, double h, int ndim, const int64_t 
       if (is_device_ptr(src_t)) {
         CK(cudaMemcpyAsync(tt.data(), src_t, nsrc * sizeof(double), cudaMemcpyDeviceToHost, stream),
            "copy src_t");
+        copied = true;
       } else {
         std::memcpy(tt.data(), src_t, nsrc * sizeof(double));
       }
     }
-    CK(cudaStreamSynchronize(stream), "sync sources");
+    if (copied) CK(cudaStreamSynchronize(stream), "sync sources");
   }
   std::vector<std::pair<int64_t, double>> st(static_cast<size_t>(nsrc));
   for (int64_t i = 0; i < nsrc; ++i) {
@@ -348,19 +392,27 @@ int default_ctas_per_sm(int di, int64_t tile_cells, int64_t total_sources) {
   return (int)std::max<int64_t>(1, per256 * 256 / tile_cells);
 }
 
-eik_status ensure_device() {
+// Select the current device's workspaces for the call in progress.
+eik_status select_device() {
   int dev = 0;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
-  if (g_ws.device != dev) {
-    if (g_ws.device >= 0) g_ws.release_all();
-    g_ws.device = dev;
+  if (dev < 0 || dev >= kMaxDevices) { set_err("device ordinal %d beyond %d", dev, kMaxDevices); return EIK_EINVAL; }
+  g_dev = dev;
+  ws().device = dev;
+  adj().device = dev;
+  bsp().device = dev;
+  return EIK_OK;
+}
+
+eik_status ensure_device() {
+  eik_status st = select_device();
+  if (st != EIK_OK) return st;
+  if (!ws().ctl_host) {
+    CK(cudaMallocHost(&ws().ctl_host, sizeof(Ctl)), "pinned control block");
   }
-  if (!g_ws.ctl_host) {
-    CK(cudaMallocHost(&g_ws.ctl_host, sizeof(Ctl)), "pinned control block");
-  }
-  if (!g_ws.ev0) {
-    CK(cudaEventCreate(&g_ws.ev0), "event");
-    CK(cudaEventCreate(&g_ws.ev1), "event");
+  if (!ws().ev0) {
+    CK(cudaEventCreate(&ws().ev0), "event");
+    CK(cudaEventCreate(&ws().ev1), "event");
   }
   return EIK_OK;
 }
@@ -379,88 +431,81 @@ eik_status run_schedule(HostProblem &hp, const eik_opts *opts, eik_stats *stats,
     set_err("opts.schedule 1-3 run the exact update on the FP64 unit only");
     return EIK_EINVAL;
   }
-  {
-    int dev = 0;
-    CK(cudaGetDevice(&dev), "cudaGetDevice");
-    if (g_bsp.device != dev) {
-      if (g_bsp.device >= 0) g_bsp.release_all();
-      g_bsp.device = dev;
-    }
-  }
   eik_status st = ensure_device();
   if (st != EIK_OK) return st;
   const int64_t n = hp.n;
   const size_t ns = hp.src.size();
-  CK(g_bsp.c.ensure((size_t)n), "schedule: c");
-  CK(g_bsp.fixed.ensure((size_t)n), "schedule: flags");
-  CK(g_bsp.mark.ensure((size_t)n * 2), "schedule: marks");
-  CK(g_bsp.front.ensure((size_t)n * 2), "schedule: worklists");
-  CK(g_bsp.ctl.ensure(1), "schedule: control");
-  CK(g_ws.ctl.ensure(1), "schedule: validation block");
-  CK(g_bsp.src.ensure(std::max<size_t>(ns, 1)), "schedule: sources");
-  CK(g_bsp.src_t.ensure(std::max<size_t>(ns, 1)), "schedule: source times");
-  if (!g_bsp.ctl_host) CK(cudaMallocHost(&g_bsp.ctl_host, sizeof(eik::BspCtl)), "schedule: pinned");
-  if (!g_bsp.ev0) {
-    CK(cudaEventCreate(&g_bsp.ev0), "schedule: event");
-    CK(cudaEventCreate(&g_bsp.ev1), "schedule: event");
+  CK(bsp().c.ensure((size_t)n), "schedule: c");
+  CK(bsp().fixed.ensure((size_t)n), "schedule: flags");
+  CK(bsp().mark.ensure((size_t)n * 2), "schedule: marks");
+  CK(bsp().front.ensure((size_t)n * 2), "schedule: worklists");
+  CK(bsp().ctl.ensure(1), "schedule: control");
+  CK(ws().ctl.ensure(1), "schedule: validation block");
+  CK(bsp().src.ensure(std::max<size_t>(ns, 1)), "schedule: sources");
+  CK(bsp().src_t.ensure(std::max<size_t>(ns, 1)), "schedule: source times");
+  if (!bsp().ctl_host) CK(cudaMallocHost(&bsp().ctl_host, sizeof(eik::BspCtl)), "schedule: pinned");
+  if (!bsp().ev0) {
+    CK(cudaEventCreate(&bsp().ev0), "schedule: event");
+    CK(cudaEventCreate(&bsp().ev1), "schedule: event");
   }
   if (ns) {
-    CK(cudaMemcpyAsync(g_bsp.src.p, hp.src.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, stream),
+    CK(cudaMemcpyAsync(bsp().src.p, hp.src.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, stream),
        "schedule: upload sources");
-    CK(cudaMemcpyAsync(g_bsp.src_t.p, hp.t0.data(), ns * sizeof(double), cudaMemcpyHostToDevice, stream),
+    CK(cudaMemcpyAsync(bsp().src_t.p, hp.t0.data(), ns * sizeof(double), cudaMemcpyHostToDevice, stream),
        "schedule: upload source times");
   }
-  CK(cudaMemsetAsync(g_bsp.fixed.p, 0, (size_t)n, stream), "schedule: clear flags");
-  CK(cudaMemsetAsync(g_bsp.mark.p, 0, (size_t)n * 2 * sizeof(unsigned), stream), "schedule: clear marks");
-  CK(cudaMemsetAsync(g_bsp.ctl.p, 0, sizeof(eik::BspCtl), stream), "schedule: clear control");
-  CK(cudaMemsetAsync(g_ws.ctl.p, 0, sizeof(Ctl), stream), "schedule: clear validation");
-  CK(eik::launch_init_c(hp.speed, hp.h, g_bsp.c.p, n, g_ws.ctl.p, stream), "schedule: c");
+  CK(cudaMemsetAsync(bsp().fixed.p, 0, (size_t)n, stream), "schedule: clear flags");
+  CK(cudaMemsetAsync(bsp().mark.p, 0, (size_t)n * 2 * sizeof(unsigned), stream), "schedule: clear marks");
+  CK(cudaMemsetAsync(bsp().ctl.p, 0, sizeof(eik::BspCtl), stream), "schedule: clear control");
+  CK(cudaMemsetAsync(ws().ctl.p, 0, sizeof(Ctl), stream), "schedule: clear validation");
+  CK(eik::launch_init_c(hp.speed, hp.h, bsp().c.p, n, ws().ctl.p, stream, 0, from_slowness(opts)),
+     "schedule: c");
   CK(eik::launch_init_t(hp.out, n, stream), "schedule: t");
   eik::BspParams bp;
   std::memset(&bp, 0, sizeof(bp));
   bp.t = hp.out;
-  bp.c = g_bsp.c.p;
+  bp.c = bsp().c.p;
   bp.ndim = hp.ndim;
   bp.nx = hp.dims[2];
   bp.ny = hp.dims[1];
   bp.nz = hp.dims[0];
-  bp.fixed = g_bsp.fixed.p;
-  bp.mark[0] = g_bsp.mark.p;
-  bp.mark[1] = g_bsp.mark.p + n;
-  bp.front[0] = g_bsp.front.p;
-  bp.front[1] = g_bsp.front.p + n;
-  bp.ctl = g_bsp.ctl.p;
+  bp.fixed = bsp().fixed.p;
+  bp.mark[0] = bsp().mark.p;
+  bp.mark[1] = bsp().mark.p + n;
+  bp.front[0] = bsp().front.p;
+  bp.front[1] = bsp().front.p + n;
+  bp.ctl = bsp().ctl.p;
   bp.timeout_ns = (opts->timeout_ms > 0 ? opts->timeout_ms : 60000) * 1000000ll;
-  CK(eik::launch_bsp_seed(bp, g_bsp.src.p, g_bsp.src_t.p, (int64_t)ns, stream), "schedule: seed");
-  CK(cudaMemcpyAsync(g_ws.ctl_host, g_ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, stream),
+  CK(eik::launch_bsp_seed(bp, bsp().src.p, bsp().src_t.p, (int64_t)ns, stream), "schedule: seed");
+  CK(cudaMemcpyAsync(ws().ctl_host, ws().ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, stream),
      "schedule: validation");
   CK(cudaStreamSynchronize(stream), "schedule: set-up");
-  if (g_ws.ctl_host->status == eik::kEinval) {
+  if (ws().ctl_host->status == eik::kEinval) {
     set_err("invalid input data (cell %llu: speed must be finite and > 0, h/v finite and > 0)",
-            (unsigned long long)g_ws.ctl_host->error_info[0]);
+            (unsigned long long)ws().ctl_host->error_info[0]);
     return EIK_EINVAL;
   }
-  CK(cudaEventRecord(g_bsp.ev0, stream), "schedule: event");
+  CK(cudaEventRecord(bsp().ev0, stream), "schedule: event");
   CK(eik::launch_schedule(schedule, bp, stream), "schedule launch");
-  CK(cudaEventRecord(g_bsp.ev1, stream), "schedule: event");
-  CK(cudaMemcpyAsync(g_bsp.ctl_host, g_bsp.ctl.p, sizeof(eik::BspCtl), cudaMemcpyDeviceToHost, stream),
+  CK(cudaEventRecord(bsp().ev1, stream), "schedule: event");
+  CK(cudaMemcpyAsync(bsp().ctl_host, bsp().ctl.p, sizeof(eik::BspCtl), cudaMemcpyDeviceToHost, stream),
      "schedule: status");
   unsigned long long finite = 0;
   if (opts->counters) {
-    CK(g_ws.count.ensure(1), "schedule: count");
-    CK(cudaMemsetAsync(g_ws.count.p, 0, sizeof(unsigned long long), stream), "schedule: count");
+    CK(ws().count.ensure(1), "schedule: count");
+    CK(cudaMemsetAsync(ws().count.p, 0, sizeof(unsigned long long), stream), "schedule: count");
     eik::Prob P;
     std::memset(&P, 0, sizeof(P));
     P.t = hp.out;
     P.nx = bp.nx;
     P.ny = bp.ny;
     P.nz = bp.nz;
-    CK(eik::launch_count_finite(&P, 1, g_ws.count.p, stream), "schedule: count");
-    CK(cudaMemcpyAsync(&finite, g_ws.count.p, sizeof(finite), cudaMemcpyDeviceToHost, stream),
+    CK(eik::launch_count_finite(&P, 1, ws().count.p, stream), "schedule: count");
+    CK(cudaMemcpyAsync(&finite, ws().count.p, sizeof(finite), cudaMemcpyDeviceToHost, stream),
        "schedule: count");
   }
   CK(cudaStreamSynchronize(stream), "schedule");
-  const eik::BspCtl &c = *g_bsp.ctl_host;
+  const eik::BspCtl &c = *bsp().ctl_host;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->evals = (int64_t)c.evals;
@@ -468,7 +513,7 @@ eik_status run_schedule(HostProblem &hp, const eik_opts *opts, eik_stats *stats,
     stats->rounds = (int64_t)c.rounds;
     if (opts->counters) stats->good = (int64_t)finite - (int64_t)ns;
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, g_bsp.ev0, g_bsp.ev1) == cudaSuccess) stats->solve_ms = ms;
+    if (cudaEventElapsedTime(&ms, bsp().ev0, bsp().ev1) == cudaSuccess) stats->solve_ms = ms;
   }
   if (c.status == eik::kEtimeout) { set_err("device wait timed out"); return EIK_ETIMEOUT; }
   if (c.status != 0) return EIK_ECUDA;
@@ -528,15 +573,15 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     for (size_t i = 0; i < hps.size(); ++i) if (prob_speed[i] == (int)j) { owner = &hps[i]; break; }
     if (!owner->speed_dev) host_speed_cells += speed_n[j];
   }
-  CK(g_ws.r.ensure((size_t)r_total), "alloc r");
-  CK(g_ws.src_idx.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc src_idx");
-  CK(g_ws.src_t.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc src_t");
-  CK(g_ws.seeds.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc seeds");
-  CK(g_ws.probs.ensure(hps.size()), "alloc probs");
-  CK(g_ws.ctl.ensure(1), "alloc ctl");
-  CK(g_ws.count.ensure(1), "alloc count");
-  if (host_out_cells) CK(g_ws.t_stage.ensure((size_t)host_out_cells), "alloc t staging");
-  if (host_speed_cells) CK(g_ws.v_stage.ensure((size_t)host_speed_cells), "alloc speed staging");
+  CK(ws().r.ensure((size_t)r_total), "alloc r");
+  CK(ws().src_idx.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc src_idx");
+  CK(ws().src_t.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc src_t");
+  CK(ws().seeds.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc seeds");
+  CK(ws().probs.ensure(hps.size()), "alloc probs");
+  CK(ws().ctl.ensure(1), "alloc ctl");
+  CK(ws().count.ensure(1), "alloc count");
+  if (host_out_cells) CK(ws().t_stage.ensure((size_t)host_out_cells), "alloc t staging");
+  if (host_speed_cells) CK(ws().v_stage.ensure((size_t)host_speed_cells), "alloc speed staging");
 
   std::vector<int64_t> all_src;
   std::vector<double> all_t0;
@@ -554,15 +599,15 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     P.ntz = (P.nz + tz - 1) / tz;
     P.tile_base = total_tiles;
     total_tiles += P.ntx * P.nty * P.ntz;
-    P.c = g_ws.r.p + speed_off[prob_speed[i]];
+    P.c = ws().r.p + speed_off[prob_speed[i]];
     if (hp.out_dev) {
       P.t = hp.out;
     } else {
-      P.t = g_ws.t_stage.p + out_stage_off;
+      P.t = ws().t_stage.p + out_stage_off;
       out_stage_off += hp.n;
     }
-    P.src_idx = g_ws.src_idx.p + all_src.size();
-    P.src_t = g_ws.src_t.p + all_src.size();
+    P.src_idx = ws().src_idx.p + all_src.size();
+    P.src_t = ws().src_t.p + all_src.size();
     P.nsrc = (int64_t)hp.src.size();
     for (size_t k = 0; k < hp.src.size(); ++k) {
       seeds.push_back(SeedItem{(int64_t)i, hp.src[k], hp.t0[k]});
@@ -571,9 +616,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     }
   }
   if (total_tiles >= (int64_t(1) << 32)) { set_err("too many tiles"); return EIK_EINVAL; }
-  CK(g_ws.state.ensure((size_t)total_tiles), "alloc tile state");
-  CK(g_ws.tile_src.ensure((size_t)total_tiles), "alloc tile flags");
-  CK(g_ws.pend.ensure((size_t)total_tiles * eik::kPendWords), "alloc pending masks");
+  CK(ws().state.ensure((size_t)total_tiles), "alloc tile state");
+  CK(ws().tile_src.ensure((size_t)total_tiles), "alloc tile flags");
+  CK(ws().pend.ensure((size_t)total_tiles * eik::kPendWords), "alloc pending masks");
 
   // frontier capacity per bucket slot
   uint64_t want_cap = opts && opts->capacity > 0 ? (uint64_t)opts->capacity
@@ -582,28 +627,28 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   while (want_cap * eik::kNumSlots > kMaxCapEntries && want_cap > 1024) want_cap >>= 1;
   // the ring layout depends on cap; storage only grows.  Entries need no
   // clearing: the sequence words (zeroed below) say which positions hold one.
-  CK(g_ws.slots.ensure((size_t)(want_cap * eik::kNumSlots)), "alloc frontier");
-  CK(g_ws.seq.ensure((size_t)(want_cap * eik::kNumSlots)), "alloc frontier sequence");
-  g_ws.cap = want_cap;
+  CK(ws().slots.ensure((size_t)(want_cap * eik::kNumSlots)), "alloc frontier");
+  CK(ws().seq.ensure((size_t)(want_cap * eik::kNumSlots)), "alloc frontier sequence");
+  ws().cap = want_cap;
 
   // uploads
   if (!all_src.empty()) {
-    CK(cudaMemcpyAsync(g_ws.src_idx.p, all_src.data(), all_src.size() * sizeof(int64_t),
+    CK(cudaMemcpyAsync(ws().src_idx.p, all_src.data(), all_src.size() * sizeof(int64_t),
                        cudaMemcpyHostToDevice, stream), "upload sources");
-    CK(cudaMemcpyAsync(g_ws.src_t.p, all_t0.data(), all_t0.size() * sizeof(double),
+    CK(cudaMemcpyAsync(ws().src_t.p, all_t0.data(), all_t0.size() * sizeof(double),
                        cudaMemcpyHostToDevice, stream), "upload source times");
-    CK(cudaMemcpyAsync(g_ws.seeds.p, seeds.data(), seeds.size() * sizeof(SeedItem),
+    CK(cudaMemcpyAsync(ws().seeds.p, seeds.data(), seeds.size() * sizeof(SeedItem),
                        cudaMemcpyHostToDevice, stream), "upload seeds");
   }
-  CK(cudaMemcpyAsync(g_ws.probs.p, probs.data(), probs.size() * sizeof(Prob),
+  CK(cudaMemcpyAsync(ws().probs.p, probs.data(), probs.size() * sizeof(Prob),
                      cudaMemcpyHostToDevice, stream), "upload problems");
-  CK(cudaMemsetAsync(g_ws.ctl.p, 0, sizeof(Ctl), stream), "clear control block");
-  CK(cudaMemsetAsync(g_ws.state.p, 0, (size_t)total_tiles * sizeof(unsigned long long), stream),
+  CK(cudaMemsetAsync(ws().ctl.p, 0, sizeof(Ctl), stream), "clear control block");
+  CK(cudaMemsetAsync(ws().state.p, 0, (size_t)total_tiles * sizeof(unsigned long long), stream),
      "clear tile states");
-  CK(cudaMemsetAsync(g_ws.tile_src.p, 0, (size_t)total_tiles, stream), "clear tile flags");
-  CK(cudaMemsetAsync(g_ws.pend.p, 0, (size_t)total_tiles * eik::kPendWords * sizeof(unsigned),
+  CK(cudaMemsetAsync(ws().tile_src.p, 0, (size_t)total_tiles, stream), "clear tile flags");
+  CK(cudaMemsetAsync(ws().pend.p, 0, (size_t)total_tiles * eik::kPendWords * sizeof(unsigned),
                      stream), "clear pending masks");
-  CK(cudaMemsetAsync(g_ws.seq.p, 0, (size_t)(want_cap * eik::kNumSlots) * sizeof(unsigned), stream),
+  CK(cudaMemsetAsync(ws().seq.p, 0, (size_t)(want_cap * eik::kNumSlots) * sizeof(unsigned), stream),
      "clear frontier sequence");
 
   // r = h / v (staging host speeds first)
@@ -613,26 +658,26 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     for (size_t i = 0; i < hps.size(); ++i) if (prob_speed[i] == (int)j) { owner = &hps[i]; break; }
     const double *vsrc = speeds[j];
     if (!owner->speed_dev) {
-      CK(cudaMemcpyAsync(g_ws.v_stage.p + v_off, vsrc, speed_n[j] * sizeof(double),
+      CK(cudaMemcpyAsync(ws().v_stage.p + v_off, vsrc, speed_n[j] * sizeof(double),
                          cudaMemcpyHostToDevice, stream), "upload speed");
-      vsrc = g_ws.v_stage.p + v_off;
+      vsrc = ws().v_stage.p + v_off;
       v_off += speed_n[j];
     }
-    CK(eik::launch_init_c(vsrc, speed_h[j], g_ws.r.p + speed_off[j], speed_n[j], g_ws.ctl.p, stream,
-                          form != 0), "init_c launch");
+    CK(eik::launch_init_c(vsrc, speed_h[j], ws().r.p + speed_off[j], speed_n[j], ws().ctl.p, stream,
+                          form != 0, from_slowness(opts)), "init_c launch");
   }
   int64_t max_cells = 0;
   for (auto &P : probs) max_cells = std::max<int64_t>(max_cells, P.nx * P.ny * P.nz);
-  CK(eik::launch_init_t_all(g_ws.probs.p, (int)probs.size(), max_cells, stream), "init_t launch");
+  CK(eik::launch_init_t_all(ws().probs.p, (int)probs.size(), max_cells, stream), "init_t launch");
 
   SolveParams sp;
   std::memset(&sp, 0, sizeof(sp));
-  sp.probs = g_ws.probs.p;
+  sp.probs = ws().probs.p;
   sp.nprob = (int)probs.size();
   sp.ndim = ndim;
-  sp.state = g_ws.state.p;
-  sp.tile_src = g_ws.tile_src.p;
-  sp.pend = g_ws.pend.p;
+  sp.state = ws().state.p;
+  sp.tile_src = ws().tile_src.p;
+  sp.pend = ws().pend.p;
   const int di = ndim == 3 ? 1 : 0;
   sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow[di]);
   sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand[di];
@@ -645,10 +690,10 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.trace = opts && opts->trace && opts->trace_cap > 0 ? static_cast<eik::TraceRec *>(opts->trace)
                                                         : nullptr;
   sp.trace_cap = sp.trace ? (unsigned long long)opts->trace_cap : 0ull;
-  sp.slots = g_ws.slots.p;
-  sp.seq = g_ws.seq.p;
-  sp.cap_mask = (unsigned)(g_ws.cap - 1);
-  sp.ctl = g_ws.ctl.p;
+  sp.slots = ws().slots.p;
+  sp.seq = ws().seq.p;
+  sp.cap_mask = (unsigned)(ws().cap - 1);
+  sp.ctl = ws().ctl.p;
   const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
   sp.timeout_ns = tmo_ms * 1000000ll;
   sp.counters = opts ? opts->counters : 0;
@@ -658,14 +703,14 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
                              : auto_config(ndim, total_src, sp.arith == eik::kArithInt).k_delta;
   const double delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
 
-  CK(eik::launch_seed(sp, g_ws.seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
+  CK(eik::launch_seed(sp, ws().seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
      "seed launch");
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm
                                              : default_ctas_per_sm(di, tx * ty * tz, total_src);
   const int occ = eik::persistent_blocks_per_sm(ndim, sp.arith, shape);
   if (per_sm > occ) per_sm = occ;
   int dev_sms = 0;
-  CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, g_ws.device), "SM count");
+  CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ws().device), "SM count");
   int64_t grid = (int64_t)dev_sms * per_sm;
   if (grid > total_tiles) grid = total_tiles;
   if (grid < 1) grid = 1;
@@ -675,16 +720,16 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   std::memset(&acc, 0, sizeof(acc));
   unsigned status = 0;
   for (int attempt = 0;; ++attempt) {
-    CK(cudaEventRecord(g_ws.ev0, stream), "event record");
+    CK(cudaEventRecord(ws().ev0, stream), "event record");
     CK(eik::launch_persistent(sp, (int)grid, stream), "solve launch");
-    CK(cudaEventRecord(g_ws.ev1, stream), "event record");
-    CK(cudaMemcpyAsync(g_ws.ctl_host, g_ws.ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, stream),
+    CK(cudaEventRecord(ws().ev1, stream), "event record");
+    CK(cudaMemcpyAsync(ws().ctl_host, ws().ctl.p, sizeof(Ctl), cudaMemcpyDeviceToHost, stream),
        "read status");
     CK(cudaStreamSynchronize(stream), "solve");
     float kms = 0.f;
-    CK(cudaEventElapsedTime(&kms, g_ws.ev0, g_ws.ev1), "event time");
+    CK(cudaEventElapsedTime(&kms, ws().ev0, ws().ev1), "event time");
     acc.solve_ms += kms;
-    const Ctl &c = *g_ws.ctl_host;
+    const Ctl &c = *ws().ctl_host;
     status = c.status;
     acc.evals += (int64_t)c.stats[eik::kStatEvals];
     acc.decreases += (int64_t)c.stats[eik::kStatDecreases];
@@ -699,27 +744,27 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     acc.trace_n = (int64_t)c.trace_n;
     for (int k = 0; k < 9; ++k) acc.detail[k] += (int64_t)c.stats[eik::kStatCycLoad + k];
     if (status != eik::kEcapacity || attempt >= kMaxRetries ||
-        g_ws.cap * 4 * eik::kNumSlots > kMaxCapEntries) break;
+        ws().cap * 4 * eik::kNumSlots > kMaxCapEntries) break;
     // grow the frontier, clear the scheduler (keep delta) and resume
-    const uint64_t ncap = g_ws.cap * 4;
-    CK(g_ws.slots.ensure((size_t)(ncap * eik::kNumSlots)), "grow frontier");
-    CK(g_ws.seq.ensure((size_t)(ncap * eik::kNumSlots)), "grow frontier sequence");
-    g_ws.cap = ncap;
-    sp.slots = g_ws.slots.p;
-    sp.seq = g_ws.seq.p;
+    const uint64_t ncap = ws().cap * 4;
+    CK(ws().slots.ensure((size_t)(ncap * eik::kNumSlots)), "grow frontier");
+    CK(ws().seq.ensure((size_t)(ncap * eik::kNumSlots)), "grow frontier sequence");
+    ws().cap = ncap;
+    sp.slots = ws().slots.p;
+    sp.seq = ws().seq.p;
     sp.cap_mask = (unsigned)(ncap - 1);
-    CK(cudaMemsetAsync(g_ws.seq.p, 0, (size_t)(ncap * eik::kNumSlots) * sizeof(unsigned), stream),
+    CK(cudaMemsetAsync(ws().seq.p, 0, (size_t)(ncap * eik::kNumSlots) * sizeof(unsigned), stream),
        "clear frontier sequence");
-    CK(cudaMemsetAsync(g_ws.ctl.p, 0, offsetof(Ctl, rsum), stream), "clear scheduler");
-    CK(cudaMemsetAsync(&g_ws.ctl.p->stats[0], 0, sizeof(Ctl) - offsetof(Ctl, stats), stream),
+    CK(cudaMemsetAsync(ws().ctl.p, 0, offsetof(Ctl, rsum), stream), "clear scheduler");
+    CK(cudaMemsetAsync(&ws().ctl.p->stats[0], 0, sizeof(Ctl) - offsetof(Ctl, stats), stream),
        "clear counters");
-    CK(cudaMemsetAsync(g_ws.state.p, 0, (size_t)total_tiles * sizeof(unsigned long long), stream),
+    CK(cudaMemsetAsync(ws().state.p, 0, (size_t)total_tiles * sizeof(unsigned long long), stream),
        "clear tile states");
     CK(eik::launch_reseed(sp, probs.data(), (int)probs.size(), stream), "reseed launch");
     acc.retries++;
   }
   if (status != 0) {
-    const Ctl &c = *g_ws.ctl_host;
+    const Ctl &c = *ws().ctl_host;
     if (status == eik::kEinval) {
       set_err("invalid input data (cell %llu: speed must be finite and > 0, h/v finite and > 0)",
               (unsigned long long)c.error_info[0]);
@@ -737,11 +782,11 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     return EIK_ECUDA;
   }
   if (sp.counters) {
-    CK(cudaMemsetAsync(g_ws.count.p, 0, sizeof(unsigned long long), stream), "clear count");
-    CK(eik::launch_count_finite_all(g_ws.probs.p, (int)probs.size(), max_cells, g_ws.count.p,
+    CK(cudaMemsetAsync(ws().count.p, 0, sizeof(unsigned long long), stream), "clear count");
+    CK(eik::launch_count_finite_all(ws().probs.p, (int)probs.size(), max_cells, ws().count.p,
                                     stream), "count");
     unsigned long long finite = 0;
-    CK(cudaMemcpyAsync(&finite, g_ws.count.p, sizeof(finite), cudaMemcpyDeviceToHost, stream),
+    CK(cudaMemcpyAsync(&finite, ws().count.p, sizeof(finite), cudaMemcpyDeviceToHost, stream),
        "read count");
     CK(cudaStreamSynchronize(stream), "count");
     acc.good = (int64_t)finite - total_src;
@@ -785,10 +830,6 @@ eik_status eik_solve_batched(const eik_problem *probs, int nprob, const eik_opts
     eik_status st = check_problem(q.speed, q.h, q.ndim, q.dims, q.src_idx, q.src_t, q.nsrc,
                                   q.out_t, hps[(size_t)i], s);
     if (st != EIK_OK) return st;
-    if (!hps[(size_t)i].speed_dev || !hps[(size_t)i].out_dev) {
-      set_err("batched problems take device pointers only (problem %d)", i);
-      return EIK_EINVAL;
-    }
   }
   return run(hps, opts, stats, s);
 }
@@ -860,10 +901,10 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
       ms = std::min(ms, stt.solve_ms);
       if (r == 0) {
         unsigned long long dig[2] = {0, 0};
-        CK(g_ws.count.ensure(2), "autotune: digest buffer");
-        CK(cudaMemsetAsync(g_ws.count.p, 0, 2 * sizeof(unsigned long long), s), "autotune: clear");
-        CK(eik::launch_checksum_all(g_ws.probs.p, nprob, max_cells, g_ws.count.p, s), "digest");
-        CK(cudaMemcpyAsync(dig, g_ws.count.p, sizeof(dig), cudaMemcpyDeviceToHost, s), "digest");
+        CK(ws().count.ensure(2), "autotune: digest buffer");
+        CK(cudaMemsetAsync(ws().count.p, 0, 2 * sizeof(unsigned long long), s), "autotune: clear");
+        CK(eik::launch_checksum_all(ws().probs.p, nprob, max_cells, ws().count.p, s), "digest");
+        CK(cudaMemcpyAsync(dig, ws().count.p, sizeof(dig), cudaMemcpyDeviceToHost, s), "digest");
         CK(cudaStreamSynchronize(s), "digest");
         if (!have_ref) {
           ref[0] = dig[0];
@@ -1012,32 +1053,59 @@ eik_status eik_residual(const eik_problem *prob, int form, int64_t *bad, double 
   st = ensure_device();
   if (st != EIK_OK) return st;
   const size_t ns = hp.src.size();
-  CK(g_ws.src_idx.ensure(std::max<size_t>(ns, 1)), "residual: sources");
-  CK(g_ws.src_t.ensure(std::max<size_t>(ns, 1)), "residual: source times");
-  CK(g_ws.count.ensure(2), "residual: result");
+  CK(ws().src_idx.ensure(std::max<size_t>(ns, 1)), "residual: sources");
+  CK(ws().src_t.ensure(std::max<size_t>(ns, 1)), "residual: source times");
+  CK(ws().count.ensure(2), "residual: result");
   if (ns) {
-    CK(cudaMemcpyAsync(g_ws.src_idx.p, hp.src.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s),
+    CK(cudaMemcpyAsync(ws().src_idx.p, hp.src.data(), ns * sizeof(int64_t), cudaMemcpyHostToDevice, s),
        "residual: upload sources");
-    CK(cudaMemcpyAsync(g_ws.src_t.p, hp.t0.data(), ns * sizeof(double), cudaMemcpyHostToDevice, s),
+    CK(cudaMemcpyAsync(ws().src_t.p, hp.t0.data(), ns * sizeof(double), cudaMemcpyHostToDevice, s),
        "residual: upload source times");
   }
-  CK(cudaMemsetAsync(g_ws.count.p, 0, 2 * sizeof(unsigned long long), s), "residual: clear");
+  CK(cudaMemsetAsync(ws().count.p, 0, 2 * sizeof(unsigned long long), s), "residual: clear");
   CK(eik::launch_residual(f, hp.ndim, hp.speed, hp.h, hp.out, hp.dims[2], hp.dims[1], hp.dims[0],
-                          g_ws.src_idx.p, g_ws.src_t.p, (int64_t)ns, g_ws.count.p, s),
+                          ws().src_idx.p, ws().src_t.p, (int64_t)ns, ws().count.p, s),
      "residual launch");
   unsigned long long res[2] = {0, 0};
-  CK(cudaMemcpyAsync(res, g_ws.count.p, sizeof(res), cudaMemcpyDeviceToHost, s), "residual: read");
+  CK(cudaMemcpyAsync(res, ws().count.p, sizeof(res), cudaMemcpyDeviceToHost, s), "residual: read");
   CK(cudaStreamSynchronize(s), "residual");
   *bad = (int64_t)res[0];
   std::memcpy(max_rel, &res[1], sizeof(double));
   return EIK_OK;
 }
 
+// The fixed-order sum of k arrays (the cross-source gradient of a sharded
+// tomography step, gathered on one device).
+eik_status eik_sum_ordered(const double *const *src, int k, double *dst, int64_t n, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (k < 0 || n < 0 || (k > 0 && !src) || (n > 0 && !dst)) {
+    set_err("bad eik_sum_ordered arguments");
+    return EIK_EINVAL;
+  }
+  if (n == 0) return EIK_OK;
+  if (!is_device_ptr(dst)) { set_err("eik_sum_ordered takes device pointers only"); return EIK_EINVAL; }
+  for (int j = 0; j < k; ++j) {
+    if (!is_device_ptr(src[j])) { set_err("eik_sum_ordered: src[%d] is not a device pointer", j); return EIK_EINVAL; }
+  }
+  eik_status st = ensure_device();
+  if (st != EIK_OK) return st;
+  CK(ws().sum_ptr.ensure((size_t)std::max(k, 1)), "sum: pointer table");
+  if (k > 0) {
+    CK(cudaMemcpyAsync(ws().sum_ptr.p, src, (size_t)k * sizeof(const double *), cudaMemcpyHostToDevice, s),
+       "sum: upload pointer table");
+  }
+  CK(eik::launch_sum_ordered(ws().sum_ptr.p, k, dst, n, s), "sum launch");
+  CK(cudaStreamSynchronize(s), "sum");
+  return EIK_OK;
+}
+
 void eik_release(void) {
   std::lock_guard<std::mutex> lk(g_mu);
-  g_ws.release_all();
-  g_adj.release_all();
-  g_bsp.release_all();
+  if (select_device() != EIK_OK) return;
+  ws().release_all();
+  adj().release_all();
+  bsp().release_all();
 }
 
 const char *eik_status_str(eik_status s) {
@@ -1070,7 +1138,10 @@ struct eik_plan {
   int device = -1;
   int ndim = 2;
   std::vector<Prob> probs;                   // host copies of the device records
-  std::vector<const double *> speeds;        // distinct speed arrays
+  std::vector<const double *> speeds;        // distinct speed arrays (device copies)
+  std::vector<const double *> speed_host;    // their pinned host sources (NULL: device input)
+  std::vector<double *> out_host;            // per problem: pinned host output (NULL: device)
+  DevBuf<double> v_stage, t_stage;           // device copies of pinned host inputs / outputs
   std::vector<int64_t> speed_off, speed_n;
   std::vector<double> speed_h;
   int64_t total_tiles = 0, nseeds = 0, total_src = 0, max_cells = 0;
@@ -1090,9 +1161,11 @@ struct eik_plan {
   SolveParams sp;
   int grid = 1;
   double k_delta = 0.0, delta_fixed = 0.0;
+  int from_slowness = 0;
   uint64_t cap = 0;
 
   ~eik_plan() {
+    v_stage.release(); t_stage.release();
     c.release(); state.release(); tile_src.release(); pend.release(); slots.release();
     seq.release(); src_idx.release(); src_t.release(); seeds.release(); probs_d.release(); ctl.release();
     count.release();
@@ -1106,9 +1179,13 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
                       cudaStream_t stream) {
   CK(cudaGetDevice(&pl.device), "cudaGetDevice");
   pl.ndim = hps[0].ndim;
-  for (auto &hp : hps) {
+  for (size_t i = 0; i < hps.size(); ++i) {
+    const HostProblem &hp = hps[i];
     if (hp.ndim != pl.ndim) { set_err("all problems of a plan must have the same ndim"); return EIK_EINVAL; }
-    if (!hp.speed_dev || !hp.out_dev) { set_err("plans take device pointers only"); return EIK_EINVAL; }
+    if ((!hp.speed_dev && !is_pinned_host(hp.speed)) || (!hp.out_dev && !is_pinned_host(hp.out))) {
+      set_err("plans take device or pinned host pointers (problem %d: pageable host memory)", (int)i);
+      return EIK_EINVAL;
+    }
   }
   int64_t tx, ty, tz;
   int shape = 0;
@@ -1128,6 +1205,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
     if (found < 0) {
       found = (int)pl.speeds.size();
       pl.speeds.push_back(hps[i].speed);
+      pl.speed_host.push_back(hps[i].speed_dev ? nullptr : hps[i].speed);
       pl.speed_off.push_back(c_total);
       pl.speed_n.push_back(hps[i].n);
       pl.speed_h.push_back(hps[i].h);
@@ -1137,6 +1215,20 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   }
   for (auto &hp : hps) pl.total_src += (int64_t)hp.src.size();
   CK(pl.c.ensure((size_t)c_total), "plan: alloc c");
+  {  // device copies of pinned host speeds and outputs
+    int64_t v_cells = 0, t_cells = 0;
+    for (size_t j = 0; j < pl.speeds.size(); ++j) if (pl.speed_host[j]) v_cells += pl.speed_n[j];
+    for (auto &hp : hps) if (!hp.out_dev) t_cells += hp.n;
+    if (v_cells) CK(pl.v_stage.ensure((size_t)v_cells), "plan: alloc speed copies");
+    if (t_cells) CK(pl.t_stage.ensure((size_t)t_cells), "plan: alloc output copies");
+    int64_t off = 0;
+    for (size_t j = 0; j < pl.speeds.size(); ++j) {
+      if (!pl.speed_host[j]) continue;
+      pl.speeds[j] = pl.v_stage.p + off;
+      off += pl.speed_n[j];
+    }
+  }
+  int64_t t_off = 0;
   CK(pl.src_idx.ensure((size_t)std::max<int64_t>(pl.total_src, 1)), "plan: alloc src_idx");
   CK(pl.src_t.ensure((size_t)std::max<int64_t>(pl.total_src, 1)), "plan: alloc src_t");
   CK(pl.seeds.ensure((size_t)std::max<int64_t>(pl.total_src, 1)), "plan: alloc seeds");
@@ -1162,7 +1254,14 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
     pl.total_tiles += P.ntx * P.nty * P.ntz;
     pl.max_cells = std::max<int64_t>(pl.max_cells, P.nx * P.ny * P.nz);
     P.c = pl.c.p + pl.speed_off[prob_speed[i]];
-    P.t = hp.out;
+    if (hp.out_dev) {
+      P.t = hp.out;
+      pl.out_host.push_back(nullptr);
+    } else {
+      P.t = pl.t_stage.p + t_off;
+      t_off += hp.n;
+      pl.out_host.push_back(hp.out);
+    }
     P.src_idx = pl.src_idx.p + all_src.size();
     P.src_t = pl.src_t.p + all_src.size();
     P.nsrc = (int64_t)hp.src.size();
@@ -1227,6 +1326,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
                    ? opts->k_delta
                    : auto_config(pl.ndim, count_sources(hps), opts && opts->arith == 2).k_delta;
   pl.delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
+  pl.from_slowness = from_slowness(opts);
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm
                                              : default_ctas_per_sm(di, tx * ty * tz, pl.nseeds);
   const int occ = eik::persistent_blocks_per_sm(pl.ndim, sp.arith, shape);
@@ -1279,12 +1379,23 @@ eik_status eik_plan_enqueue(eik_plan *pl, void *stream) {
   CK(cudaMemsetAsync(pl->seq.p, 0, (size_t)(pl->cap * eik::kNumSlots) * sizeof(unsigned), s),
      "clear frontier sequence");
   for (size_t j = 0; j < pl->speeds.size(); ++j) {
+    if (pl->speed_host[j]) {
+      CK(cudaMemcpyAsync(const_cast<double *>(pl->speeds[j]), pl->speed_host[j],
+                         (size_t)pl->speed_n[j] * sizeof(double), cudaMemcpyHostToDevice, s),
+         "plan: upload speed");
+    }
     CK(eik::launch_init_c(pl->speeds[j], pl->speed_h[j], pl->c.p + pl->speed_off[j], pl->speed_n[j],
-                          pl->ctl.p, s, pl->sp.update != 0), "init_c launch");
+                          pl->ctl.p, s, pl->sp.update != 0, pl->from_slowness), "init_c launch");
   }
   CK(eik::launch_init_t_all(pl->sp.probs, (int)pl->probs.size(), pl->max_cells, s), "init_t launch");
   CK(eik::launch_seed(pl->sp, pl->seeds.p, pl->nseeds, pl->k_delta, pl->delta_fixed, s), "seed launch");
   CK(eik::launch_persistent(pl->sp, pl->grid, s), "solve launch");
+  for (size_t i = 0; i < pl->probs.size(); ++i) {
+    if (!pl->out_host[i]) continue;
+    const Prob &P = pl->probs[i];
+    CK(cudaMemcpyAsync(pl->out_host[i], P.t, (size_t)(P.nx * P.ny * P.nz) * sizeof(double),
+                       cudaMemcpyDeviceToHost, s), "plan: download t");
+  }
   return EIK_OK;
 }
 
@@ -1354,12 +1465,8 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
     total_src += (int64_t)hps[(size_t)i].src.size();
   }
   {
-    int dev = 0;
-    CK(cudaGetDevice(&dev), "cudaGetDevice");
-    if (g_adj.device != dev) {
-      if (g_adj.device >= 0) g_adj.release_all();
-      g_adj.device = dev;
-    }
+    eik_status sd = select_device();
+    if (sd != EIK_OK) return sd;
   }
   // schedule: sched_flags bits 3-4, 1 = levels, 2 = tiles, 0 = default (tiles
   // when every problem has the same ndim)
@@ -1383,30 +1490,52 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
   }
   if (tiles && total_tiles >= (int64_t(1) << 31)) { set_err("adjoint: too many tiles"); return EIK_EINVAL; }
   const uint64_t qcap = next_pow2((uint64_t)std::max<int64_t>(total_tiles, 2));
-  if (!g_adj.ctl_host) CK(cudaMallocHost(&g_adj.ctl_host, sizeof(eik::AdjCtl)), "adjoint: pinned");
-  CK(g_adj.cnt.ensure((size_t)total), "adjoint: alloc counts");
+  if (!adj().ctl_host) CK(cudaMallocHost(&adj().ctl_host, sizeof(eik::AdjCtl)), "adjoint: pinned");
+  CK(adj().cnt.ensure((size_t)total), "adjoint: alloc counts");
   if (tiles) {
-    CK(g_adj.cnt_out.ensure((size_t)total), "adjoint: alloc counts");
-    CK(g_adj.status.ensure((size_t)total), "adjoint: alloc status");
-    CK(g_adj.tile_state.ensure((size_t)total_tiles), "adjoint: alloc tile states");
-    CK(g_adj.ring.ensure((size_t)qcap), "adjoint: alloc tile queue");
+    CK(adj().cnt_out.ensure((size_t)total), "adjoint: alloc counts");
+    CK(adj().status.ensure((size_t)total), "adjoint: alloc status");
+    CK(adj().tile_state.ensure((size_t)total_tiles), "adjoint: alloc tile states");
+    CK(adj().ring.ensure((size_t)qcap), "adjoint: alloc tile queue");
   } else {
-    CK(g_adj.front.ensure((size_t)total * 2), "adjoint: alloc frontiers");
+    CK(adj().front.ensure((size_t)total * 2), "adjoint: alloc frontiers");
   }
-  CK(g_adj.W.ensure((size_t)total * 3), "adjoint: alloc weights");
-  CK(g_adj.mask.ensure((size_t)total), "adjoint: alloc masks");
-  if (!tiles) CK(g_adj.lam.ensure((size_t)total), "adjoint: alloc lambda");
-  CK(g_adj.probs.ensure((size_t)nprob), "adjoint: alloc problems");
-  CK(g_adj.ctl.ensure(1), "adjoint: alloc control");
-  CK(g_adj.src.ensure((size_t)std::max<int64_t>(total_src, 1)), "adjoint: alloc sources");
+  CK(adj().W.ensure((size_t)total * 3), "adjoint: alloc weights");
+  CK(adj().mask.ensure((size_t)total), "adjoint: alloc masks");
+  if (!tiles) CK(adj().lam.ensure((size_t)total), "adjoint: alloc lambda");
+  CK(adj().probs.ensure((size_t)nprob), "adjoint: alloc problems");
+  CK(adj().ctl.ensure(1), "adjoint: alloc control");
+  CK(adj().src.ensure((size_t)std::max<int64_t>(total_src, 1)), "adjoint: alloc sources");
+  // summed outputs: problems that share a dL_dslowness array form a group (in
+  // order of first appearance); each problem's gradient goes to the workspace
+  // and the group's output receives +0 + g_first + ... + g_last in problem order
+  const bool sum_shared = opts && (opts->sched_flags & kFlagSumShared);
+  std::vector<double *> group_out;
+  std::vector<std::vector<int>> group_of;
+  if (sum_shared) {
+    for (int i = 0; i < nprob; ++i) {
+      size_t g = 0;
+      while (g < group_out.size() && group_out[g] != dL_dslowness[i]) ++g;
+      if (g == group_out.size()) {
+        group_out.push_back(dL_dslowness[i]);
+        group_of.emplace_back();
+      } else if (hps[(size_t)group_of[g][0]].n != hps[(size_t)i].n) {
+        set_err("adjoint: problems %d and %d share an output but differ in size", group_of[g][0], i);
+        return EIK_EINVAL;
+      }
+      group_of[g].push_back(i);
+    }
+    CK(adj().gsum.ensure((size_t)total), "adjoint: alloc summed gradients");
+    CK(adj().gptr.ensure((size_t)nprob), "adjoint: alloc gradient table");
+  }
   std::vector<eik::AdjProb> ap((size_t)nprob);
   std::vector<int64_t> all_src;
   int64_t base = 0, tile_base = 0;
   for (int i = 0; i < nprob; ++i) {
     const HostProblem &hp = hps[(size_t)i];
     eik::AdjProb &A = ap[(size_t)i];
-    A.cnt_out = tiles ? g_adj.cnt_out.p + base : nullptr;
-    A.status = tiles ? g_adj.status.p + base : nullptr;
+    A.cnt_out = tiles ? adj().cnt_out.p + base : nullptr;
+    A.status = tiles ? adj().status.p + base : nullptr;
     A.ntx = ntile[(size_t)i * 3];
     A.nty = ntile[(size_t)i * 3 + 1];
     A.ntz = ntile[(size_t)i * 3 + 2];
@@ -1414,13 +1543,14 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
     tile_base += A.ntx * A.nty * A.ntz;
     A.t = hp.out;
     A.v = hp.speed;
+    A.v_is_slowness = from_slowness(opts);
     A.g = dL_dt ? dL_dt[i] : nullptr;
-    A.grad = dL_dslowness[i];
-    A.lam = tiles ? nullptr : g_adj.lam.p + base;
-    for (int k = 0; k < 3; ++k) A.W[k] = g_adj.W.p + (size_t)k * (size_t)total + base;
-    A.mask = g_adj.mask.p + base;
-    A.cnt = g_adj.cnt.p + base;
-    A.src_idx = g_adj.src.p + all_src.size();
+    A.grad = sum_shared ? adj().gsum.p + base : dL_dslowness[i];
+    A.lam = tiles ? nullptr : adj().lam.p + base;
+    for (int k = 0; k < 3; ++k) A.W[k] = adj().W.p + (size_t)k * (size_t)total + base;
+    A.mask = adj().mask.p + base;
+    A.cnt = adj().cnt.p + base;
+    A.src_idx = adj().src.p + all_src.size();
     A.nsrc = (int64_t)hp.src.size();
     A.nx = hp.dims[2];
     A.ny = hp.dims[1];
@@ -1432,36 +1562,50 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
     base += hp.n;
   }
   if (!all_src.empty())
-    CK(cudaMemcpyAsync(g_adj.src.p, all_src.data(), all_src.size() * sizeof(int64_t),
+    CK(cudaMemcpyAsync(adj().src.p, all_src.data(), all_src.size() * sizeof(int64_t),
                        cudaMemcpyHostToDevice, s), "adjoint: upload sources");
-  CK(cudaMemcpyAsync(g_adj.probs.p, ap.data(), ap.size() * sizeof(eik::AdjProb),
+  CK(cudaMemcpyAsync(adj().probs.p, ap.data(), ap.size() * sizeof(eik::AdjProb),
                      cudaMemcpyHostToDevice, s), "adjoint: upload problems");
-  CK(cudaMemsetAsync(g_adj.cnt.p, 0, (size_t)total * sizeof(int), s), "adjoint: clear counts");
+  CK(cudaMemsetAsync(adj().cnt.p, 0, (size_t)total * sizeof(int), s), "adjoint: clear counts");
   if (tiles) {
-    CK(cudaMemsetAsync(g_adj.cnt_out.p, 0, (size_t)total * sizeof(int), s), "adjoint: clear counts");
-    CK(cudaMemsetAsync(g_adj.tile_state.p, 0, (size_t)total_tiles * sizeof(unsigned), s),
+    CK(cudaMemsetAsync(adj().cnt_out.p, 0, (size_t)total * sizeof(int), s), "adjoint: clear counts");
+    CK(cudaMemsetAsync(adj().tile_state.p, 0, (size_t)total_tiles * sizeof(unsigned), s),
        "adjoint: clear tile states");
   }
-  CK(cudaMemsetAsync(g_adj.ctl.p, 0, sizeof(eik::AdjCtl), s), "adjoint: clear control");
+  CK(cudaMemsetAsync(adj().ctl.p, 0, sizeof(eik::AdjCtl), s), "adjoint: clear control");
   const int64_t tmo_ms = opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000;
-  if (!g_adj.ev0) {
-    CK(cudaEventCreate(&g_adj.ev0), "adjoint: event");
-    CK(cudaEventCreate(&g_adj.ev1), "adjoint: event");
+  if (!adj().ev0) {
+    CK(cudaEventCreate(&adj().ev0), "adjoint: event");
+    CK(cudaEventCreate(&adj().ev1), "adjoint: event");
   }
-  CK(cudaEventRecord(g_adj.ev0, s), "adjoint: event record");
+  CK(cudaEventRecord(adj().ev0, s), "adjoint: event record");
   if (tiles)
-    CK(eik::launch_adjoint_tiles(g_adj.probs.p, nprob, total, total_tiles, hps[0].ndim, g_adj.ctl.p,
-                                 g_adj.tile_state.p, g_adj.ring.p, qcap,
+    CK(eik::launch_adjoint_tiles(adj().probs.p, nprob, total, total_tiles, hps[0].ndim, adj().ctl.p,
+                                 adj().tile_state.p, adj().ring.p, qcap,
                                  opts ? opts->ctas_per_sm : 0, tmo_ms * 1000000ll, s),
        "adjoint launch");
   else
-    CK(eik::launch_adjoint(g_adj.probs.p, nprob, total, g_adj.ctl.p, g_adj.front.p,
+    CK(eik::launch_adjoint(adj().probs.p, nprob, total, adj().ctl.p, adj().front.p,
                            tmo_ms * 1000000ll, s), "adjoint launch");
-  CK(cudaEventRecord(g_adj.ev1, s), "adjoint: event record");
-  CK(cudaMemcpyAsync(g_adj.ctl_host, g_adj.ctl.p, sizeof(eik::AdjCtl), cudaMemcpyDeviceToHost, s),
+  if (sum_shared) {
+    std::vector<const double *> table;
+    std::vector<size_t> first;
+    for (size_t g = 0; g < group_out.size(); ++g) {
+      first.push_back(table.size());
+      for (int i : group_of[g]) table.push_back(ap[(size_t)i].grad);
+    }
+    CK(cudaMemcpyAsync(adj().gptr.p, table.data(), table.size() * sizeof(const double *),
+                       cudaMemcpyHostToDevice, s), "adjoint: upload gradient table");
+    for (size_t g = 0; g < group_out.size(); ++g) {
+      CK(eik::launch_sum_ordered(adj().gptr.p + first[g], (int)group_of[g].size(), group_out[g],
+                                 hps[(size_t)group_of[g][0]].n, s), "adjoint: ordered sum");
+    }
+  }
+  CK(cudaEventRecord(adj().ev1, s), "adjoint: event record");
+  CK(cudaMemcpyAsync(adj().ctl_host, adj().ctl.p, sizeof(eik::AdjCtl), cudaMemcpyDeviceToHost, s),
      "adjoint: read status");
   CK(cudaStreamSynchronize(s), "adjoint");
-  const eik::AdjCtl &c = *g_adj.ctl_host;
+  const eik::AdjCtl &c = *adj().ctl_host;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->good = (int64_t)c.done;
@@ -1473,7 +1617,7 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
     stats->ctas = (int64_t)c.ctas;
     for (int i = 0; i < 4; ++i) stats->detail[i] = (int64_t)c.cycles[i];
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, g_adj.ev0, g_adj.ev1) == cudaSuccess) stats->solve_ms = ms;
+    if (cudaEventElapsedTime(&ms, adj().ev0, adj().ev1) == cudaSuccess) stats->solve_ms = ms;
   }
   if (c.status == eik::kEtimeout) { set_err("adjoint: device wait timed out"); return EIK_ETIMEOUT; }
   if (c.status != 0) return EIK_ECUDA;

@@ -143,6 +143,11 @@ __device__ __forceinline__ unsigned long long from_f(float f) {
          (static_cast<unsigned long long>(b & 0x7fffffu) << 29);
 }
 
+// fp32 (finite, either sign) to the bit pattern of the equal double (exact).
+__device__ __forceinline__ unsigned long long from_f_signed(float f) {
+  return from_f(f) | (static_cast<unsigned long long>(__float_as_uint(f) >> 31) << 63);
+}
+
 __device__ __forceinline__ unsigned long long umin(unsigned long long a, unsigned long long b) {
   return a < b ? a : b;
 }
@@ -406,13 +411,13 @@ __device__ __forceinline__ unsigned long long ffguess(const unsigned long long (
       }
     }
   }
-  // tau = s0 + hi + lo on the FP64 unit (two additions, the second rounded
-  // upward: d-bar is the double just above the real root, so rounding up
-  // lands on it far more often than rounding to nearest)
-  double t = __dadd_rn(xf::as_d(s0), xf::as_d(xf::from_f(u.hi)));
-  const unsigned long long lob = xf::from_f(fabsf(u.lo));
-  t = u.lo < 0.0f ? __dsub_ru(t, xf::as_d(lob)) : __dadd_ru(t, xf::as_d(lob));
-  unsigned long long tau = xf::as_u(t);
+  // tau = s0 + (hi + lo) on the FP64 unit: hi + lo as one double (exact, or
+  // within 2^-53 of u when lo is far below hi), then one addition rounded
+  // upward.  d-bar is the double just above the real root, so rounding the
+  // whole sum up once lands on it far more often than rounding s0 + hi to
+  // nearest first (which loses up to half an ulp of tau before lo is added).
+  const double ud = __dadd_rn(xf::as_d(xf::from_f(u.hi)), xf::as_d(xf::from_f_signed(u.lo)));
+  unsigned long long tau = xf::as_u(__dadd_ru(xf::as_d(s0), ud));
   if (!(tau > s0) || tau >= xf::kInf) tau = s0 + 1ull;
   return tau;
 }
@@ -463,6 +468,40 @@ __device__ __forceinline__ unsigned long long G_slope(unsigned long long tau,
   return as_u(g);
 }
 
+// Is G(tau - 1) < c (ge: G(tau) >= c) or G(tau + 1) >= c (!ge: G(tau) < c)
+// certain without evaluating it?  Rounding-error argument, 3D, for non-negative
+// doubles a_k and c > 0:
+//   each of the five roundings in G (difference, square, two sums) is within
+//   2^-53 relative (underflow is far below the slack), so with
+//   T(x) = sum_k ((x - a_k)^+)^2 exactly, (1 - 2^-53)^5 T <= G <= (1 + 2^-53)^5 T;
+//   with d = tau - prev(tau) (ge) or next(tau) - tau (!ge) and
+//   M = sum_{a_k < tau} (tau - a_k):
+//     T(prev tau) <= T(tau) - 2 d M + 3 d^2,   T(next tau) >= T(tau) + 2 d M,
+//   hence (rho = ((1 + 2^-53) / (1 - 2^-53))^5 <= 1 + 11 * 2^-53)
+//     |G(tau) - c| + 11 * 2^-53 G(tau) < 2 d M - 3 d^2
+//   implies G(prev tau) < c (ge), resp. G(next tau) >= c (!ge).
+// The test runs in fp32 with margins that cover its own roundings: |G - c| in
+// ulps of c rounded up, M from the truncated m_k (msum <= sum m_k), 3 d^2 below
+// 2^-19 of 2 d M (checked), and a 1e-4 relative margin on both sides.  Outside
+// the exponent ranges where these fp32 quantities stay normal it answers no.
+__device__ __forceinline__ bool neighbour_certified(unsigned long long tau, unsigned long long g,
+                                                    unsigned long long cb, float msum, bool ge) {
+  const int et = static_cast<int>(tau >> 52), ec = static_cast<int>(cb >> 52);
+  if (static_cast<int>(g >> 52) != ec || ec < 960 || ec > 1150 || et < 960 || et > 1150) return false;
+  // |G - c| = k ulps of c (same binade), ulp(c) = 2^(ec - 1075): exact power of two
+  const unsigned long long k = ge ? g - cb : cb - g;
+  const float diff = __ull2float_ru(k) * __int_as_float((ec - 948) << 23);
+  // d: ulp(tau), halved below tau when tau is a power of two
+  const int ed = (ge && (tau & xf::kFrac) == 0ull) ? et - 949 : et - 948;
+  const float d = __int_as_float(ed << 23);
+  if (!(msum >= d * 1048576.0f)) return false;                   // 3 d^2 <= 2^-19 (2 d M)
+  const float slack = xf::to_f(g) * 1.33226763e-15f;              // >= 11 * 2^-53 G
+  const float lhs = __fadd_rn(diff, slack);
+  const float rhs = __fmul_rn(2.0f * d, msum);   // exact (2 d a power of two) unless not normal
+  if (!(rhs >= 1.17549435e-38f)) return false;
+  return __fmul_rn(lhs, 1.0001f) < __fmul_rn(rhs, 0.9999f);
+}
+
 // d-bar with the exact G on the FP64 unit: float-float starting point
 // (ffguess), then the exact test G(tau) >= c > G(prev(tau)) with a few ulp
 // steps and bisection as the last resort.  About 13 (2D) FP64 instructions in
@@ -485,11 +524,31 @@ __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned lo
     }
   }
   unsigned long long tau = ffguess<D>(a, cb);
-  // the exact test at the starting point: two independent G evaluations
-  const unsigned long long g_prev = G<D>(tau - 1ull, a);
-  const unsigned long long g_here = G<D>(tau, a);
-  if (g_here >= cb && g_prev < cb) return tau;
-  bool above = g_here >= cb;
+  bool above;
+  if (D == 3) {
+    // G at the starting point first; its side picks the second point: tau - 1
+    // when G(tau) >= c (is tau the smallest?), tau + 1 when G(tau) < c (then
+    // G(tau + 1) >= c makes tau + 1 the smallest).  The float-float starting
+    // point is most often one ulp low in 3D, which this settles without a walk.
+    // The side of the second point is first decided by a rounding-error bound
+    // (no FP64 work); only undecided cells evaluate G there.
+    float msum;
+    const unsigned long long g_here = G_slope<D>(tau, a, msum);
+    const bool ge = g_here >= cb;
+    if (neighbour_certified(tau, g_here, cb, msum, ge)) return ge ? tau : tau + 1ull;
+    const unsigned long long p2 = ge ? tau - 1ull : tau + 1ull;
+    const bool ge2 = G<D>(p2, a) >= cb;
+    if (ge && !ge2) return tau;
+    if (!ge && ge2) return p2;
+    tau = p2;
+    above = ge2;
+  } else {
+    // the exact test at the starting point: two independent G evaluations
+    const unsigned long long g_prev = G<D>(tau - 1ull, a);
+    const unsigned long long g_here = G<D>(tau, a);
+    if (g_here >= cb && g_prev < cb) return tau;
+    above = g_here >= cb;
+  }
   // walk a few ulps; if the root is farther (float-float carries ~47 bits, too
   // few when tau - s0 is large against tau), one Newton step on G(tau) - c on
   // the FP64 unit, walk again, then bracket and bisect

@@ -3,9 +3,15 @@
 #pragma once
 
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 namespace eik {
+
+// The process-wide lock that serialises the C ABI's calls, and the message
+// returned by eik_last_error (both owned by eik_api.cu).
+std::mutex &api_mutex();
+void set_last_error(const char *fmt, ...);
 
 // Bucket ring: NB slots; bucket b lives in slot b & (NB - 1).  Each slot is a
 // ring of `cap` 64-bit entries (cap a power of two) with one sequence word per
@@ -142,8 +148,13 @@ __host__ __device__ inline TileShape tile_shape_of(int ndim, int shape) {
 
 // Launch wrappers (eik_solver.cu).  All enqueue on `stream`.
 // store_r: write r = fl(h/v) instead of c (the explicit update forms use r).
+// from_slowness: `speed` holds slowness s, and v = fl(1/s) is used.
 cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
-                          cudaStream_t stream, int store_r = 0);
+                          cudaStream_t stream, int store_r = 0, int from_slowness = 0);
+// dst[i] = (((+0 + src[0][i]) + src[1][i]) + ...) + src[k-1][i], every addition
+// rounded to nearest in that order (src: device array of k device pointers).
+cudaError_t launch_sum_ordered(const double *const *src, int k, double *dst, int64_t n,
+                               cudaStream_t stream);
 cudaError_t launch_init_t(double *t, int64_t n, cudaStream_t stream);
 // t = +inf on every problem of a batch in one launch (dev_probs: device array;
 // max_cells: the largest problem's cell count).
@@ -215,7 +226,8 @@ cudaError_t launch_residual(int form, int ndim, const double *speed, double h, c
 // Adjoint (eik_adjoint.cu).
 struct AdjProb {
   const double *t;          // forward arrival times (the exact fixed point)
-  const double *v;          // speed
+  const double *v;          // speed (slowness s when v_is_slowness: v = fl(1/s))
+  int v_is_slowness;
   const double *g;          // dL/dt (NULL: 0)
   double *grad;             // dL/ds output
   double *lam;              // adjoint variable (workspace; NULL in the tile schedule)

@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "../../include/eik.h"
@@ -45,9 +46,6 @@ constexpr size_t kOffSeeds = up256(kOffSrcT + sizeof(double) * kMaxSources);
 constexpr size_t kBytes = up256(kOffSeeds + sizeof(SeedItem) * kMaxSources);
 
 __device__ __align__(256) unsigned char g_scratch[kBytes];
-
-constexpr int kMaxDevices = 64;
-unsigned char *g_base[kMaxDevices] = {};           // device address of g_scratch, per device
 
 // Validate, sort and de-duplicate the sources (smallest time per cell), write
 // the problem record and one seed item per input source (duplicates repeat
@@ -152,62 +150,70 @@ bool device_ptr(const void *p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-}  // namespace na
-}  // namespace eik
+// Every return path of eik_solve_noalloc leaves its reason for eik_last_error.
+eik_status fail(eik_status st, const char *msg) {
+  set_last_error("eik_solve_noalloc: %s", msg);
+  return st;
+}
+eik_status cuda_fail(cudaError_t e, const char *what) {
+  cudaGetLastError();
+  set_last_error("eik_solve_noalloc: %s: %s", what, cudaGetErrorString(e));
+  return EIK_ECUDA;
+}
 
-extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
-                                        const int64_t *dims, const int64_t *src_idx,
-                                        const double *src_t, int64_t nsrc, double *out_t,
-                                        const eik_opts *opts, eik_stats *stats, void *stream) {
-  using namespace eik;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if ((ndim != 2 && ndim != 3) || !dims || !(h > 0.0) || !(h < 1e308)) return EIK_EINVAL;
+eik_status solve(const double *speed, double h, int ndim, const int64_t *dims,
+                 const int64_t *src_idx, const double *src_t, int64_t nsrc, double *out_t,
+                 const eik_opts *opts, eik_stats *stats, cudaStream_t s) {
+  if (ndim != 2 && ndim != 3) return fail(EIK_EINVAL, "ndim must be 2 or 3");
+  if (!dims) return fail(EIK_EINVAL, "dims is NULL");
+  if (!(h > 0.0) || !(h < 1e308)) return fail(EIK_EINVAL, "h must be finite and > 0");
   int64_t n = 1;
   for (int k = 0; k < ndim; ++k) {
-    if (dims[k] < 1 || dims[k] > na::kMaxCells) return EIK_EINVAL;
+    if (dims[k] < 1) return fail(EIK_EINVAL, "every extent must be >= 1");
+    if (dims[k] > kMaxCells) return fail(EIK_EINVAL, "more than 2^20 cells (the scratch limit)");
     n *= dims[k];
-    if (n > na::kMaxCells) return EIK_EINVAL;                 // beyond the scratch limit
+    if (n > kMaxCells) return fail(EIK_EINVAL, "more than 2^20 cells (the scratch limit)");
   }
-  if (nsrc < 0 || nsrc > na::kMaxSources) return EIK_EINVAL;  // beyond the scratch limit
+  if (nsrc < 0) return fail(EIK_EINVAL, "nsrc must be >= 0");
+  if (nsrc > kMaxSources) return fail(EIK_EINVAL, "more than 2048 sources (the scratch limit)");
   if (opts && (opts->update != 0 || opts->tile != 0 || opts->schedule != 0))
-    return EIK_EINVAL;   // default form, tile and schedule only
-  if (!na::device_ptr(speed) || !na::device_ptr(out_t)) return EIK_EINVAL;
-  if (nsrc > 0 && !na::device_ptr(src_idx)) return EIK_EINVAL;
-  if (src_t && !na::device_ptr(src_t)) return EIK_EINVAL;
+    return fail(EIK_EINVAL, "opts.update, opts.tile and opts.schedule must be 0");
+  if (!device_ptr(speed) || !device_ptr(out_t))
+    return fail(EIK_EINVAL, "speed and out_t must be device pointers");
+  if (nsrc > 0 && !device_ptr(src_idx)) return fail(EIK_EINVAL, "src_idx must be a device pointer");
+  if (src_t && !device_ptr(src_t)) return fail(EIK_EINVAL, "src_t must be a device pointer");
   const int64_t nx = dims[ndim - 1], ny = dims[ndim - 2], nz = ndim == 3 ? dims[0] : 1;
   const int64_t tx = ndim == 3 ? kTX3 : kTX2, ty = ndim == 3 ? kTY3 : kTY2, tz = ndim == 3 ? kTZ3 : 1;
   const int64_t ntx = (nx + tx - 1) / tx, nty = (ny + ty - 1) / ty, ntz = (nz + tz - 1) / tz;
   const int64_t ntiles = ntx * nty * ntz;
-  if (ntiles > na::kMaxTiles) return EIK_EINVAL;              // beyond the scratch limit
+  if (ntiles > kMaxTiles) return fail(EIK_EINVAL, "more than 2^15 tiles (the scratch limit)");
 
-  // once per device, with that device current: the device address of the array
+  // The device address of the array on the current device.  In host code the
+  // name g_scratch is a host-side stand-in, not a device address; the lookup
+  // allocates nothing and is repeated on every call (no per-device cache).
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= na::kMaxDevices) return EIK_ECUDA;
-  if (!na::g_base[dev]) {
-    void *ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, na::g_scratch) != cudaSuccess || !ptr) {
-      cudaGetLastError();
-      return EIK_ECUDA;
-    }
-    na::g_base[dev] = static_cast<unsigned char *>(ptr);
-  }
-  unsigned char *base = na::g_base[dev];
-  Ctl *ctl = reinterpret_cast<Ctl *>(base + na::kOffCtl);
-  Prob *prob_dev = reinterpret_cast<Prob *>(base + na::kOffProb);
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  void *ptr = nullptr;
+  e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+  if (!ptr) return fail(EIK_ECUDA, "cudaGetSymbolAddress gave a null address");
+  unsigned char *base = static_cast<unsigned char *>(ptr);
+  Ctl *ctl = reinterpret_cast<Ctl *>(base + kOffCtl);
+  Prob *prob_dev = reinterpret_cast<Prob *>(base + kOffProb);
 
   // clear what must start at zero (the array keeps the previous call's contents)
-  if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess ||
-      cudaMemsetAsync(base + na::kOffState, 0, sizeof(unsigned long long) * ntiles, s) != cudaSuccess ||
-      cudaMemsetAsync(base + na::kOffTileSrc, 0, ntiles, s) != cudaSuccess ||
-      cudaMemsetAsync(base + na::kOffPend, 0, sizeof(unsigned) * kPendWords * ntiles, s) != cudaSuccess ||
-      cudaMemsetAsync(base + na::kOffSeq, 0, sizeof(unsigned) * kNumSlots * na::kCap, s) !=
-          cudaSuccess) {
-    return EIK_ECUDA;
+  if ((e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(base + kOffState, 0, sizeof(unsigned long long) * ntiles, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(base + kOffTileSrc, 0, ntiles, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(base + kOffPend, 0, sizeof(unsigned) * kPendWords * ntiles, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(base + kOffSeq, 0, sizeof(unsigned) * kNumSlots * kCap, s)) != cudaSuccess) {
+    return cuda_fail(e, "clearing the scratch array");
   }
   Prob prob;
   std::memset(&prob, 0, sizeof(prob));
   prob.t = out_t;
-  prob.c = reinterpret_cast<const double *>(base + na::kOffC);
+  prob.c = reinterpret_cast<const double *>(base + kOffC);
   prob.nx = nx;
   prob.ny = ny;
   prob.nz = nz;
@@ -215,29 +221,31 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
   prob.nty = nty;
   prob.ntz = ntz;
   prob.tile_base = 0;
-  prob.src_idx = reinterpret_cast<const int64_t *>(base + na::kOffSrcIdx);
-  prob.src_t = reinterpret_cast<const double *>(base + na::kOffSrcT);
+  prob.src_idx = reinterpret_cast<const int64_t *>(base + kOffSrcIdx);
+  prob.src_t = reinterpret_cast<const double *>(base + kOffSrcT);
   prob.nsrc = 0;
 
-  if (launch_init_c(speed, h, reinterpret_cast<double *>(base + na::kOffC), n, ctl, s) != cudaSuccess ||
-      launch_init_t(out_t, n, s) != cudaSuccess) {
-    return EIK_ECUDA;
+  const int from_slowness = opts && (opts->sched_flags & (1 << 6)) ? 1 : 0;
+  if ((e = launch_init_c(speed, h, reinterpret_cast<double *>(base + kOffC), n, ctl, s, 0,
+                         from_slowness)) != cudaSuccess ||
+      (e = launch_init_t(out_t, n, s)) != cudaSuccess) {
+    return cuda_fail(e, "set-up launch");
   }
-  na::sources_kernel<<<1, na::kSortThreads, 0, s>>>(src_idx, src_t, nsrc, prob, n, base);
+  sources_kernel<<<1, kSortThreads, 0, s>>>(src_idx, src_t, nsrc, prob, n, base);
   note_launches(1);
-  if (cudaGetLastError() != cudaSuccess) return EIK_ECUDA;
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "sources launch");
 
   SolveParams sp;
   std::memset(&sp, 0, sizeof(sp));
   sp.probs = prob_dev;
   sp.nprob = 1;
   sp.ndim = ndim;
-  sp.state = reinterpret_cast<unsigned long long *>(base + na::kOffState);
-  sp.tile_src = base + na::kOffTileSrc;
-  sp.pend = reinterpret_cast<unsigned *>(base + na::kOffPend);
-  sp.slots = reinterpret_cast<unsigned long long *>(base + na::kOffSlots);
-  sp.seq = reinterpret_cast<unsigned *>(base + na::kOffSeq);
-  sp.cap_mask = static_cast<unsigned>(na::kCap - 1);
+  sp.state = reinterpret_cast<unsigned long long *>(base + kOffState);
+  sp.tile_src = base + kOffTileSrc;
+  sp.pend = reinterpret_cast<unsigned *>(base + kOffPend);
+  sp.slots = reinterpret_cast<unsigned long long *>(base + kOffSlots);
+  sp.seq = reinterpret_cast<unsigned *>(base + kOffSeq);
+  sp.cap_mask = static_cast<unsigned>(kCap - 1);
   sp.ctl = ctl;
   sp.timeout_ns = (opts && opts->timeout_ms > 0 ? opts->timeout_ms : 60000) * 1000000ll;
   sp.counters = opts ? opts->counters : 0;
@@ -250,9 +258,9 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
   sp.trace_cap = 0;
   const double k_delta = opts && opts->k_delta > 0 ? opts->k_delta : (ndim == 3 ? 2.0 : 16.0);
   const double delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
-  if (launch_seed(sp, reinterpret_cast<const SeedItem *>(base + na::kOffSeeds), nsrc, k_delta,
-                  delta_fixed, s) != cudaSuccess) {
-    return EIK_ECUDA;
+  if ((e = launch_seed(sp, reinterpret_cast<const SeedItem *>(base + kOffSeeds), nsrc, k_delta,
+                       delta_fixed, s)) != cudaSuccess) {
+    return cuda_fail(e, "seed launch");
   }
   int sms = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -264,24 +272,27 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
   if (grid < 1) grid = 1;
   // lane-group d-bar when the solve has few tiles per CTA (as the main path)
   sp.lane_group_cells = ntiles < 8 * grid ? static_cast<int>(tx * ty * tz / 4) : 0;
-  if (launch_persistent(sp, static_cast<int>(grid), s) != cudaSuccess) return EIK_ECUDA;
+  if ((e = launch_persistent(sp, static_cast<int>(grid), s)) != cudaSuccess)
+    return cuda_fail(e, "solve launch");
 
-  unsigned long long *count = reinterpret_cast<unsigned long long *>(base + na::kOffCount);
+  unsigned long long *count = reinterpret_cast<unsigned long long *>(base + kOffCount);
   if (stats) {
-    if (cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess ||
-        launch_count_finite(&prob, 1, count, s) != cudaSuccess) {
-      return EIK_ECUDA;
+    if ((e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), s)) != cudaSuccess ||
+        (e = launch_count_finite(&prob, 1, count, s)) != cudaSuccess) {
+      return cuda_fail(e, "count launch");
     }
   }
   // read back the status and counters into host stack memory
   unsigned status = 0;
   unsigned long long st[kNumStats];
   unsigned long long finite = 0;
-  if (cudaMemcpyAsync(&status, &ctl->status, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(st, ctl->stats, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      (stats && cudaMemcpyAsync(&finite, count, sizeof(finite), cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    return EIK_ECUDA;
+  unsigned long long info = 0;
+  if ((e = cudaMemcpyAsync(&status, &ctl->status, sizeof(status), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&info, &ctl->error_info[0], sizeof(info), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(st, ctl->stats, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (stats && (e = cudaMemcpyAsync(&finite, count, sizeof(finite), cudaMemcpyDeviceToHost, s)) != cudaSuccess) ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    return cuda_fail(e, "status read-back");
   }
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -293,18 +304,37 @@ extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
     stats->rounds = static_cast<int64_t>(st[kStatRounds]);
     stats->ctas = grid;
   }
-  if (status == kEinval) return EIK_EINVAL;
-  if (status == kEtimeout) return EIK_ETIMEOUT;
-  if (status == kEcapacity) return EIK_ECAPACITY;
-  if (status != 0) return EIK_ECUDA;
+  if (status == kEinval) {
+    if (info == ~0ull)
+      return fail(EIK_EINVAL, "invalid sources (index out of range, or time negative, NaN or inf)");
+    set_last_error("eik_solve_noalloc: invalid input data (cell %llu: speed must be finite and > 0, "
+                   "h/v finite and > 0)", info);
+    return EIK_EINVAL;
+  }
+  if (status == kEtimeout) return fail(EIK_ETIMEOUT, "a device wait reached its limit");
+  if (status == kEcapacity)
+    return fail(EIK_ECAPACITY, "frontier overflow (no capacity retry without allocation)");
+  if (status != 0) return fail(EIK_ECUDA, "unexpected device status");
   if (stats) {
     // good = reached non-source cells; the number of unique sources is in the problem record
     Prob pr;
-    if (cudaMemcpyAsync(&pr, prob_dev, sizeof(pr), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-      return EIK_ECUDA;
+    if ((e = cudaMemcpyAsync(&pr, prob_dev, sizeof(pr), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+      return cuda_fail(e, "problem record read-back");
     }
     stats->good = static_cast<int64_t>(finite) - pr.nsrc;
   }
   return EIK_OK;
+}
+
+}  // namespace na
+}  // namespace eik
+
+extern "C" eik_status eik_solve_noalloc(const double *speed, double h, int ndim,
+                                        const int64_t *dims, const int64_t *src_idx,
+                                        const double *src_t, int64_t nsrc, double *out_t,
+                                        const eik_opts *opts, eik_stats *stats, void *stream) {
+  std::lock_guard<std::mutex> lk(eik::api_mutex());
+  return eik::na::solve(speed, h, ndim, dims, src_idx, src_t, nsrc, out_t, opts, stats,
+                        static_cast<cudaStream_t>(stream));
 }

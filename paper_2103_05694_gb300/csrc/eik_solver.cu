@@ -55,6 +55,9 @@ __device__ __forceinline__ double from_bits(unsigned long long u) {
 __device__ __forceinline__ unsigned long long umin64(unsigned long long a, unsigned long long b) {
   return a < b ? a : b;
 }
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a < b ? b : a;
+}
 
 // Minimum of a 64-bit value over the full warp with two warp-reduce
 // instructions (high words first, then the low words of the lanes that hold
@@ -64,6 +67,17 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
   const unsigned lo = __reduce_min_sync(
       0xffffffffu, static_cast<unsigned>(v >> 32) == hi ? static_cast<unsigned>(v) : 0xffffffffu);
   return (static_cast<unsigned long long>(hi) << 32) | lo;
+}
+
+// One axis of a cell after an acceptance step: sides (left/right) with their
+// values after the step and whether they changed (decreased).  True when the
+// axis minimum decreased and is now below `best`: the smallest changed value
+// lies below every unchanged side's value and below `best`.
+__device__ __forceinline__ bool axis_fell(bool c1, unsigned long long v1, bool c2,
+                                          unsigned long long v2, unsigned long long best) {
+  const unsigned long long lowered = umin64(c1 ? v1 : kInfBits, c2 ? v2 : kInfBits);
+  const unsigned long long kept = umin64(c1 ? kInfBits : v1, c2 ? kInfBits : v2);
+  return lowered < kept && lowered < best;
 }
 
 // A cell's candidate is pending while it differs from the cell's value
@@ -425,7 +439,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
   __shared__ unsigned long long s_min[3];
   __shared__ unsigned long long s_cmin;
   __shared__ unsigned long long s_vlim;
-  __shared__ unsigned long long s_band;
+  __shared__ float s_band_f;
   __shared__ long long s_tile;
   __shared__ int s_prob, s_faces;
   __shared__ unsigned s_slot, s_lo;
@@ -582,22 +596,25 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
     __syncthreads();
     if (timing) { const long long c1 = clock64(); cyc[0] += c1 - c0; c0 = c1; }
     if (first && tid == 0) {   // band = k * sqrt(c_min) / sqrt(D): one cell's travel time
-      const float cm = s_cmin < kInfBits ? __double2float_rn(from_bits(s_cmin)) : 0.0f;
+      const float cm = s_cmin < kInfBits ? xf::to_f(s_cmin) : 0.0f;
       // s_cmin is the smallest c (or r for the explicit roots): one cell's travel time
-      s_band = bits_of(static_cast<double>((p.update ? cm : sqrtf(cm)) * band_scale));
+      s_band_f = (p.update ? cm : sqrtf(cm)) * band_scale;
       s_cmin = kInfBits;
     }
     vlim = s_vlim;
 
     const double tv0 = tv;
-    bool need = active;
-    if (need && !(faces_now & (1 << kFaceFull))) {
-      const bool pend_cell = first ? ((pword >> lane) & 1u) != 0u : is_pending(s_pv[tid], bits_of(tv));
-      need = ((faces_now & 1) && lx == 0) || ((faces_now & 2) && lx == TX - 1) ||
-             ((faces_now & 4) && ly == 0) || ((faces_now & 8) && ly == TY - 1) ||
-             (D == 3 && (((faces_now & 16) && lz == 0) || ((faces_now & 32) && lz == TZ - 1))) ||
-             pend_cell;
-    }
+    // cells to evaluate in the pass's first round: every cell (a seeded tile),
+    // cells with a deferred candidate, and cells on a face whose halo changed
+    // (bit k of face_need: the neighbour across face k)
+    const bool full_pass = (faces_now & (1 << kFaceFull)) != 0;
+    const bool pend_cell = first ? ((pword >> lane) & 1u) != 0u : is_pending(s_pv[tid], bits_of(tv));
+    const unsigned face_need =
+        (((faces_now & 1) && lx == 0) ? 1u : 0u) | (((faces_now & 2) && lx == TX - 1) ? 2u : 0u) |
+        (((faces_now & 4) && ly == 0) ? 4u : 0u) | (((faces_now & 8) && ly == TY - 1) ? 8u : 0u) |
+        ((D == 3 && (faces_now & 16) && lz == 0) ? 16u : 0u) |
+        ((D == 3 && (faces_now & 32) && lz == TZ - 1) ? 32u : 0u);
+    bool need = active && (full_pass || pend_cell || face_need != 0u);
     // Pending candidates live in s_pv (owner-indexed); a candidate is pending
     // while it differs from the cell's value, so accepting it needs no clearing.
     // The values at the start of round R are in s_t[R & 1].  Accepting round
@@ -618,7 +635,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         m = s_min[(R - 1u) % 3u];
         ++rounds;
         if (m >= vlim) break;   // nothing pending below the visit limit (uniform)
-        lim = umin64(bits_of(__dadd_rn(from_bits(m), from_bits(s_band))), vlim - 1);
+        // m + band on the FP32 pipe (every thread gets the same value; the band is
+        // a scheduling heuristic), never below m so the smallest candidate is
+        // always accepted
+        const float lf = __fadd_rn(xf::to_f(m), s_band_f);
+        lim = umin64(umax64(xf::from_f(lf), m), vlim - 1);
       }
       bool acc = false;
       const unsigned long long pv = s_pv[tid];
@@ -632,35 +653,57 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         if (lane == 0 && keep < kInfBits) atomicMin(&s_min[R % 3u], keep);
       }
       if (accept) s_t[b][zc][yc][xc] = tv;
-      // (A) neighbour values after the acceptance, whether they changed, and the
+      // (A) neighbour values after the acceptance, which of them changed, and the
       //     exact integer filters; the cells that may decrease go on a dense list
       //     for the FP64 phase
       double xl = __shfl_up_sync(kFull, tv, 1, TX);
       double xr = __shfl_down_sync(kFull, tv, 1, TX);
       const unsigned accbits = __ballot_sync(kFull, acc);
-      bool changed = (lx > 0 && ((accbits >> (lane - 1)) & 1u)) ||
-                     (lx < TX - 1 && ((accbits >> (lane + 1)) & 1u));
+      const bool cxl = lx > 0 && ((accbits >> (lane - 1)) & 1u);
+      const bool cxr = lx < TX - 1 && ((accbits >> (lane + 1)) & 1u);
       if (lx == 0) xl = s_t[bo][zc][yc][0];
       if (lx == TX - 1) xr = s_t[bo][zc][yc][TX + 1];
       // a neighbour in another warp (or the halo) at offset (dz, dy) and tile
-      // thread offset dt: its value after the acceptance
-      auto across = [&](int dz, int dy, int dt, bool inside) -> double {
+      // thread offset dt: its value after the acceptance, and whether it changed
+      auto across = [&](int dz, int dy, int dt, bool inside, bool &chg) -> double {
+        chg = false;
         const double old = s_t[accept ? bo : b][zc + dz][yc + dy][xc];
         if (!accept || !inside) return old;
         const unsigned long long q = s_pv[tid + dt];
         if (is_pending(q, bits_of(old)) && q <= lim) {
-          changed = true;
+          chg = true;
           return from_bits(q);
         }
         return old;
       };
-      const double yl = across(0, -1, -TX, ly > 0), yr = across(0, 1, TX, ly < TY - 1);
+      bool cyl, cyr, czl = false, czr = false;
+      const double yl = across(0, -1, -TX, ly > 0, cyl), yr = across(0, 1, TX, ly < TY - 1, cyr);
       double zl = 0.0, zr = 0.0;
       if constexpr (D == 3) {
-        zl = across(-1, 0, -TX * TY, lz > 0);
-        zr = across(1, 0, TX * TY, lz < TZ - 1);
+        zl = across(-1, 0, -TX * TY, lz > 0, czl);
+        zr = across(1, 0, TX * TY, lz < TZ - 1, czr);
       }
-      if (accept) need = active && changed;
+      // change tracking compares with the cell's value (a recomputed value may
+      // also be larger); otherwise a candidate must beat value and pending
+      const unsigned long long best =
+          p.track_changes ? bits_of(tv) : umin64(bits_of(tv), is_pending(pv, bits_of(tv)) ? pv : kInfBits);
+      if (p.update) {
+        // the explicit forms (not monotone): any neighbour change re-evaluates
+        if (accept) need = active && (cxl || cxr || cyl || cyr || czl || czr);
+      } else if (accept) {
+        // d-bar (monotone, causal): the cell can decrease only if an axis
+        // minimum fell below `best` -- for tau < best, G(tau) is unchanged when
+        // every axis minimum that moved is still >= best, so d-bar < best iff it
+        // was before (and it was not, or the cell would hold that value)
+        need = active && (axis_fell(cxl, bits_of(xl), cxr, bits_of(xr), best) ||
+                          axis_fell(cyl, bits_of(yl), cyr, bits_of(yr), best) ||
+                          (D == 3 && axis_fell(czl, bits_of(zl), czr, bits_of(zr), best)));
+      } else if (need && !full_pass && !pend_cell) {
+        // first round: a changed halo value matters only below `best`
+        need = ((face_need & 1u) && bits_of(xl) < best) || ((face_need & 2u) && bits_of(xr) < best) ||
+               ((face_need & 4u) && bits_of(yl) < best) || ((face_need & 8u) && bits_of(yr) < best) ||
+               ((face_need & 16u) && bits_of(zl) < best) || ((face_need & 32u) && bits_of(zr) < best);
+      }
       bool go = false;
       if (need) {
         unsigned long long a[D];
@@ -670,10 +713,6 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         unsigned long long amin = a[0];
 #pragma unroll
         for (int k = 1; k < D; ++k) amin = umin64(amin, a[k]);
-        // change tracking compares with the cell's value (a recomputed value may
-        // also be larger); otherwise a candidate must beat value and pending
-        const unsigned long long best =
-            p.track_changes ? bits_of(tv) : umin64(bits_of(tv), is_pending(pv, bits_of(tv)) ? pv : kInfBits);
         go = amin < kInfBits && (p.track_changes || best > amin);
         if (go) {
 #pragma unroll
@@ -921,12 +960,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
 // (h/v)^2 of Eq. difference_as_root); checks v > 0 finite and r, c finite and
 // positive; sums r = fl(h / v) for the auto bucket width.
 __global__ void init_c_kernel(const double *__restrict__ speed, double h, double *__restrict__ c_out,
-                              int64_t n, Ctl *ctl, int store_r) {
+                              int64_t n, Ctl *ctl, int store_r, int from_slowness) {
   double sum = 0.0;
   unsigned long long cnt = 0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const double v = speed[i];
+    // slowness input: the speed is v = fl(1/s), correctly rounded
+    const double v = from_slowness ? __ddiv_rn(1.0, speed[i]) : speed[i];
     const double ri = __ddiv_rn(h, v);
     const double c = __dmul_rn(ri, ri);
     const bool ok = v > 0.0 && bits_of(v) < kInfBits && ri > 0.0 && bits_of(ri) < kInfBits &&
@@ -944,6 +984,20 @@ __global__ void init_c_kernel(const double *__restrict__ speed, double h, double
   if ((threadIdx.x & 31) == 0 && cnt) {
     atomicAdd(&ctl->rsum, sum);
     atomicAdd(&ctl->rcount, cnt);
+  }
+}
+
+// Sum of k arrays in a fixed order (the cross-source gradient of a
+// tomography batch): starting from +0, src[0], src[1], ... are added one
+// after the other, each addition rounded to nearest.  Streams k + 1 arrays:
+// 8 (k + 1) bytes per element, HBM-bound.
+__global__ void sum_ordered_kernel(const double *const *__restrict__ src, int k,
+                                   double *__restrict__ dst, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = __dadd_rn(acc, __ldcs(src[j] + i));
+    dst[i] = acc;
   }
 }
 
@@ -1118,9 +1172,17 @@ void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_o
 unsigned long long kernel_launches() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t launch_init_c(const double *speed, double h, double *c, int64_t n, Ctl *ctl,
-                          cudaStream_t stream, int store_r) {
+                          cudaStream_t stream, int store_r, int from_slowness) {
   if (n <= 0) return cudaSuccess;
-  init_c_kernel<<<grid_for(n, 8), 256, 0, stream>>>(speed, h, c, n, ctl, store_r);
+  init_c_kernel<<<grid_for(n, 8), 256, 0, stream>>>(speed, h, c, n, ctl, store_r, from_slowness);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sum_ordered(const double *const *src, int k, double *dst, int64_t n,
+                               cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  sum_ordered_kernel<<<grid_for(n, 8), 256, 0, stream>>>(src, k, dst, n);
   note_launches(1);
   return cudaGetLastError();
 }

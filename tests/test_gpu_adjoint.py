@@ -75,8 +75,49 @@ def test_autograd_function_matches_oracle_adjoint():
         _, gs = oracle.adjoint(v_used, p.h, src, tt, 0.5 * w[i].cpu().numpy())
         total = total + gs
     got = s.grad.cpu().numpy()
-    assert np.allclose(got, total, rtol=1e-14, atol=0)
+    # the library converts slowness on the device and sums the per-source
+    # gradients from +0 in source order, as the loop above does
+    assert np.array_equal(got.view(np.uint64), total.view(np.uint64))
     del speed
+
+
+@pytest.mark.parametrize("sched", sorted(SCHEDULES))
+def test_slowness_input_and_ordered_gradient_sum(sched):
+    """sched_flags bit 6 (slowness in, v = fl(1/s) on the device) and bit 7
+    (problems sharing a gradient array receive +0 + g_0 + g_1 + ... in problem
+    order): equal to the oracle forward and adjoint run on v = 1/s and summed
+    in the same order, bit for bit; two groups of outputs, one of them with a
+    single problem."""
+    rng = np.random.Generator(np.random.PCG64(77))
+    shape = (23, 31) if sched == "levels" else (9, 11, 13)
+    base = synth.random_problem(41, shape, n_src=1, contrast=5.0, smooth_sigma=1.0, h=0.75)
+    s_np = 1.0 / base.speed
+    v = 1.0 / s_np
+    slow = torch.from_numpy(s_np).to(DEV)
+    N = s_np.size
+    srcs = [rng.choice(N, size=1 + k % 2, replace=False).astype(np.int64) for k in range(4)]
+    outs = [torch.empty_like(slow) for _ in srcs]
+    probs = [{"speed": slow, "h": base.h, "sources": torch.from_numpy(src).to(DEV), "out": o}
+             for src, o in zip(srcs, outs)]
+    eik.eik_solve_batched(probs, {"sched_flags": eik.SLOWNESS_INPUT})
+    gs_dev = [torch.from_numpy(rng.standard_normal(shape) * (rng.random(shape) < 0.2)).to(DEV)
+              for _ in srcs]
+    shared, single = torch.full_like(slow, np.nan), torch.full_like(slow, np.nan)
+    eik.eik_adjoint(probs, gs_dev, [shared, single, shared, shared],
+                    {"sched_flags": eik.SLOWNESS_INPUT | eik.SUM_SHARED_GRADIENTS | SCHEDULES[sched],
+                     "timeout_ms": 10000})
+    torch.cuda.synchronize()
+    want_shared, want_single = np.zeros(shape), np.zeros(shape)
+    for k, (src, o, g) in enumerate(zip(srcs, outs, gs_dev)):
+        t = oracle.fmm(v, base.h, src).t
+        assert np.array_equal(o.cpu().numpy().view(np.uint64), t.view(np.uint64))
+        gk = oracle.adjoint(v, base.h, src, t, g.cpu().numpy())[1]
+        if k == 1:
+            want_single = want_single + gk
+        else:
+            want_shared = want_shared + gk
+    assert np.array_equal(shared.cpu().numpy().view(np.uint64), want_shared.view(np.uint64))
+    assert np.array_equal(single.cpu().numpy().view(np.uint64), want_single.view(np.uint64))
 
 
 @pytest.mark.parametrize("sched", sorted(SCHEDULES))
@@ -108,6 +149,24 @@ def test_adjoint_bit_exact_vs_oracle_tomography_grid(sched):
         assert np.array_equal(p["grad"].cpu().numpy().view(np.uint64), gs.view(np.uint64))
 
 
+def _upwind_masks(t):
+    """Per cell of a (sources, ny, nx) stack of fields: for each axis, which side
+    holds the axis minimum (low, high or a tie) and whether the axis is active
+    (minimum below the cell's time).  Two fields with equal masks everywhere
+    are solutions of the same local equations (no upwind switch between them)."""
+    inf = torch.full_like(t[..., :1], float("inf"))
+    codes = []
+    for ax in (2, 1):
+        tt = t if ax == 2 else t.transpose(1, 2)
+        lo = torch.cat([inf, tt[..., :-1]], dim=-1)
+        hi = torch.cat([tt[..., 1:], inf], dim=-1)
+        side = (lo < hi).to(torch.int8) + 2 * (hi < lo).to(torch.int8)     # 0 = tie
+        active = (torch.minimum(lo, hi) < tt).to(torch.int8)
+        code = side + 4 * active
+        codes.append(code if ax == 2 else code.transpose(1, 2))
+    return codes[0] + 8 * codes[1]
+
+
 @pytest.mark.slow
 def test_tomography_gradient_central_differences():
     """1024^2, 32 sources, 512 receivers, L = 1/2 sum (t - t_obs)^2.  Finite
@@ -117,8 +176,11 @@ def test_tomography_gradient_central_differences():
     D is formed from t+ - t- so it does not cancel in L itself.  A step of
     1e-4 keeps the rounding of the perturbed times (a few ulps, ~1e-8 of the
     difference) and the stencil's eps^4 term far below the tolerance.
-    Relative error against max(|g_FD|, 1e-3 max|g|) must be <= 1e-6 (a
-    perturbation may flip an upwind choice: at most a few cells may exceed it).
+    Relative error against max(|g_FD|, 1e-3 max|g|) must be <= 1e-6, except at
+    cells whose perturbations switch an upwind choice somewhere in the 32
+    fields (the upwind masks of the four perturbed solutions differ: the loss
+    has a kink inside the stencil, so central differences do not estimate the
+    derivative there).  Those cells are listed; every other cell must pass.
     The four perturbed fields x 32 sources of one cell run as one batch."""
     cfg = synth.tomography_2d_1024()
     h = cfg["h"]
@@ -143,28 +205,35 @@ def test_tomography_gradient_central_differences():
 
     steps = (1.0, -1.0, 2.0, -2.0)          # multiples of eps
     speeds = [torch.empty_like(s0) for _ in steps]
-    outs = [[torch.empty_like(s0) for _ in srcs] for _ in steps]
+    outs = [torch.empty((len(srcs), n, n), dtype=torch.float64, device=DEV) for _ in steps]
     probs = [{"speed": speeds[j], "h": h, "sources": src, "out": outs[j][i]}
              for j in range(len(steps)) for i, src in enumerate(srcs)]
-    fd = []
+    fd, kink = [], []
     with torch.no_grad():
         for c in cells:
             eps = 1e-4 * float(s0.reshape(-1)[c])
             for j, m in enumerate(steps):
                 sp = s0.clone().reshape(-1)
                 sp[c] += m * eps
-                speeds[j].copy_(torch.reciprocal(sp.reshape(n, n)))
-            eik.eik_solve_batched(probs)
-            tr = [torch.stack([o.reshape(-1)[rcv] for o in outs[j]]) for j in range(len(steps))]
+                speeds[j].copy_(sp.reshape(n, n))
+            eik.eik_solve_batched(probs, {"sched_flags": eik.SLOWNESS_INPUT})
+            tr = [outs[j].reshape(len(srcs), -1)[:, rcv] for j in range(len(steps))]
+            masks = [_upwind_masks(outs[j]) for j in range(len(steps))]
+            kink.append(any(not torch.equal(masks[0], mk) for mk in masks[1:]))
 
             def D(jp, jm):
                 return float(0.5 * ((tr[jp] - tr[jm]) * (tr[jp] + tr[jm] - 2.0 * t_obs)).sum())
             fd.append((8.0 * D(0, 1) - D(2, 3)) / (12.0 * eps))
     fd = np.array(fd)
+    kink = np.array(kink)
     ad = flat[torch.from_numpy(cells).to(DEV)].cpu().numpy()
     scale = np.maximum(np.abs(fd), 1e-3 * gmax)
     err = np.abs(ad - fd) / scale
-    print("tomography FD: median rel err %.2e, max %.2e, cells > 1e-6: %d"
-          % (np.median(err), err.max(), int((err > 1e-6).sum())))
+    over = err > 1e-6
+    print("tomography FD: median rel err %.2e, max over smooth cells %.2e; cells above 1e-6: %d "
+          "(all at an upwind switch: cells %s, errors %s); upwind switches at %d cells"
+          % (np.median(err), err[~kink].max() if (~kink).any() else 0.0, int(over.sum()),
+             cells[over].tolist(), np.round(err[over], 9).tolist(), int(kink.sum())))
     assert np.median(err) <= 1e-6, (np.median(err), err.max())
-    assert int((err > 1e-6).sum()) <= 3, err
+    unexplained = over & ~kink
+    assert not unexplained.any(), (cells[unexplained], err[unexplained])

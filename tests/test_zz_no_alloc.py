@@ -82,6 +82,8 @@ def test_noalloc_rejects_inputs_beyond_its_limits():
         eik.eik_solve_noalloc(small.data_ptr(), 1.0, 2, small.shape, bad_src.data_ptr(), None, 1,
                               out.data_ptr())
     assert ei.value.status == eik.EIK_EINVAL
+    # the message names this call and the reason, not an earlier call's error
+    assert "eik_solve_noalloc" in str(ei.value) and "sources" in str(ei.value)
     # still usable afterwards
     good = torch.zeros(1, dtype=torch.int64, device=DEV)
     eik.eik_solve_noalloc(small.data_ptr(), 1.0, 2, small.shape, good.data_ptr(), None, 1,
