@@ -7,13 +7,15 @@ with the exactly monotone d-bar of arXiv 2103.05694); for the tomography
 workload the step adds the adjoint gradient.  Workloads (synthetic, seeded):
 
   layered_2d     2D layered seismic-like section 2301 x 751, h = 4 m, one
-                 surface source (default; it stands in for the Marmousi section)
+                 surface source (it stands in for the Marmousi section)
   const_2d       2D 129 x 129, constant speed, h = 1/128, centre source
   checker_3d     3D 256^3 smooth random 1500-4500 m/s with a 10:1 checkerboard
                  in the central 128^3 block, h = 10 m, source at (128, 128, 0)
   batched_3d     64 single-source solves on one shared smooth 128^3 model plus
                  24 grids of uneven size (64^3..192^3, 1-4 sources each), one
-                 plan replayed from a captured CUDA graph
+                 plan replayed from a captured CUDA graph, options autotuned
+                 before the timed region (default: the largest single-GPU
+                 workload)
   tomography_2d  2D 1024^2, 32 surface sources, 512 receivers: batched forward
                  solve + adjoint gradient of the receiver misfit
 
@@ -22,8 +24,11 @@ Prints one JSON line (rank 0).  Arms:
   --impl reference the CPU oracle (single-threaded fast marching, Algorithm 2,
                    plus the oracle adjoint for tomography) on the host cores,
                    on bounded samples of the same workload.
-Multi-GPU (torchrun): every rank solves its own replica (the single-grid path
-does not shard: replicas only, weak scaling); no collective touches the data.
+Multi-GPU (torchrun): the batch and the tomography sources shard by problem
+(rank r takes problems r, r + N, ...; strong scaling, no exchange during the
+solve; the tomography gradient is gathered on rank 0 and summed in source
+order).  A single grid does not shard: every rank solves its own replica
+(weak scaling); no collective touches its data.
 """
 from __future__ import annotations
 
@@ -51,6 +56,12 @@ L2_FLUSH_BYTES = 512 << 20
 # whenever the kernel changes)
 MEASURED_TRAFFIC = {"layered_2d": 28160000 + 682496, "checker_3d": 280830720 + 109687040}
 
+# FP64 thread instructions (DADD + DMUL + DFMA, ncu sass counters) per operator
+# evaluation of the persistent kernel, by dimension, from one-launch captures
+# summarised in profiles/ (refresh them whenever the kernel changes); None: not
+# measured for this build
+MEASURED_FP64_PER_EVAL = {2: None, 3: None}
+
 WORKLOADS = {
     "layered_2d": "2d_2301x751_layered_h4_1src",
     "const_2d": "2d_129x129_const_h1/128_centre_src",
@@ -68,6 +79,18 @@ def scaled_layered(scale: float):
     speed = synth.layered_section(nx, nz, 4.0, seed=2)
     src = np.array([nx // 2], dtype=np.int64)
     return synth.Problem(f"2d_{nx}x{nz}_layered", speed, 4.0, src, np.zeros(1), {})
+
+
+def single_problem(args):
+    """The single-grid workload, or a reduced case of it (--scale: fraction of
+    the extent per axis; layered 2D section and 3D checkerboard volume)."""
+    if args.scale != 1.0:
+        if args.workload == "layered_2d":
+            return scaled_layered(args.scale)
+        if args.workload == "checker_3d":
+            return synth.checker_3d(max(32, round(256 * args.scale)))
+        raise SystemExit("--scale applies to layered_2d and checker_3d")
+    return SINGLE[args.workload]()
 
 
 def useful_of(prob) -> int:
@@ -151,8 +174,7 @@ def oracle_units(args):
     oracle.build()
     wl = args.workload
     if wl in SINGLE:
-        prob = scaled_layered(args.scale) if (wl == "layered_2d" and args.scale != 1.0) \
-            else SINGLE[wl]()
+        prob = single_problem(args)
 
         def unit(p=prob):
             oracle.fmm(p.speed, p.h, p.sources, p.src_t)
@@ -410,6 +432,23 @@ def roofline(useful_per_launch: int, kern_ms: float, traffic, what: str):
             "peak_kind": f"{kind} copy bandwidth"}
 
 
+def roofline_fp64(C, evals_per_launch: int, kern_ms: float, ndim: int, what: str):
+    """The FP64 roofline of the persistent kernel: FP64 thread instructions per
+    launch (ncu instructions per evaluation x the live evaluation count) over the
+    kernel's event time, against the device's measured FP64 add rate."""
+    per_eval = MEASURED_FP64_PER_EVAL.get(ndim)
+    peak = C.eik.eik_fp64_rate() / 1e9
+    if per_eval is None:
+        return {"bound": "fp64", "achieved": None, "peak": peak, "unit": "G FP64 inst/s",
+                "frac": None, "kernel": what, "note": "FP64 instructions per evaluation not "
+                "measured for this build", "peak_kind": "measured (eik_fp64_rate, DADD chains)"}
+    achieved = per_eval * evals_per_launch / (kern_ms / 1e3) / 1e9
+    return {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "G FP64 inst/s",
+            "frac": achieved / peak, "kernel": what, "kernel_ms": kern_ms,
+            "fp64_inst_per_eval": per_eval, "evals_per_launch": int(evals_per_launch),
+            "peak_kind": "measured (eik_fp64_rate, DADD chains)"}
+
+
 def base_line(args, n, wl_name, value, total_ms, extra_cfg):
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n, "steps": args.steps,
@@ -456,8 +495,7 @@ def autotuned(args, C, problems, opts):
 
 def run_single(args, C, wl_name):
     torch, eik = C.torch, C.eik
-    prob = scaled_layered(args.scale) if (args.workload == "layered_2d" and args.scale != 1.0) \
-        else SINGLE[args.workload]()
+    prob = single_problem(args)
     if args.scale != 1.0:
         wl_name = prob.name + "_scaled"
     if args.upsample > 1:
@@ -531,6 +569,9 @@ def run_single(args, C, wl_name):
                                  "fim_kernel (Algorithm 3 rounds)",
                                  "topo_kernel (Algorithm 4 iterations)",
                                  "fsm_kernel (Algorithm 5 sweeps)"][args.schedule])
+    if args.schedule == 0:
+        line["roofline_fp64"] = roofline_fp64(C, st["evals"], statistics.mean(solve_ms),
+                                              prob.speed.ndim, line["roofline"]["kernel"])
     line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(prob.speed.nbytes + h_src.nbytes),
                    "d2h_bytes_per_step": int(prob.speed.nbytes)}
@@ -539,10 +580,28 @@ def run_single(args, C, wl_name):
     return line
 
 
+def _total_over_ranks(C, x: float) -> float:
+    """Sum of x over the ranks (bookkeeping of shard sizes; x itself at N = 1)."""
+    if C.dist is None:
+        return x
+    t = C.torch.tensor([x], device=C.dev, dtype=C.torch.float64)
+    C.dist.all_reduce(t)
+    return float(t.item())
+
+
 def run_batched(args, C, wl_name):
+    """The 88-problem 3D batch in one persistent launch (a plan replayed from a
+    captured CUDA graph).  With N ranks, rank r solves problems r, r + N, ...
+    (sharded by problem, no exchange: total work fixed, strong scaling)."""
+    from paper_2103_05694_gb300 import shard
     torch, eik = C.torch, C.eik
-    probs = synth.batched_3d()
-    useful = sum(useful_of(p) for p in probs)
+    n = args.gpus
+    n_all = 88
+    mine = shard.problem_shard(n_all, args.rank, n)
+    model = synth.smooth_model_3d_128()
+    probs = [synth.batched_3d_item(i, model) for i in mine]
+    useful_mine = sum(useful_of(p) for p in probs)
+    useful_all = _total_over_ranks(C, useful_mine)
     opts = make_opts(args)
     dev_speed = {}
     problems = []
@@ -556,7 +615,7 @@ def run_batched(args, C, wl_name):
     opts, tune = autotuned(args, C, problems, opts)
     st = eik.eik_solve_batched(problems, dict(opts, counters=1))
     torch.cuda.synchronize(C.dev)
-    assert st["good"] == useful, (st["good"], useful)
+    assert st["good"] == useful_mine, (st["good"], useful_mine)
     refs = [q["out"].clone() for q in problems]
 
     # kernel-only duration of the persistent launch (events inside the library)
@@ -580,35 +639,48 @@ def run_batched(args, C, wl_name):
     plan.status(C.stream)                  # raises unless the last replay succeeded
     for q, r in zip(problems, refs):
         assert torch.equal(q["out"], r)
-    n = args.gpus
-    value = job_value(useful * args.steps, n, total_ms)
+    value = useful_all * args.steps / (total_ms / 1e3)
 
-    # end to end: each step copies the models from pinned host memory into the
-    # plan's device buffers, replays the plan and copies every field back
-    h_speed = {key: torch.from_numpy(p.speed).pin_memory() for key, p in
-               ((id(p.speed), p) for p in probs)}
-    h_out = [torch.empty(p.speed.shape, dtype=torch.float64).pin_memory() for p in probs]
+    # end to end through the C ABI: one eik_solve_batched call per step on
+    # pinned host buffers (the call stages the models in, solves, and copies
+    # every field back)
+    h_speed = {}
+    for p in probs:
+        if id(p.speed) not in h_speed:
+            h_speed[id(p.speed)] = torch.from_numpy(p.speed).pin_memory()
+    host_problems = [{"speed": h_speed[id(p.speed)], "h": p.h,
+                      "sources": np.ascontiguousarray(p.sources, dtype=np.int64),
+                      "out": torch.empty(p.speed.shape, dtype=torch.float64).pin_memory()}
+                     for p in probs]
 
     def e2e_call():
-        for key, hs in h_speed.items():
-            dev_speed[key].copy_(hs, non_blocking=True)
-        graph.replay()
-        for q, ho in zip(problems, h_out):
-            ho.copy_(q["out"], non_blocking=True)
+        eik.eik_solve_batched(host_problems, opts, C.stream)
     e2e_ms = time_e2e(C, e2e_call, 3)
-    for ho, r in zip(h_out, refs):
-        assert np.array_equal(ho.numpy(), r.cpu().numpy())
-    h2d = sum(t.numel() * 8 for t in h_speed.values())
+    for hp, r in zip(host_problems, refs):
+        assert np.array_equal(hp["out"].numpy(), r.cpu().numpy())
+    h2d = sum(t.numel() * 8 for t in h_speed.values()) + sum(p.sources.nbytes for p in probs)
     d2h = sum(p.speed.nbytes for p in probs)
+    e2e_ms = C.max_over_ranks(e2e_ms)
 
     line = base_line(args, n, wl_name, value, total_ms,
-                     {"problems": len(probs), "cells": int(sum(p.ncells for p in probs)),
+                     {"problems": n_all, "problems_per_rank": len(probs),
+                      "cells": int(_total_over_ranks(C, sum(p.ncells for p in probs))),
                       "distinct_models": len(dev_speed), "captured_graph": True, "opts": opts,
                       "autotune": tune})
-    line["roofline"] = roofline(useful, statistics.mean(solve_ms), args.traffic_bytes,
+    if n > 1:
+        line["scaling"] = "strong"
+        line["config"]["parallelism"] = f"sharded by problem x{n} (rank r: problems r, r+{n}, ...)"
+    line["work_per_step"] = {k: st[k] for k in ("evals", "decreases", "good", "visits", "pushes",
+                                                "stale_pops", "rounds")}
+    line["work_per_step"].update(empty=st["evals"] - st["decreases"],
+                                 bad=st["decreases"] - st["good"])
+    line["roofline"] = roofline(useful_mine, statistics.mean(solve_ms), args.traffic_bytes,
                                 "persistent_kernel (all problems in one launch)")
-    line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
-                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    line["roofline_fp64"] = roofline_fp64(C, st["evals"], statistics.mean(solve_ms), 3,
+                                          line["roofline"]["kernel"])
+    line["e2e"] = {"value": useful_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                   "call": "eik_solve_batched with pinned host buffers (copies inside the call)"}
     line["gpu_launches"] = int(per_replay * args.steps)
     line["clocks"] = clocks
     plan.close()
@@ -616,87 +688,122 @@ def run_batched(args, C, wl_name):
 
 
 def run_tomography(args, C, wl_name):
+    """Batched forward + adjoint gradient of the receiver misfit.  At N = 1 the
+    step is the differentiable solve (eikonal + autograd); with N ranks, rank r
+    solves sources r, r + N, ... and its per-source gradients are gathered on
+    rank 0, which sums them in source order (bit-identical to N = 1)."""
+    from paper_2103_05694_gb300 import shard
     torch, eik = C.torch, C.eik
     cfg = synth.tomography_2d_1024()
     h = cfg["h"]
     sources = cfg["sources"][:args.sources] if args.sources > 0 else cfg["sources"]
     n_src = len(sources)
+    n = args.gpus
+    mine = shard.problem_shard(n_src, args.rank, n)
     s0 = torch.from_numpy(1.0 / cfg["start"]).to(C.dev)
-    srcs = [torch.tensor([int(i)], device=C.dev) for i in sources]
+    srcs = [torch.tensor([int(sources[i])], device=C.dev) for i in mine]
     rcv = torch.from_numpy(cfg["receivers"]).to(C.dev)
     with torch.no_grad():
         t_obs = eik.eikonal(torch.from_numpy(1.0 / cfg["true"]).to(C.dev), h, srcs) \
-            .reshape(n_src, -1)[:, rcv].contiguous()
-    useful = n_src * (s0.numel() - 1)
+            .reshape(len(srcs), -1)[:, rcv].contiguous()
+    useful_all = n_src * (s0.numel() - 1)
 
     def grad_of(s_dev):
         s = s_dev.detach().requires_grad_(True)
         t = eik.eikonal(s, h, srcs)
-        loss = 0.5 * ((t.reshape(n_src, -1)[:, rcv] - t_obs) ** 2).sum()
+        loss = 0.5 * ((t.reshape(len(srcs), -1)[:, rcv] - t_obs) ** 2).sum()
         loss.backward()
-        return s.grad, loss.detach()
+        return s.grad
 
-    g_ref, _ = grad_of(s0)
+    # sharded step: per-source gradients (no sum) -> gather -> ordered sum on rank 0
+    outs = torch.empty((len(srcs),) + tuple(s0.shape), dtype=torch.float64, device=C.dev)
+    gts = torch.zeros_like(outs)
+    grads = torch.empty_like(outs)
+    g_total = torch.empty_like(s0)
+
+    def grad_sharded(s_dev):
+        probs = [{"speed": s_dev, "h": h, "sources": src, "out": outs[i]} for i, src in enumerate(srcs)]
+        eik.eik_solve_batched(probs, {"sched_flags": eik.SLOWNESS_INPUT})
+        gts.reshape(len(srcs), -1)[:, rcv] = outs.reshape(len(srcs), -1)[:, rcv] - t_obs
+        eik.eik_adjoint(probs, [gts[i] for i in range(len(srcs))], [grads[i] for i in range(len(srcs))],
+                        {"sched_flags": eik.SLOWNESS_INPUT})
+        allg = shard.gather_items(grads, n_src, args.rank, n, C.dist, dst=0)
+        if allg is not None:
+            eik.eik_sum_ordered([allg[i] for i in range(n_src)], g_total)
+        return g_total
+
+    step = grad_of if n == 1 else grad_sharded
+    g_ref = step(s0).clone()
     for _ in range(args.warmup):
-        grad_of(s0)
+        step(s0)
         C.flush.zero_()
     torch.cuda.synchronize(C.dev)
-    total_ms, _, launches, clocks = C.timed(args.steps, lambda: grad_of(s0))
-    g_last, _ = grad_of(s0)
-    assert torch.equal(g_last, g_ref)       # the gradient is deterministic
-    n = args.gpus
-    value = job_value(useful * args.steps, n, total_ms)
+    total_ms, _, launches, clocks = C.timed(args.steps, lambda: step(s0))
+    g_last = step(s0)
+    if args.rank == 0:
+        assert torch.equal(g_last, g_ref)       # the gradient is deterministic
+    value = useful_all * args.steps / (total_ms / 1e3)
 
-    # the same gradient from per-source solves and adjoints (one problem per call)
-    speed = torch.reciprocal(s0)
-    outs = [torch.empty_like(s0) for _ in srcs]
-    grads = [torch.empty_like(s0) for _ in srcs]
+    per_source_ms = None
+    if n == 1:
+        # the same gradient from per-source solves and adjoints (one problem per call)
+        speed = torch.reciprocal(s0)
+        po = [torch.empty_like(s0) for _ in srcs]
+        pg = [torch.empty_like(s0) for _ in srcs]
 
-    def per_source():
-        total = torch.zeros_like(s0)
-        for i, src in enumerate(srcs):
-            eik.solve(speed, h, src, out=outs[i])
-            gt = torch.zeros_like(s0)
-            gt.reshape(-1)[rcv] = outs[i].reshape(-1)[rcv] - t_obs[i]
-            eik.eik_adjoint([{"speed": speed, "h": h, "sources": src, "out": outs[i]}], [gt],
-                            [grads[i]])
-            total += grads[i]
-        return total
-    g_ps = per_source()
-    torch.cuda.synchronize(C.dev)
-    assert torch.allclose(g_ps, g_ref, rtol=1e-12, atol=1e-12 * float(g_ref.abs().max()))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = max(1, min(args.steps, 3))
-    e0.record(C.stream)
-    for _ in range(reps):
-        per_source()
-    e1.record(C.stream)
-    torch.cuda.synchronize(C.dev)
-    per_source_ms = e0.elapsed_time(e1) / reps
+        def per_source():
+            total = torch.zeros_like(s0)
+            for i, src in enumerate(srcs):
+                eik.solve(speed, h, src, out=po[i])
+                gt = torch.zeros_like(s0)
+                gt.reshape(-1)[rcv] = po[i].reshape(-1)[rcv] - t_obs[i]
+                eik.eik_adjoint([{"speed": speed, "h": h, "sources": src, "out": po[i]}], [gt],
+                                [pg[i]])
+                total += pg[i]
+            return total
+        g_ps = per_source()
+        torch.cuda.synchronize(C.dev)
+        assert torch.allclose(g_ps, g_ref, rtol=1e-12, atol=1e-12 * float(g_ref.abs().max()))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(args.steps, 3))
+        e0.record(C.stream)
+        for _ in range(reps):
+            per_source()
+        e1.record(C.stream)
+        torch.cuda.synchronize(C.dev)
+        per_source_ms = e0.elapsed_time(e1) / reps
 
     # kernel-only duration of the batched forward launch
-    probs = [{"speed": speed, "h": h, "sources": src, "out": outs[i]} for i, src in enumerate(srcs)]
-    solve_ms = [eik.eik_solve_batched(probs)["solve_ms"] for _ in range(3)]
+    probs = [{"speed": s0, "h": h, "sources": src, "out": outs[i]} for i, src in enumerate(srcs)]
+    solve_ms = [eik.eik_solve_batched(probs, {"sched_flags": eik.SLOWNESS_INPUT})["solve_ms"]
+                for _ in range(3)]
 
     # end to end: slowness from pinned host memory, gradient back to the host
     h_s = s0.cpu().pin_memory()
     h_g = torch.empty_like(h_s).pin_memory()
 
     def e2e_call():
-        g, _ = grad_of(h_s.to(C.dev, non_blocking=True))
-        h_g.copy_(g, non_blocking=True)
-    e2e_ms = time_e2e(C, e2e_call, max(3, min(args.steps, 10)))
-    assert torch.equal(h_g, g_ref.cpu())
+        g = step(h_s.to(C.dev, non_blocking=True))
+        if args.rank == 0:
+            h_g.copy_(g, non_blocking=True)
+    e2e_ms = C.max_over_ranks(time_e2e(C, e2e_call, max(3, min(args.steps, 10))))
+    if args.rank == 0:
+        assert torch.equal(h_g, g_ref.cpu())
 
     line = base_line(args, n, wl_name, value, total_ms,
                      {"cells": int(s0.numel()), "h": h, "sources": n_src,
                       "receivers": int(rcv.numel()), "step": "batched forward + adjoint + misfit"})
+    if n > 1:
+        line["scaling"] = "strong"
+        line["config"]["parallelism"] = (f"sharded by source x{n}; per-source gradients gathered "
+                                         "on rank 0 and summed in source order")
     line["tomography"] = {"batched_step_ms": total_ms / args.steps,
                           "per_source_step_ms": per_source_ms,
-                          "speedup_vs_per_source": per_source_ms / (total_ms / args.steps)}
-    line["roofline"] = roofline(useful, statistics.mean(solve_ms), args.traffic_bytes,
-                                "persistent_kernel (32-source forward)")
-    line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
+                          "speedup_vs_per_source": (per_source_ms / (total_ms / args.steps)
+                                                    if per_source_ms else None)}
+    line["roofline"] = roofline(len(srcs) * (s0.numel() - 1), statistics.mean(solve_ms),
+                                args.traffic_bytes, "persistent_kernel (batched forward)")
+    line["e2e"] = {"value": useful_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(h_s.numel() * 8),
                    "d2h_bytes_per_step": int(h_g.numel() * 8)}
     line["gpu_launches"] = int(launches)
@@ -710,9 +817,9 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="layered_2d", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="batched_3d", choices=sorted(WORKLOADS))
     ap.add_argument("--scale", type=float, default=1.0,
-                    help="layered_2d only: fraction of the extent per axis (profiling)")
+                    help="layered_2d and checker_3d: fraction of the extent per axis (profiling)")
     ap.add_argument("--upsample", type=int, default=1,
                     help="2D single grids: nearest-neighbour upsampling by this factor per axis, "
                          "spacing h / factor (Table 3's input scale)")
@@ -733,8 +840,9 @@ def main():
                          "then Newton (0: d-bar)")
     ap.add_argument("--track-changes", action="store_true",
                     help="with --update 1-3: conservative work tracking (activate on any change)")
-    ap.add_argument("--autotune", action="store_true",
-                    help="pick the scheduling options with eik_autotune on the workload first")
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=None,
+                    help="pick the scheduling options with eik_autotune on the workload first "
+                         "(outside the timed region); default: on for batched_3d")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -742,6 +850,8 @@ def main():
                     help="ncu dram bytes per launch of the solve kernel, if measured")
     args = ap.parse_args()
     args.rank = int(os.environ.get("RANK", "0"))
+    if args.autotune is None:
+        args.autotune = args.workload == "batched_3d"
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
         args.gpus = world

@@ -70,9 +70,12 @@ typedef enum {
  * batch has:
  *   2D, fewer than 8 sources in the batch: 16x16 tiles, k_delta 16, window 16,
  *     band 16, 1 CTA per SM (latency-bound: one front);
- *   2D, 8 or more sources: 16x8 tiles, k_delta 2, window 16, band 16, 4 CTAs of
+ *   2D, 8 or more sources: 16x8 tiles, k_delta 2, window 16, band 16, 8 CTAs of
  *     128 threads per SM;
- *   3D: 8x4x4 tiles, k_delta 1, window 16, band 8, 4 CTAs of 128 threads per SM.
+ *   3D: 8x4x4 tiles, k_delta 1, window 16, band 8, 8 CTAs of 128 threads per SM.
+ * (The per-CTA work is latency-bound, so the kernel is compiled for as many
+ * resident CTAs as registers allow: 2 per SM for 256-cell tiles, 8 for 128-cell
+ * tiles, 16 for 64-cell tiles.)
  * With arith = 2 the first shape (16x16, 8x8x4) and k_delta 16 (2D) / 2 (3D). */
 typedef struct {
     double delta;          /* bucket width in time units; <= 0: auto (k_delta * mean h/v) */
@@ -119,9 +122,9 @@ typedef struct {
                               rounds, flags}; NULL: no trace */
     int64_t trace_cap;
     int tile;              /* tile shape, cells x*y(*z), one CTA thread per cell; 0: default
-                              (above).  2D: 1 = 16x16, 2 = 32x8, 3 = 32x4, 4 = 16x8;
-                              3D: 1 = 8x8x4, 2 = 16x4x4, 3 = 32x4x2, 4 = 8x4x4.
-                              Shapes 2-4 need arith 0/1 (EIK_EINVAL otherwise). */
+                              (above).  2D: 1 = 16x16, 2 = 32x8, 3 = 32x4, 4 = 16x8,
+                              5 = 16x4; 3D: 1 = 8x8x4, 2 = 16x4x4, 3 = 32x4x2, 4 = 8x4x4,
+                              5 = 4x4x4.  Shapes 2-5 need arith 0/1 (EIK_EINVAL otherwise). */
     int update;            /* the local update: 0 = d-bar, exactly monotone (section "Achieving
                               Exact Monotonicity"), the default; for the ablation of the
                               Mitigation Strategies section, 2D only: 1 = Algorithm 1 with the
@@ -214,6 +217,15 @@ eik_status eik_solve_batched(const eik_problem *probs, int nprob, const eik_opts
  * Allocates and frees a small device buffer; synchronises `stream`. */
 eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches, void *stream);
 
+/* Instrument for the FP64 roofline (the paper has no counterpart): the
+ * current device's throughput of FP64 additions, in thread instructions per
+ * second (*inst_per_s), timed with CUDA events over one launch of eight
+ * independent __dadd_rn chains per thread, `iters` steps each, on 8 CTAs of
+ * 256 threads per SM (after one shorter warm-up launch).  GB300's FP64 unit
+ * runs DADD, DMUL and DFMA at one rate.  Allocates and frees a small device
+ * buffer; synchronises `stream`.  EIK_EINVAL for iters <= 0. */
+eik_status eik_fp64_rate(int64_t iters, double *inst_per_s, void *stream);
+
 /* The single-grid solve of eik_solve without allocating any memory.  (The
  * paper has no counterpart: this serves callers that cannot allocate device
  * memory, e.g. code whose device memory belongs to an arena allocator that
@@ -277,6 +289,35 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
 eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
                        double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,
                        void *stream);
+
+/* Slab decomposition of one grid (the domain decomposition that the paper
+ * leaves to future work, Introduction).  Solves the same problem as eik_solve,
+ * with the same result bit for bit: the outermost axis (z in 3D, y in 2D) is
+ * split into nslabs slabs of near-equal thickness; each slab, extended by one
+ * ghost row on each side it shares with a neighbour, is one problem of a batch
+ * (one persistent launch for all slabs).  A ghost row holds the neighbour's
+ * values of those cells from the previous epoch as fixed sources (cells the
+ * neighbour has not reached yet stay free).  Between epochs the rows next to
+ * each slab boundary are copied, device to device, into an exchange buffer;
+ * the epochs repeat until no exchanged value changes (a global AND over the
+ * boundaries).  Ghost values only decrease from epoch to epoch, so the loop
+ * ends, and then every cell satisfies the update with its neighbours' final
+ * values: the union is the unique fixed point (Theorem 1).  Every epoch
+ * solves the slabs from +inf; all slabs run on the calling device (with one
+ * slab per GPU, the exchange is a peer copy of one row into the neighbour's
+ * memory).
+ *   speed, out_t: device pointers; src_idx / src_t: host or device; other
+ *   arguments as eik_solve.  1 <= nslabs <= outermost extent (EIK_EINVAL
+ *   otherwise); opts->update, schedule, test_stall and sched_flags bit 5 must
+ *   be 0.  *epochs (optional) receives the number of epochs; stats accumulate
+ *   over them (good: reached non-source cells, with opts->counters).  More than
+ *   64 + 8 nslabs epochs give EIK_ETIMEOUT.  Workspace: one field per slab (the
+ *   grid plus 2 (nslabs - 1) rows) and 2 (nslabs - 1) exchanged rows.
+ *   Synchronises `stream`. */
+eik_status eik_solve_slabs(const double *speed, double h, int ndim, const int64_t *dims,
+                           const int64_t *src_idx, const double *src_t, int64_t nsrc,
+                           double *out_t, int nslabs, const eik_opts *opts, eik_stats *stats,
+                           int *epochs, void *stream);
 
 /* Fixed-order sum of k arrays of n doubles: dst[i] = (((+0 + src[0][i]) +
  * src[1][i]) + ...) + src[k-1][i], each addition rounded to nearest in that

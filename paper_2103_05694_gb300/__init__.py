@@ -38,10 +38,10 @@ class EikOpts(ctypes.Structure):
                 ("tile", ctypes.c_int), ("update", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("reserved", ctypes.c_int)]
 
-# opts["tile"] = k (1..4) selects TILE_SHAPES[ndim][k - 1]; 0 is automatic (16x16 for
+# opts["tile"] = k (1..5) selects TILE_SHAPES[ndim][k - 1]; 0 is automatic (16x16 for
 # one 2D front, 16x8 for 2D batches of 8 or more sources, 8x4x4 in 3D)
-TILE_SHAPES = {2: [(16, 16), (32, 8), (32, 4), (16, 8)],
-               3: [(8, 8, 4), (16, 4, 4), (32, 4, 2), (8, 4, 4)]}
+TILE_SHAPES = {2: [(16, 16), (32, 8), (32, 4), (16, 8), (16, 4)],
+               3: [(8, 8, 4), (16, 4, 4), (32, 4, 2), (8, 4, 4), (4, 4, 4)]}
 
 
 TUNED_FIELDS = ("delta", "k_delta", "capacity", "ctas_per_sm", "window", "band", "arith", "tile")
@@ -144,6 +144,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     L.eik_residual.argtypes = [ctypes.POINTER(EikProblem), ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double), vp]
     L.eik_residual.restype = ctypes.c_int
+    L.eik_fp64_rate.argtypes = [i64, ctypes.POINTER(ctypes.c_double), vp]
+    L.eik_fp64_rate.restype = ctypes.c_int
+    L.eik_solve_slabs.argtypes = [vp, ctypes.c_double, ctypes.c_int, vp, vp, vp, i64, vp,
+                                  ctypes.c_int, ctypes.POINTER(EikOpts), ctypes.POINTER(EikStats),
+                                  ctypes.POINTER(ctypes.c_int), vp]
+    L.eik_solve_slabs.restype = ctypes.c_int
     L.eik_sum_ordered.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, i64, vp]
     L.eik_sum_ordered.restype = ctypes.c_int
     _lib = L
@@ -154,7 +160,7 @@ EXPORTED = ["eik_solve", "eik_solve_batched", "eik_release", "eik_status_str", "
             "eik_abi_version", "eik_selftest", "eik_solve_noalloc", "eik_plan_create",
             "eik_plan_enqueue", "eik_plan_status", "eik_plan_destroy", "eik_adjoint",
             "eik_kernel_launches", "eik_autotune", "eik_eval_update", "eik_residual",
-            "eik_sum_ordered"]
+            "eik_sum_ordered", "eik_solve_slabs", "eik_fp64_rate"]
 
 SELFTEST_CHECKS = ["sub", "sq", "add", "G2", "G3", "dbar2", "dbar3", "group2x8", "group3x8",
                    "group2x4", "dbar2_fp64", "dbar3_fp64"]
@@ -501,6 +507,56 @@ def eik_residual(problem: dict, form: int = 0, stream=None) -> tuple[int, float]
     if rc != EIK_OK:
         raise EikError(rc, eik_last_error())
     return int(bad.value), float(rel.value)
+
+
+def solve_slabs(speed, h: float, sources, nslabs: int, src_t=None, out=None,
+                opts: dict | None = None, stream=None) -> SolveResult:
+    """The grid split into ``nslabs`` slabs along its outermost axis, solved by
+    epochs with halo exchange (eik_solve_slabs; same bits as ``solve``).  torch
+    CUDA float64 tensors; stats["epochs"] is the number of epochs."""
+    import torch
+    if speed.dtype != torch.float64 or not speed.is_contiguous() or not speed.is_cuda:
+        raise ValueError("speed must be a contiguous float64 CUDA tensor")
+    src = sources if isinstance(sources, torch.Tensor) else torch.as_tensor(
+        np.asarray(sources, dtype=np.int64))
+    src = src.to(device=speed.device, dtype=torch.int64).contiguous().reshape(-1)
+    st_t = None
+    if src_t is not None:
+        st_t = torch.as_tensor(src_t, dtype=torch.float64).to(speed.device).contiguous().reshape(-1)
+    if out is None:
+        out = torch.empty_like(speed)
+    stats = eik_solve_slabs(_ptr(speed), h, speed.ndim, speed.shape, _ptr(src), _ptr(st_t),
+                            int(src.numel()), _ptr(out), nslabs, opts, _stream_handle(stream))
+    return SolveResult(out, stats)
+
+
+def eik_solve_slabs(speed_ptr: int, h: float, ndim: int, dims, src_ptr: int | None,
+                    src_t_ptr: int | None, nsrc: int, out_ptr: int, nslabs: int,
+                    opts: dict | None = None, stream: int | None = None) -> dict:
+    """Raw call of the slab-decomposed solve (device speed and out); the stats
+    dict adds "epochs"."""
+    L = load_library()
+    d = (ctypes.c_int64 * ndim)(*[int(x) for x in dims])
+    st = EikStats()
+    ep = ctypes.c_int(0)
+    o = _make_opts(opts)
+    rc = L.eik_solve_slabs(speed_ptr, float(h), int(ndim), d, src_ptr, src_t_ptr, int(nsrc),
+                           out_ptr, int(nslabs), ctypes.byref(o) if o is not None else None,
+                           ctypes.byref(st), ctypes.byref(ep), stream)
+    if rc != EIK_OK:
+        raise EikError(rc, eik_last_error())
+    stats = st.as_dict()
+    stats["epochs"] = int(ep.value)
+    return stats
+
+
+def eik_fp64_rate(iters: int = 1 << 16, stream=None) -> float:
+    """Measured FP64 add throughput of the current device (thread instructions/s)."""
+    r = ctypes.c_double(0.0)
+    rc = load_library().eik_fp64_rate(int(iters), ctypes.byref(r), _stream_handle(stream))
+    if rc != EIK_OK:
+        raise EikError(rc, "eik_fp64_rate")
+    return float(r.value)
 
 
 def eik_sum_ordered(srcs: list, out, stream=None):

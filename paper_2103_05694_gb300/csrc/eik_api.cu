@@ -43,7 +43,7 @@ constexpr bool kAdjTilesDefault = true;
 constexpr double kDefaultKDelta[2] = {16.0, 2.0};
 constexpr int kDefaultWindow[2] = {16, 16};
 constexpr double kDefaultBand[2] = {16.0, 8.0};
-constexpr int kDefaultCtasPerSm[2] = {1, 2};
+constexpr int kDefaultCtasPerSm[2] = {1, 2};   // per 256 cells of tile (single 2D front)
 constexpr int kMaxRetries = 4;
 // eik_opts.sched_flags bits of the tomography interface
 constexpr int kFlagSlowness = 1 << 6;     // speed arrays hold slowness s; v = fl(1/s) is used
@@ -88,6 +88,8 @@ struct Workspace {
   DevBuf<Ctl> ctl;
   DevBuf<unsigned long long> count;
   DevBuf<const double *> sum_ptr;   // eik_sum_ordered's pointer table
+  DevBuf<double> slab_t;       // eik_solve_slabs: each slab's field (own rows + ghost rows)
+  DevBuf<double> slab_x;       // eik_solve_slabs: exchanged boundary rows
   Ctl *ctl_host = nullptr;     // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   uint64_t cap = 0;            // entries per slot
@@ -96,7 +98,8 @@ struct Workspace {
     r.release(); t_stage.release(); v_stage.release(); state.release(); tile_src.release();
     pend.release();
     slots.release(); seq.release(); src_idx.release(); src_t.release(); seeds.release();
-    probs.release(); ctl.release(); count.release(); sum_ptr.release();
+    probs.release(); ctl.release(); count.release(); sum_ptr.release(); slab_t.release();
+    slab_x.release();
     if (ctl_host) cudaFreeHost(ctl_host);
     ctl_host = nullptr;
     if (ev0) cudaEventDestroy(ev0);
@@ -387,9 +390,10 @@ int lane_group_cells(const eik_opts *opts, int64_t tile_cells, int64_t total_til
 // 1024^2 tomography forward: 75 ms against 93 ms with one); a single front
 // runs faster with one.
 int default_ctas_per_sm(int di, int64_t tile_cells, int64_t total_sources) {
-  int per256 = kDefaultCtasPerSm[di];
-  if (di == 0 && total_sources >= 8) per256 = 2;
-  return (int)std::max<int64_t>(1, per256 * 256 / tile_cells);
+  // one 2D front is latency-bound on few tiles: one CTA per SM; otherwise as
+  // many CTAs as the register budget of the tile size allows
+  if (di == 0 && total_sources < 8) return (int)std::max<int64_t>(1, kDefaultCtasPerSm[0] * 256 / tile_cells);
+  return eik::resident_ctas((int)tile_cells);
 }
 
 // Select the current device's workspaces for the call in progress.
@@ -1097,6 +1101,149 @@ eik_status eik_sum_ordered(const double *const *src, int k, double *dst, int64_t
   }
   CK(eik::launch_sum_ordered(ws().sum_ptr.p, k, dst, n, s), "sum launch");
   CK(cudaStreamSynchronize(s), "sum");
+  return EIK_OK;
+}
+
+// Slab decomposition of one grid (the domain decomposition the paper leaves
+// to future work, Introduction): the outermost axis is split into nslabs
+// slabs, each solved as one problem of a batch with a ghost row on each side
+// it shares with a neighbour.  The ghost rows hold the neighbour's boundary
+// values as fixed sources (finite ones); between epochs the boundary rows are
+// copied into an exchange buffer on the device and the epochs repeat until
+// no exchanged value changes.  Ghost values only decrease from epoch to epoch
+// (the solve is monotone in its boundary values), so the loop ends; at the
+// end every cell of every slab satisfies the update with its neighbours'
+// final values across the slab boundaries, i.e. the union is the fixed point
+// of the whole grid (unique, Theorem 1), bit for bit.  One device runs all
+// slabs here; with one slab per GPU the exchange is a peer copy of one row
+// into the neighbour's memory.
+eik_status eik_solve_slabs(const double *speed, double h, int ndim, const int64_t *dims,
+                           const int64_t *src_idx, const double *src_t, int64_t nsrc,
+                           double *out_t, int nslabs, const eik_opts *opts, eik_stats *stats,
+                           int *epochs, void *stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (epochs) *epochs = 0;
+  HostProblem hp;
+  eik_status st = check_problem(speed, h, ndim, dims, src_idx, src_t, nsrc, out_t, hp, s);
+  if (st != EIK_OK) return st;
+  if (!hp.speed_dev || !hp.out_dev) { set_err("eik_solve_slabs takes device speed and out_t"); return EIK_EINVAL; }
+  if (opts && (opts->update != 0 || opts->schedule != 0 || (opts->sched_flags & 32) || opts->test_stall)) {
+    set_err("eik_solve_slabs runs the exact update (opts.update 0) on the asynchronous schedule");
+    return EIK_EINVAL;
+  }
+  const int64_t L = hp.dims[3 - ndim];                  // outermost extent
+  const int64_t plane = hp.n / L;
+  if (nslabs < 1 || nslabs > L) { set_err("nslabs must be in 1..%lld", (long long)L); return EIK_EINVAL; }
+  st = ensure_device();
+  if (st != EIK_OK) return st;
+  const int K = nslabs;
+  std::vector<int64_t> lo(K + 1), glo(K), ghi(K), toff(K);
+  for (int k = 0; k <= K; ++k) lo[k] = (int64_t)k * L / K;
+  int64_t tcells = 0;
+  for (int k = 0; k < K; ++k) {
+    glo[k] = lo[k] > 0 ? lo[k] - 1 : 0;
+    ghi[k] = lo[k + 1] < L ? lo[k + 1] + 1 : L;
+    toff[k] = tcells;
+    tcells += (ghi[k] - glo[k]) * plane;
+  }
+  // exchange buffer: for boundary b (between slabs b and b+1) two rows: slab b's
+  // last own row (slab b+1's ghost) and slab b+1's first own row (slab b's ghost)
+  const int64_t nx_rows = 2 * (int64_t)(K - 1);
+  CK(ws().slab_t.ensure((size_t)std::max<int64_t>(tcells, 1)), "slabs: fields");
+  CK(ws().slab_x.ensure((size_t)std::max<int64_t>(nx_rows * plane, 1)), "slabs: exchange");
+  std::vector<double> xprev((size_t)(nx_rows * plane), INFINITY), xcur((size_t)(nx_rows * plane));
+  const int max_epochs = 64 + 8 * K;
+  eik_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  bool done = false;
+  int e = 0;
+  for (; e < max_epochs && !done; ++e) {
+    std::vector<HostProblem> hps((size_t)K);
+    for (int k = 0; k < K; ++k) {
+      HostProblem &q = hps[(size_t)k];
+      q.speed = speed + glo[k] * plane;
+      q.speed_dev = true;
+      q.h = hp.h;
+      q.ndim = ndim;
+      q.dims[0] = q.dims[1] = q.dims[2] = 1;
+      for (int a = 0; a < ndim; ++a) q.dims[3 - ndim + a] = hp.dims[3 - ndim + a];
+      q.dims[3 - ndim] = ghi[k] - glo[k];
+      q.n = q.dims[0] * q.dims[1] * q.dims[2];
+      q.out = ws().slab_t.p + toff[k];
+      q.out_dev = true;
+      // ghost sources first (they precede or follow the own rows, so the list
+      // stays sorted with the own sources in between)
+      if (k > 0) {                                      // row glo[k] = slab k-1's last own row
+        const double *g = xprev.data() + (size_t)(2 * (k - 1)) * plane;
+        for (int64_t j = 0; j < plane; ++j)
+          if (std::isfinite(g[j])) { q.src.push_back(j); q.t0.push_back(g[j]); }
+      }
+      for (size_t i = 0; i < hp.src.size(); ++i) {
+        const int64_t row = hp.src[i] / plane;
+        if (row >= lo[k] && row < lo[k + 1]) {
+          q.src.push_back(hp.src[i] - glo[k] * plane);
+          q.t0.push_back(hp.t0[i]);
+        }
+      }
+      if (k + 1 < K) {                                  // row ghi[k]-1 = slab k+1's first own row
+        const double *g = xprev.data() + (size_t)(2 * k + 1) * plane;
+        const int64_t base = (ghi[k] - 1 - glo[k]) * plane;
+        for (int64_t j = 0; j < plane; ++j)
+          if (std::isfinite(g[j])) { q.src.push_back(base + j); q.t0.push_back(g[j]); }
+      }
+    }
+    eik_stats es;
+    st = run(hps, opts, &es, s);
+    if (st != EIK_OK) return st;
+    acc.evals += es.evals; acc.decreases += es.decreases; acc.visits += es.visits;
+    acc.pushes += es.pushes; acc.stale_pops += es.stale_pops; acc.rounds += es.rounds;
+    acc.retries += es.retries; acc.max_queue = std::max(acc.max_queue, es.max_queue);
+    acc.visit_ns += es.visit_ns; acc.idle_ns += es.idle_ns; acc.ctas = es.ctas;
+    acc.solve_ms += es.solve_ms;
+    // exchange: each boundary row into the buffer slot of the slab that reads it
+    for (int b = 0; b + 1 < K; ++b) {
+      const double *last_b = ws().slab_t.p + toff[b] + (lo[b + 1] - 1 - glo[b]) * plane;
+      const double *first_b1 = ws().slab_t.p + toff[b + 1] + (lo[b + 1] - glo[b + 1]) * plane;
+      CK(cudaMemcpyAsync(ws().slab_x.p + (size_t)(2 * b) * plane, last_b, (size_t)plane * sizeof(double),
+                         cudaMemcpyDeviceToDevice, s), "slabs: exchange");
+      CK(cudaMemcpyAsync(ws().slab_x.p + (size_t)(2 * b + 1) * plane, first_b1,
+                         (size_t)plane * sizeof(double), cudaMemcpyDeviceToDevice, s), "slabs: exchange");
+    }
+    if (nx_rows > 0)
+      CK(cudaMemcpyAsync(xcur.data(), ws().slab_x.p, (size_t)(nx_rows * plane) * sizeof(double),
+                         cudaMemcpyDeviceToHost, s), "slabs: read exchange");
+    CK(cudaStreamSynchronize(s), "slabs: epoch");
+    // global AND: done when no exchanged value changed
+    done = std::memcmp(xcur.data(), xprev.data(), xcur.size() * sizeof(double)) == 0;
+    xprev.swap(xcur);
+  }
+  if (!done) {
+    set_err("eik_solve_slabs: exchanged values still changing after %d epochs", max_epochs);
+    return EIK_ETIMEOUT;
+  }
+  for (int k = 0; k < K; ++k) {
+    CK(cudaMemcpyAsync(out_t + lo[k] * plane, ws().slab_t.p + toff[k] + (lo[k] - glo[k]) * plane,
+                       (size_t)((lo[k + 1] - lo[k]) * plane) * sizeof(double), cudaMemcpyDeviceToDevice, s),
+       "slabs: assemble");
+  }
+  if (opts && opts->counters) {
+    CK(cudaMemsetAsync(ws().count.p, 0, sizeof(unsigned long long), s), "slabs: count");
+    Prob P;
+    std::memset(&P, 0, sizeof(P));
+    P.t = out_t;
+    P.nx = hp.dims[2];
+    P.ny = hp.dims[1];
+    P.nz = hp.dims[0];
+    CK(eik::launch_count_finite(&P, 1, ws().count.p, s), "slabs: count");
+    unsigned long long finite = 0;
+    CK(cudaMemcpyAsync(&finite, ws().count.p, sizeof(finite), cudaMemcpyDeviceToHost, s), "slabs: count");
+    CK(cudaStreamSynchronize(s), "slabs: count");
+    acc.good = (int64_t)finite - (int64_t)hp.src.size();
+  }
+  CK(cudaStreamSynchronize(s), "slabs");
+  if (stats) *stats = acc;
+  if (epochs) *epochs = e;
   return EIK_OK;
 }
 

@@ -557,7 +557,7 @@ __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned lo
     if (above) {
 #pragma unroll 1
       for (int i = 0; i < 4; ++i) {
-        if (path) path[1] += 1u;
+        if (path) atomicAdd(&path[1], 1u);
         if (tau - 1ull <= s0) return tau;                  // G(a_0) = 0 < c
         if (G<D>(tau - 1ull, a) < cb) return tau;
         --tau;
@@ -565,13 +565,13 @@ __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned lo
     } else {
 #pragma unroll 1
       for (int i = 0; i < 4; ++i) {
-        if (path) path[1] += 1u;
+        if (path) atomicAdd(&path[1], 1u);
         ++tau;
         if (G<D>(tau, a) >= cb) return tau;
       }
     }
     if (pass == 1) break;
-    if (path) path[0] += 1u;
+    if (path) atomicAdd(&path[0], 1u);
     float msum;
     const unsigned long long gs = G_slope<D>(tau, a, msum);
     if (!(msum > 0.0f) || gs >= kInf) break;
@@ -600,7 +600,7 @@ __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned lo
       hi = xf::umin(lo + step, kInf);
     }
   }
-  if (path) path[2] += 1u;
+  if (path) atomicAdd(&path[2], 1u);
 #pragma unroll 1
   while (hi - lo > 1ull) {
     const unsigned long long mid = lo + (hi - lo) / 2ull;
@@ -617,7 +617,7 @@ __device__ __forceinline__ bool relax(unsigned long long best, const unsigned lo
 #pragma unroll
   for (int k = 1; k < D; ++k) amin = xf::umin(amin, a[k]);
   if (amin >= kInf || best <= amin) return false;
-  if (path) path[3] += 1u;
+  if (path) atomicAdd(&path[3], 1u);
   // d-bar directly (no separate G(prev(best)) test): a decrease iff d-bar < best
   out = dbar<D>(a, cb, path);
   return out < best;

@@ -125,7 +125,22 @@ constexpr int kArithFp64 = 1, kArithInt = 2;   // d-bar on the FP64 unit / on th
 // default; the others are alternatives (opts.tile) for the autotuner.
 constexpr int kTX2 = 16, kTY2 = 16;                // 2D default
 constexpr int kTX3 = 8, kTY3 = 8, kTZ3 = 4;        // 3D default
-constexpr int kNumTileShapes = 4;
+constexpr int kNumTileShapes = 5;
+// Resident CTAs per SM that the register budget of the persistent kernel
+// allows, by tile size (launch bounds; the solve is latency-bound per CTA, so
+// small tiles run many CTAs per SM).
+#ifndef EIK_MIN_CTAS_256
+#define EIK_MIN_CTAS_256 2
+#endif
+#ifndef EIK_MIN_CTAS_128
+#define EIK_MIN_CTAS_128 8
+#endif
+#ifndef EIK_MIN_CTAS_64
+#define EIK_MIN_CTAS_64 16
+#endif
+constexpr int resident_ctas(int tile_cells) {
+  return tile_cells >= 256 ? EIK_MIN_CTAS_256 : tile_cells >= 128 ? EIK_MIN_CTAS_128 : EIK_MIN_CTAS_64;
+}
 struct TileShape {
   int tx, ty, tz;
 };
@@ -135,6 +150,7 @@ __host__ __device__ inline TileShape tile_shape_of(int ndim, int shape) {
       case 1: return TileShape{16, 4, 4};
       case 2: return TileShape{32, 4, 2};
       case 3: return TileShape{8, 4, 4};
+      case 4: return TileShape{4, 4, 4};
       default: return TileShape{kTX3, kTY3, kTZ3};
     }
   }
@@ -142,6 +158,7 @@ __host__ __device__ inline TileShape tile_shape_of(int ndim, int shape) {
     case 1: return TileShape{32, 8, 1};
     case 2: return TileShape{32, 4, 1};
     case 3: return TileShape{16, 8, 1};
+    case 4: return TileShape{16, 4, 1};
     default: return TileShape{kTX2, kTY2, 1};
   }
 }

@@ -164,8 +164,62 @@ __global__ void selftest_kernel(int64_t n, unsigned long long seed, unsigned lon
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&bad[15], static_cast<unsigned long long>(n));
 }
 
+// FP64 add throughput: eight independent DADD chains per thread (enough to
+// cover the pipe's latency with the resident warps), `iters` steps each.  The
+// sum is written so the chains are not removed.
+__global__ void __launch_bounds__(256) fp64_rate_kernel(double *out, int64_t iters, double step) {
+  double a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = static_cast<double>(threadIdx.x * 8 + k);
+#pragma unroll 1
+  for (int64_t i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = __dadd_rn(a[k], step);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sum = __dadd_rn(sum, a[k]);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 }  // namespace
 }  // namespace eik
+
+// Instrument (the paper has no counterpart): FP64 add throughput of the
+// current device, for the FP64 roofline of the solver.
+extern "C" eik_status eik_fp64_rate(int64_t iters, double *inst_per_s, void *stream) {
+  if (iters <= 0 || !inst_per_s) return EIK_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = 8 * sms, block = 256;
+  double *d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * grid * block) != cudaSuccess) {
+    cudaGetLastError();
+    return EIK_ENOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  eik::fp64_rate_kernel<<<grid, block, 0, s>>>(d, iters / 8 + 1, 1.0);   // warm-up
+  cudaEventRecord(e0, s);
+  eik::fp64_rate_kernel<<<grid, block, 0, s>>>(d, iters, 1.0);
+  cudaEventRecord(e1, s);
+  eik::note_launches(2);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess || !(ms > 0.f)) {
+    cudaGetLastError();
+    return EIK_ECUDA;
+  }
+  *inst_per_s = static_cast<double>(grid) * block * 8.0 * static_cast<double>(iters) / (ms * 1e-3);
+  return EIK_OK;
+}
 
 extern "C" eik_status eik_selftest(int64_t n, uint64_t seed, int64_t *mismatches, void *stream) {
   if (n < 0 || !mismatches) return EIK_EINVAL;

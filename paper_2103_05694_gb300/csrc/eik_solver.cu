@@ -69,6 +69,14 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
   return (static_cast<unsigned long long>(hi) << 32) | lo;
 }
 
+// Phase timing (counters >= 2, thread 0): add the cycles since the last lap
+// to slot k of the CTA's statistics (slot 12 holds the last lap's clock).
+__device__ __forceinline__ void lap(long long *st, int k) {
+  const long long c1 = clock64();
+  st[k] += c1 - st[12];
+  st[12] = c1;
+}
+
 // One axis of a cell after an acceptance step: sides (left/right) with their
 // values after the step and whether they changed (decreased).  True when the
 // axis minimum decreased and is now below `best`: the smallest changed value
@@ -415,13 +423,9 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 // + 1) * delta are deferred: recorded in the tile's pending mask and the tile
 // re-queued at their bucket.  Only accepted values are written to memory.
 // ---------------------------------------------------------------------------
-// Register budget: at least this many 256-thread CTAs per SM (scaled for
-// other tile sizes).
-#ifndef EIK_MIN_CTAS_256
-#define EIK_MIN_CTAS_256 2
-#endif
+// Register budget: resident_ctas(tile cells) CTAs per SM.
 template <int D, int TX, int TY, int TZ, int ARITH>
-__global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * TY * TZ))
+__global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     persistent_kernel(SolveParams p) {
   constexpr int NT = TX * TY * TZ;
   static_assert(NT % 32 == 0 && NT <= 32 * kPendWords, "whole warps, one pending bit per cell");
@@ -444,6 +448,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
   __shared__ int s_prob, s_faces;
   __shared__ unsigned s_slot, s_lo;
   __shared__ int s_cont;
+  // statistics, kept in shared memory so that no thread carries them in
+  // registers through the persistent loop: [0] evaluations, [1] acceptances,
+  // [2] commits, [3] visits, [4] rounds, [5] visit ns, [6] idle ns, [7..11]
+  // cycles per phase (counters >= 2), [12] phase clock, [13] idle since,
+  // [14] claim time; s_path: d-bar path counts (counters >= 2)
+  __shared__ long long s_stat[15];
+  __shared__ unsigned s_path[4];
 
   const int tid = threadIdx.x;
   const unsigned lane = tid & 31;
@@ -452,6 +463,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
   const int xc = lx + 1, yc = ly + 1, zc = lz + HZ;
   s_pv[tid] = kInfBits;
   if (tid == 0) { s_cmin = kInfBits; s_min[0] = s_min[1] = s_min[2] = kInfBits; s_cnt[0] = s_cnt[1] = 0; }
+  if (tid < 15) s_stat[tid] = 0;
+  if (tid < 4) s_path[tid] = 0u;
   const double delta = p.ctl->delta;
   const float inv_delta = static_cast<float>(p.ctl->inv_delta);
   const float band_scale = static_cast<float>(p.band) * rsqrtf(static_cast<float>(D));
@@ -463,12 +476,6 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
     }
   }
   unsigned R = 1;
-  unsigned long long n_evals = 0, n_dec = 0, n_commits = 0, n_visits = 0, n_rounds = 0;
-  unsigned long long visit_ns = 0, idle_ns = 0;
-  unsigned path[4] = {0u, 0u, 0u, 0u};          // newton, walk, bisect, dbar calls
-  unsigned long long cyc[5] = {0ull, 0ull, 0ull, 0ull, 0ull};   // load, A, B, C, commit
-  long long c0 = 0;
-  long long idle_since = 0, t_claim = 0;
   __syncthreads();
 
 #pragma unroll 1
@@ -480,7 +487,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
       const long long t_pop = (p.counters || p.trace) ? now_ns() : 0;
 #pragma unroll 1
       for (;;) {
-        const unsigned long long e = pop_entry(p, idle_since, slot, lo);
+        const unsigned long long e = pop_entry(p, s_stat[13], slot, lo);
         if (e == kEmpty) break;
         const unsigned long long tl = e & 0xffffffffull;
         const unsigned b = static_cast<unsigned>(e >> 32);
@@ -495,10 +502,10 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         }
       }
       if (tid == 0) {
-        idle_since = 0;
+        s_stat[13] = 0;
         if (p.counters || p.trace) {
-          t_claim = now_ns();
-          idle_ns += static_cast<unsigned long long>(t_claim - t_pop);
+          s_stat[14] = now_ns();
+          s_stat[6] += s_stat[14] - t_pop;
         }
         int prob = 0;
         if (tile >= 0) {
@@ -520,7 +527,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
     const long long tile = s_tile;
     if (tile < 0) break;
     const bool timing = p.counters >= 2 && tid == 0;
-    if (timing) c0 = clock64();
+    if (timing) s_stat[12] = clock64();
     const int faces = s_faces;
     const Prob &P = p.probs[s_prob];
     double *const T = P.t;
@@ -594,7 +601,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
     if (tid < 6) s_facemin[tid] = kInfBits;
     if (tid == 0) { s_min[0] = s_min[1] = s_min[2] = kInfBits; s_cnt[0] = 0; s_cnt[1] = 0; }
     __syncthreads();
-    if (timing) { const long long c1 = clock64(); cyc[0] += c1 - c0; c0 = c1; }
+    if (timing) lap(s_stat, 7);
     if (first && tid == 0) {   // band = k * sqrt(c_min) / sqrt(D): one cell's travel time
       const float cm = s_cmin < kInfBits ? xf::to_f(s_cmin) : 0.0f;
       // s_cmin is the smallest c (or r for the explicit roots): one cell's travel time
@@ -646,7 +653,6 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
       if (accept && is_pending(pv, bits_of(tv)) && pv <= lim) {
         tv = from_bits(pv);
         acc = true;
-        ++n_dec;
       }
       {  // what stays pending takes part in this round's minimum
         const unsigned long long keep = warp_min64(is_pending(pv, bits_of(tv)) ? pv : kInfBits);
@@ -719,7 +725,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
           for (int k = 0; k < D; ++k) s_a[k][tid] = a[k];
           s_best[tid] = best;
         }
-        ++n_evals;
+      }
+      if (p.counters) {   // evaluations and acceptances of this round (warp-aggregated)
+        const unsigned ev = __ballot_sync(kFull, need);
+        if (lane == 0 && (ev | accbits)) {
+          atomicAdd(reinterpret_cast<unsigned long long *>(&s_stat[0]), static_cast<unsigned long long>(__popc(ev)));
+          atomicAdd(reinterpret_cast<unsigned long long *>(&s_stat[1]), static_cast<unsigned long long>(__popc(accbits)));
+        }
       }
       ++pass_round;
       {
@@ -730,7 +742,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         if (go) s_list[base + __popc(bal & ((1u << lane) - 1u))] = static_cast<unsigned short>(tid);
       }
       __syncthreads();                                              // barrier 1
-      if (timing) { const long long c1 = clock64(); cyc[1] += c1 - c0; c0 = c1; }
+      if (timing) lap(s_stat, 8);
       // (B) dense arithmetic phase.  Few cells (at most p.lane_group_cells): a
       //     group of 8 (or 4) lanes per cell evaluates d-bar (guess + one G
       //     pass over a window of points); else one lane per cell.  Only warps
@@ -782,7 +794,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
             } else {
               dec = ARITH == kArithInt ? xf::relax<D>(s_best[c], a, s_c[c], nv)
                                        : hw::relax<D>(s_best[c], a, s_c[c], nv,
-                                                      p.counters >= 2 ? path : nullptr);
+                                                      p.counters >= 2 ? s_path : nullptr);
             }
             if (dec) s_pv[c] = nv; else nv = kInfBits;
           }
@@ -793,7 +805,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
         }
       }
       __syncthreads();                                              // barrier 2
-      if (timing) { const long long c1 = clock64(); cyc[2] += c1 - c0; c0 = c1; }
+      if (timing) lap(s_stat, 9);
       ++R;
       if (rounds >= kMaxRounds) {   // uniform across the CTA
         if (tid == 0) raise_status(p.ctl, kEtimeout, 7);
@@ -804,13 +816,18 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
 
     // commit and collect the smallest committed time per tile face
     const bool track = p.track_changes != 0;
-    if (track ? bits_of(tv) != bits_of(tv0) : bits_of(tv) < bits_of(tv0)) {
+    const bool commit = track ? bits_of(tv) != bits_of(tv0) : bits_of(tv) < bits_of(tv0);
+    if (p.counters) {
+      const unsigned cm = __ballot_sync(kFull, commit);
+      if (lane == 0 && cm)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&s_stat[2]), static_cast<unsigned long long>(__popc(cm)));
+    }
+    if (commit) {
       const unsigned long long tb = bits_of(tv);
       if (track)   // a value may rise: only this tile's visit writes its cells
         st_rlx(reinterpret_cast<unsigned long long *>(T + gidx), tb);
       else
         atomicMin(reinterpret_cast<unsigned long long *>(T + gidx), tb);
-      ++n_commits;
       // a face value can change the cell across the face only if it is below
       // that cell's value (causality; the loaded halo value is an upper bound).
       // Change tracking activates on any change.
@@ -888,7 +905,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
     }
     __syncthreads();
     if (tid == 0) {
-      if (timing) { const long long c1 = clock64(); cyc[4] += c1 - c0; c0 = c1; }
+      if (timing) lap(s_stat, 11);
       if (m < kInfBits) {   // deferred cells: come back at their bucket, beyond this window
         unsigned b = bucket_of_time(m, inv_delta);
         const unsigned bmin = s_lo + p.window + 1u;
@@ -899,14 +916,14 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
       __threadfence();
       atomicAdd(&p.ctl->run[s_slot * kCounterPad], 0xffffffffu);
       atomicAdd(&p.ctl->work, -1);
-      ++n_visits;
-      n_rounds += rounds;
-      if (p.counters) visit_ns += static_cast<unsigned long long>(now_ns() - t_claim);
+      s_stat[3] += 1;
+      s_stat[4] += rounds;
+      if (p.counters) s_stat[5] += now_ns() - s_stat[14];
       if (p.trace) {
         const unsigned long long k = atomicAdd(&p.ctl->trace_n, 1ull);
         if (k < p.trace_cap) {
           TraceRec rec;
-          rec.t_claim = t_claim;
+          rec.t_claim = s_stat[14];
           rec.t_end = now_ns();
           rec.tile = static_cast<unsigned>(tile);
           rec.lo = s_lo;
@@ -919,35 +936,23 @@ __global__ void __launch_bounds__(TX * TY * TZ, EIK_MIN_CTAS_256 * 256 / (TX * T
   }
 
   if (p.counters) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      n_evals += __shfl_xor_sync(kFull, n_evals, o);
-      n_dec += __shfl_xor_sync(kFull, n_dec, o);
-      n_commits += __shfl_xor_sync(kFull, n_commits, o);
-    }
-    if (p.counters >= 2) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        unsigned v = path[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-        if (lane == 0 && v) atomicAdd(&p.ctl->stats[kStatNewton + k], static_cast<unsigned long long>(v));
-      }
-      if (tid == 0) {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) atomicAdd(&p.ctl->stats[kStatCycLoad + k], cyc[k]);
-      }
-    }
-    if (lane == 0) {
-      atomicAdd(&p.ctl->stats[kStatEvals], n_evals);
-      atomicAdd(&p.ctl->stats[kStatDecreases], n_dec);
-      atomicAdd(&p.ctl->stats[kStatCommits], n_commits);
-    }
+    __syncthreads();
     if (tid == 0) {
-      atomicAdd(&p.ctl->stats[kStatVisits], n_visits);
-      atomicAdd(&p.ctl->stats[kStatRounds], n_rounds);
-      atomicAdd(&p.ctl->stats[kStatVisitNs], visit_ns);
-      atomicAdd(&p.ctl->stats[kStatIdleNs], idle_ns);
+      const unsigned long long *st = reinterpret_cast<const unsigned long long *>(s_stat);
+      atomicAdd(&p.ctl->stats[kStatEvals], st[0]);
+      atomicAdd(&p.ctl->stats[kStatDecreases], st[1]);
+      atomicAdd(&p.ctl->stats[kStatCommits], st[2]);
+      atomicAdd(&p.ctl->stats[kStatVisits], st[3]);
+      atomicAdd(&p.ctl->stats[kStatRounds], st[4]);
+      atomicAdd(&p.ctl->stats[kStatVisitNs], st[5]);
+      atomicAdd(&p.ctl->stats[kStatIdleNs], st[6]);
+      if (p.counters >= 2) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) atomicAdd(&p.ctl->stats[kStatCycLoad + k], st[7 + k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (s_path[k]) atomicAdd(&p.ctl->stats[kStatNewton + k], static_cast<unsigned long long>(s_path[k]));
+      }
     }
   }
 }
@@ -1306,6 +1311,7 @@ struct ShapeOps {
         case 1: { using S = ShapeOps<3, 16, 4, 4, false>; CALL; } break;     \
         case 2: { using S = ShapeOps<3, 32, 4, 2, false>; CALL; } break;     \
         case 3: { using S = ShapeOps<3, 8, 4, 4, false>; CALL; } break;      \
+        case 4: { using S = ShapeOps<3, 4, 4, 4, false>; CALL; } break;      \
         default: { using S = ShapeOps<3, kTX3, kTY3, kTZ3, true>; CALL; }    \
       }                                                                      \
     } else {                                                                 \
@@ -1313,6 +1319,7 @@ struct ShapeOps {
         case 1: { using S = ShapeOps<2, 32, 8, 1, false>; CALL; } break;     \
         case 2: { using S = ShapeOps<2, 32, 4, 1, false>; CALL; } break;     \
         case 3: { using S = ShapeOps<2, 16, 8, 1, false>; CALL; } break;     \
+        case 4: { using S = ShapeOps<2, 16, 4, 1, false>; CALL; } break;     \
         default: { using S = ShapeOps<2, kTX2, kTY2, 1, true>; CALL; }       \
       }                                                                      \
     }                                                                        \

@@ -128,20 +128,28 @@ def smooth_random_volume(n: int, seed: int, vmin: float, vmax: float,
     return vmin + (g - lo) * ((vmax - vmin) / (hi - lo))
 
 
-def checker_3d_256() -> Problem:
-    """3D 256^3, h = 10 m, smooth random 1500-4500 m/s with a 16^3-cell 10:1
-    checkerboard (slow cells v/10) in the central 128^3 block; source at
-    (x, y, z) = (128, 128, 0)."""
-    n = 256
+def checker_3d(n: int = 256) -> Problem:
+    """3D n^3, h = 10 m, smooth random 1500-4500 m/s with a 16^3-cell 10:1
+    checkerboard (slow cells v/10) in the central (n/2)^3 block; source at
+    (x, y, z) = (n/2, n/2, 0).  n = 256 is the benchmark volume; smaller n give
+    reduced cases of the same structure (profiling)."""
     v = smooth_random_volume(n, 3, 1500.0, 4500.0, 8.0)
-    lo, hi = 64, 192
+    lo, hi = n // 4, n // 4 + n // 2
     idx = np.arange(lo, hi)
     cz, cy, cx = np.meshgrid(idx // 16, idx // 16, idx // 16, indexing="ij")
     slow = ((cz + cy + cx) % 2) == 1
     block = v[lo:hi, lo:hi, lo:hi]
     v[lo:hi, lo:hi, lo:hi] = np.where(slow, block / 10.0, block)
-    src = np.array([_flat(v.shape, 0, 128, 128)], dtype=np.int64)
-    return Problem("3d_256_checker", v, 10.0, src, np.zeros(1), {})
+    src = np.array([_flat(v.shape, 0, n // 2, n // 2)], dtype=np.int64)
+    name = "3d_256_checker" if n == 256 else f"3d_{n}_checker"
+    return Problem(name, v, 10.0, src, np.zeros(1), {})
+
+
+def checker_3d_256() -> Problem:
+    """3D 256^3, h = 10 m, smooth random 1500-4500 m/s with a 16^3-cell 10:1
+    checkerboard (slow cells v/10) in the central 128^3 block; source at
+    (x, y, z) = (128, 128, 0)."""
+    return checker_3d(256)
 
 
 def smooth_model_3d_128(n: int = 128) -> np.ndarray:

@@ -64,3 +64,22 @@ def test_all_cores_oracle_baseline_runs_every_core():
     cores = len(os.sched_getaffinity(0))
     assert r["cores"] == cores and r["kind"] == "oracle" and r["value"] > 0
     assert f"on {cores} host cores" in r["sample"]
+
+
+def test_fp64_roofline_arithmetic():
+    """FP64 instructions per launch = instructions per evaluation (ncu) x the live
+    evaluation count; achieved over the kernel time, against the measured rate."""
+    fake = types.SimpleNamespace(eik=types.SimpleNamespace(eik_fp64_rate=lambda: 5.0e11))
+    saved = dict(bench.MEASURED_FP64_PER_EVAL)
+    try:
+        bench.MEASURED_FP64_PER_EVAL[3] = 20.0
+        r = bench.roofline_fp64(fake, 1_000_000, 4.0, 3, "k")
+        assert r["bound"] == "fp64" and r["peak"] == 500.0
+        assert abs(r["achieved"] - 20.0 * 1e6 / 4e-3 / 1e9) < 1e-9
+        assert abs(r["frac"] - r["achieved"] / 500.0) < 1e-15
+        bench.MEASURED_FP64_PER_EVAL[3] = None
+        r = bench.roofline_fp64(fake, 1_000_000, 4.0, 3, "k")
+        assert r["achieved"] is None and r["frac"] is None and r["peak"] == 500.0
+    finally:
+        bench.MEASURED_FP64_PER_EVAL.clear()
+        bench.MEASURED_FP64_PER_EVAL.update(saved)

@@ -24,6 +24,10 @@ def _built():
     eik.load_library()
 
 
+def _bits(x):
+    return np.ascontiguousarray(x).view(np.uint64)
+
+
 SCHEDULES = {"levels": eik.ADJ_LEVELS, "tiles": eik.ADJ_TILES}
 
 
@@ -237,3 +241,24 @@ def test_tomography_gradient_central_differences():
     assert np.median(err) <= 1e-6, (np.median(err), err.max())
     unexplained = over & ~kink
     assert not unexplained.any(), (cells[unexplained], err[unexplained])
+
+
+def test_sum_ordered_bits():
+    """eik_sum_ordered: +0 + x_0 + x_1 + ... in list order, each addition
+    rounded to nearest, bit for bit as a sequential sum on the host; the order
+    matters for these inputs; k = 0 writes +0."""
+    rng = np.random.Generator(np.random.PCG64(12))
+    xs = [rng.standard_normal(50_001) * 10.0 ** rng.integers(-12, 12, 50_001) for _ in range(9)]
+    dev = [torch.from_numpy(x).to(DEV) for x in xs]
+    out = torch.full_like(dev[0], np.nan)
+    eik.eik_sum_ordered(dev, out)
+    want = np.zeros(xs[0].shape)
+    for x in xs:
+        want = want + x
+    assert np.array_equal(_bits(out.cpu().numpy()), _bits(want))
+    rev = np.zeros(xs[0].shape)
+    for x in xs[::-1]:
+        rev = rev + x
+    assert not np.array_equal(_bits(rev), _bits(want))
+    eik.eik_sum_ordered([], out)
+    assert np.array_equal(_bits(out.cpu().numpy()), _bits(np.zeros(xs[0].shape)))

@@ -33,7 +33,7 @@ SHAPES = [(1, 1), (7, 300), (33, 65), (100, 37), (64, 64), (300, 5),
           (1, 1, 1), (5, 5, 5), (17, 5, 9), (9, 33, 5), (20, 21, 22), (3, 40, 2)]
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_tile_shapes_bit_exact(shape, tile):
     p = synth.random_problem(500 + len(shape) * 7 + shape[0], shape, n_src=3, contrast=8.0,
@@ -46,7 +46,7 @@ def test_tile_shapes_bit_exact(shape, tile):
     assert r.stats["good"] == int(np.isfinite(ref).sum()) - len(np.unique(p.sources))
 
 
-@pytest.mark.parametrize("tile", [2, 3, 4])
+@pytest.mark.parametrize("tile", [2, 3, 4, 5])
 def test_tile_shapes_layered_section(tile):
     p = synth.layered_2d_2301x751()
     ref = oracle.fmm(p.speed, p.h, p.sources).t
@@ -56,7 +56,7 @@ def test_tile_shapes_layered_section(tile):
     _bits_equal(r.t.cpu().numpy(), ref, f"layered tile {tile}")
 
 
-@pytest.mark.parametrize("tile", [0, 2, 4])
+@pytest.mark.parametrize("tile", [0, 2, 4, 5])
 def test_tile_shapes_batched_and_plan(tile):
     base = synth.random_problem(31, (30, 41, 23), n_src=1, contrast=6.0, smooth_sigma=1.5, h=1.0)
     speed = torch.from_numpy(base.speed).to(DEV)
@@ -76,7 +76,8 @@ def test_tile_shapes_batched_and_plan(tile):
     plan.close()
 
 
-@pytest.mark.parametrize("opts", [{"tile": 5}, {"tile": -1}, {"tile": 2, "arith": 2}])
+@pytest.mark.parametrize("opts", [{"tile": 6}, {"tile": -1}, {"tile": 2, "arith": 2},
+                                  {"tile": 6, "arith": 2}])
 def test_bad_tile_is_einval(opts):
     speed = torch.ones((8, 9), dtype=torch.float64, device=DEV)
     with pytest.raises(eik.EikError) as e:
