@@ -70,9 +70,9 @@ typedef enum {
  * batch has:
  *   2D, fewer than 8 sources in the batch: 16x16 tiles, k_delta 16, window 16,
  *     band 16, 1 CTA per SM (latency-bound: one front);
- *   2D, 8 or more sources: 16x8 tiles, k_delta 2, window 16, band 16, 8 CTAs of
+ *   2D, 8 or more sources: 16x8 tiles, k_delta 4, window 16, band 8, 8 CTAs of
  *     128 threads per SM;
- *   3D: 8x4x4 tiles, k_delta 1, window 16, band 8, 8 CTAs of 128 threads per SM.
+ *   3D: 8x4x4 tiles, k_delta 0.75, window 31, band 6, 8 CTAs of 128 threads per SM.
  * (The per-CTA work is latency-bound, so the kernel is compiled for as many
  * resident CTAs as registers allow: 2 per SM for 256-cell tiles, 8 for 128-cell
  * tiles, 16 for 64-cell tiles.)
@@ -88,7 +88,8 @@ typedef struct {
                               that nothing sets, so the wait reaches timeout_ms and the
                               call returns EIK_ETIMEOUT (exercises the bounded waits) */
     int window;            /* buckets above the lowest active bucket that may be worked on
-                              (look-ahead of the relaxed priority order); 0: default */
+                              (look-ahead of the relaxed priority order; values above 31
+                              act as 31); 0: default */
     double band;           /* in-tile acceptance band in units of (smallest h/v of the tile)
                               / sqrt(ndim), i.e. one cell's travel time; <= 0: default */
     int arith;             /* arithmetic of d-bar: 1 = FP64 unit, 2 = exact emulation on the

@@ -41,8 +41,8 @@ constexpr uint64_t kMaxCapEntries = uint64_t(1) << 30;   // whole ring storage l
 // adjoint schedule by default: the tile schedule (else level-synchronous)
 constexpr bool kAdjTilesDefault = true;
 constexpr double kDefaultKDelta[2] = {16.0, 2.0};
-constexpr int kDefaultWindow[2] = {16, 16};
-constexpr double kDefaultBand[2] = {16.0, 8.0};
+constexpr int kDefaultWindow[2] = {16, 31};      // single 2D front, 3D (2D batches: 16)
+constexpr double kDefaultBand[2] = {16.0, 6.0};  // single 2D front, 3D (2D batches: 8)
 constexpr int kDefaultCtasPerSm[2] = {1, 2};   // per 256 cells of tile (single 2D front)
 constexpr int kMaxRetries = 4;
 // eik_opts.sched_flags bits of the tomography interface
@@ -322,12 +322,14 @@ eik_status check_problem(const double *speed, double h, int ndim, const int64_t 
 struct AutoCfg {
   int shape;
   double k_delta;
+  double band;
+  int window;
 };
 AutoCfg auto_config(int ndim, int64_t total_sources, bool int_arith) {
-  if (int_arith) return {0, kDefaultKDelta[ndim == 3 ? 1 : 0]};
-  if (ndim == 3) return {3, 1.0};
-  if (total_sources >= 8) return {3, 2.0};
-  return {0, kDefaultKDelta[0]};
+  if (int_arith) return {0, kDefaultKDelta[ndim == 3 ? 1 : 0], ndim == 3 ? 8.0 : 16.0, 16};
+  if (ndim == 3) return {3, 0.75, kDefaultBand[1], kDefaultWindow[1]};
+  if (total_sources >= 8) return {3, 4.0, 8.0, 16};
+  return {0, kDefaultKDelta[0], kDefaultBand[0], kDefaultWindow[0]};
 }
 
 int64_t count_sources(const std::vector<HostProblem> &hps) {
@@ -683,8 +685,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.tile_src = ws().tile_src.p;
   sp.pend = ws().pend.p;
   const int di = ndim == 3 ? 1 : 0;
-  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow[di]);
-  sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand[di];
+  const AutoCfg ac = auto_config(ndim, total_src, opts && opts->arith == 2);
+  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : ac.window);
+  sp.band = opts && opts->band > 0 ? opts->band : ac.band;
   sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
   sp.tile_shape = shape;
@@ -702,9 +705,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.timeout_ns = tmo_ms * 1000000ll;
   sp.counters = opts ? opts->counters : 0;
   sp.test_stall = opts ? opts->test_stall : 0;
-  const double k_delta = opts && opts->k_delta > 0
-                             ? opts->k_delta
-                             : auto_config(ndim, total_src, sp.arith == eik::kArithInt).k_delta;
+  const double k_delta = opts && opts->k_delta > 0 ? opts->k_delta : ac.k_delta;
   const double delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
 
   CK(eik::launch_seed(sp, ws().seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
@@ -864,7 +865,6 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
     max_cells = std::max<int64_t>(max_cells, hps[(size_t)i].n);
   }
   const int ndim = hps[0].ndim;
-  const int di = ndim == 3 ? 1 : 0;
   if (base && base->schedule != 0) {
     set_err("eik_autotune tunes the asynchronous schedule (opts.schedule 0)");
     return EIK_EINVAL;
@@ -887,9 +887,9 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
     const AutoCfg ac = auto_config(ndim, count_sources(hps), int_arith);
     if (cur.tile <= 0) cur.tile = ac.shape + 1;
     if (cur.k_delta <= 0) cur.k_delta = ac.k_delta;
+    if (cur.window <= 0) cur.window = ac.window;
+    if (cur.band <= 0) cur.band = ac.band;
   }
-  if (cur.window <= 0) cur.window = kDefaultWindow[di];
-  if (cur.band <= 0) cur.band = kDefaultBand[di];
 
   unsigned long long ref[2] = {0, 0};
   bool have_ref = false;
@@ -934,9 +934,9 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
   double best_ms = 0;
   eik_status st = trial(cur, best_ms);
   if (st != EIK_OK) { if (ntrials) *ntrials = std::min(n, max_trials); return st; }
-  static const double kds[] = {1, 2, 4, 8, 16, 32};
-  static const int wins[] = {1, 2, 4, 8, 16};
-  static const double bands[] = {1, 2, 4, 8, 16};
+  static const double kds[] = {0.5, 0.75, 1, 2, 4, 8, 16, 32};
+  static const int wins[] = {1, 2, 4, 8, 16, 24, 31};
+  static const double bands[] = {1, 2, 4, 6, 8, 12, 16};
   constexpr double kGain = 0.01;   // a change must save more than 1 %
   auto consider = [&](const eik_opts &o) -> eik_status {
     double ms = 0;
@@ -1269,7 +1269,7 @@ const char *eik_status_str(eik_status s) {
 
 const char *eik_last_error(void) { return g_err; }
 
-int eik_abi_version(void) { return 107; }
+int eik_abi_version(void) { return 108; }
 
 uint64_t eik_kernel_launches(void) { return (uint64_t)eik::kernel_launches(); }
 
@@ -1459,8 +1459,9 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   sp.counters = opts ? opts->counters : 0;
   sp.test_stall = 0;
   const int di = pl.ndim == 3 ? 1 : 0;
-  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : kDefaultWindow[di]);
-  sp.band = opts && opts->band > 0 ? opts->band : kDefaultBand[di];
+  const AutoCfg ac = auto_config(pl.ndim, count_sources(hps), opts && opts->arith == 2);
+  sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : ac.window);
+  sp.band = opts && opts->band > 0 ? opts->band : ac.band;
   sp.arith = opts && opts->arith == 2 ? eik::kArithInt : eik::kArithFp64;
   sp.gate_pending_only = opts && (opts->sched_flags & 1) ? 1 : 0;
   sp.tile_shape = shape;
@@ -1469,9 +1470,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   sp.visit_budget = sp.track_changes ? (unsigned long long)pl.total_tiles * 256ull + 4096ull : 0ull;
   sp.trace = nullptr;
   sp.trace_cap = 0;
-  pl.k_delta = opts && opts->k_delta > 0
-                   ? opts->k_delta
-                   : auto_config(pl.ndim, count_sources(hps), opts && opts->arith == 2).k_delta;
+  pl.k_delta = opts && opts->k_delta > 0 ? opts->k_delta : ac.k_delta;
   pl.delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
   pl.from_slowness = from_slowness(opts);
   int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm

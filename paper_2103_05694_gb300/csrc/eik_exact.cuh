@@ -389,27 +389,29 @@ __device__ __forceinline__ unsigned long long ffguess(const unsigned long long (
     }
   }
   const ffa::F2 c = ffa::split(cb);
-  ffa::F2 u = ffa::sqrt(c);                                      // one-sided
+  // the roots with one, two and three active axes are computed independently
+  // (no chain from one to the next, no divergence between lanes with
+  // different active sets) and the active set picks one: two axes when
+  // b1 < u1, three when also b2 < u2 (and the discriminant is positive)
+  const ffa::F2 u1 = ffa::sqrt(c);                               // one-sided
+  ffa::F2 u = u1;
   if (s1 < xf::kInf) {
     const ffa::F2 b1 = ffa::split(xf::as_u(__dsub_rn(xf::as_d(s1), xf::as_d(s0))));
-    if (b1.hi < u.hi) {                                          // two axes
-      const ffa::F2 X = ffa::add(ffa::scale2(c, 2.0f), ffa::neg(ffa::mul(b1, b1)));
-      u = ffa::scale2(ffa::add(b1, ffa::sqrt(X)), 0.5f);
-      if (D > 2 && s2 < xf::kInf) {
-        const ffa::F2 b2 = ffa::split(xf::as_u(__dsub_rn(xf::as_d(s2), xf::as_d(s0))));
-        if (b2.hi < u.hi) {                                      // three axes
-          const ffa::F2 S = ffa::add(b1, b2);
-          const ffa::F2 Q = ffa::add(ffa::mul(b1, b1), ffa::mul(b2, b2));
-          const ffa::F2 disc = ffa::add(ffa::mul(S, S),
-                                        ffa::mul(ffa::F2{-3.0f, 0.0f}, ffa::add(Q, ffa::neg(c))));
-          if (disc.hi > 0.0f) {
-            const ffa::F2 third{__int_as_float(0x3eaaaaab),
-                                __int_as_float(static_cast<int>(0xb22aaaabu))};
-            u = ffa::mul(ffa::add(S, ffa::sqrt(disc)), third);
-          }
-        }
-      }
+    const ffa::F2 X = ffa::add(ffa::scale2(c, 2.0f), ffa::neg(ffa::mul(b1, b1)));
+    const ffa::F2 u2 = ffa::scale2(ffa::add(b1, ffa::sqrt(X)), 0.5f);   // two axes
+    bool three = false;
+    ffa::F2 u3 = u2;
+    if (D > 2) {
+      const ffa::F2 b2 = ffa::split(xf::as_u(__dsub_rn(xf::as_d(s2), xf::as_d(s0))));
+      const ffa::F2 S = ffa::add(b1, b2);
+      const ffa::F2 Q = ffa::add(ffa::mul(b1, b1), ffa::mul(b2, b2));
+      const ffa::F2 disc = ffa::add(ffa::mul(S, S),
+                                    ffa::mul(ffa::F2{-3.0f, 0.0f}, ffa::add(Q, ffa::neg(c))));
+      const ffa::F2 third{__int_as_float(0x3eaaaaab), __int_as_float(static_cast<int>(0xb22aaaabu))};
+      u3 = ffa::mul(ffa::add(S, ffa::sqrt(disc)), third);            // three axes
+      three = s2 < xf::kInf && b2.hi < u2.hi && disc.hi > 0.0f;
     }
+    if (b1.hi < u1.hi) u = three ? u3 : u2;
   }
   // tau = s0 + (hi + lo) on the FP64 unit: hi + lo as one double (exact, or
   // within 2^-53 of u when lo is far below hi), then one addition rounded

@@ -47,7 +47,7 @@ def test_status_strings_without_gpu(lib):
     assert lib.eik_status_str(0) == b"EIK_OK"
     assert lib.eik_status_str(3) == b"EIK_ECAPACITY"
     lib.eik_abi_version.restype = ctypes.c_int
-    assert lib.eik_abi_version() == 107
+    assert lib.eik_abi_version() == 108
 
 
 def test_struct_layouts_match_header():
