@@ -54,13 +54,16 @@ L2_FLUSH_BYTES = 512 << 20
 # ncu DRAM bytes (read + write) per launch of the persistent kernel in its default
 # configuration, from the one-pass captures summarised in profiles/ (refresh them
 # whenever the kernel changes)
-MEASURED_TRAFFIC = {"layered_2d": 28160000 + 682496, "checker_3d": 280830720 + 109687040}
+MEASURED_TRAFFIC = {"layered_2d": 28484864 + 732416, "checker_3d": 277765120 + 108154368}
+# ncu DRAM bytes of one launch of the 88-problem batch in the default options
+# (the benchmark autotunes, so this is context, not the traffic of the timed launch)
+BATCH_TRAFFIC_DEFAULT_OPTIONS = 11749174784 + 2233317376
 
 # FP64 thread instructions (DADD + DMUL + DFMA, ncu sass counters) per operator
 # evaluation of the persistent kernel, by dimension, from one-launch captures
 # summarised in profiles/ (refresh them whenever the kernel changes); None: not
 # measured for this build
-MEASURED_FP64_PER_EVAL = {2: None, 3: None}
+MEASURED_FP64_PER_EVAL = {2: 13.117, 3: 14.952, "batched_3d": 14.488}
 
 WORKLOADS = {
     "layered_2d": "2d_2301x751_layered_h4_1src",
@@ -432,11 +435,12 @@ def roofline(useful_per_launch: int, kern_ms: float, traffic, what: str):
             "peak_kind": f"{kind} copy bandwidth"}
 
 
-def roofline_fp64(C, evals_per_launch: int, kern_ms: float, ndim: int, what: str):
+def roofline_fp64(C, evals_per_launch: int, kern_ms: float, ndim: int, what: str,
+                  workload: str | None = None):
     """The FP64 roofline of the persistent kernel: FP64 thread instructions per
     launch (ncu instructions per evaluation x the live evaluation count) over the
     kernel's event time, against the device's measured FP64 add rate."""
-    per_eval = MEASURED_FP64_PER_EVAL.get(ndim)
+    per_eval = MEASURED_FP64_PER_EVAL.get(workload, MEASURED_FP64_PER_EVAL.get(ndim))
     peak = C.eik.eik_fp64_rate() / 1e9
     if per_eval is None:
         return {"bound": "fp64", "achieved": None, "peak": peak, "unit": "G FP64 inst/s",
@@ -571,7 +575,8 @@ def run_single(args, C, wl_name):
                                  "fsm_kernel (Algorithm 5 sweeps)"][args.schedule])
     if args.schedule == 0:
         line["roofline_fp64"] = roofline_fp64(C, st["evals"], statistics.mean(solve_ms),
-                                              prob.speed.ndim, line["roofline"]["kernel"])
+                                              prob.speed.ndim, line["roofline"]["kernel"],
+                                              args.workload)
     line["e2e"] = {"value": useful * n / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(prob.speed.nbytes + h_src.nbytes),
                    "d2h_bytes_per_step": int(prob.speed.nbytes)}
@@ -653,8 +658,10 @@ def run_batched(args, C, wl_name):
                       "out": torch.empty(p.speed.shape, dtype=torch.float64).pin_memory()}
                      for p in probs]
 
+    e2e_retries = []
+
     def e2e_call():
-        eik.eik_solve_batched(host_problems, opts, C.stream)
+        e2e_retries.append(eik.eik_solve_batched(host_problems, opts, C.stream)["retries"])
     e2e_ms = time_e2e(C, e2e_call, 3)
     for hp, r in zip(host_problems, refs):
         assert np.array_equal(hp["out"].numpy(), r.cpu().numpy())
@@ -676,11 +683,13 @@ def run_batched(args, C, wl_name):
                                  bad=st["decreases"] - st["good"])
     line["roofline"] = roofline(useful_mine, statistics.mean(solve_ms), args.traffic_bytes,
                                 "persistent_kernel (all problems in one launch)")
+    line["roofline"]["traffic_default_options"] = BATCH_TRAFFIC_DEFAULT_OPTIONS
     line["roofline_fp64"] = roofline_fp64(C, st["evals"], statistics.mean(solve_ms), 3,
-                                          line["roofline"]["kernel"])
+                                          line["roofline"]["kernel"], "batched_3d")
     line["e2e"] = {"value": useful_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                   "call": "eik_solve_batched with pinned host buffers (copies inside the call)"}
+                   "call": "eik_solve_batched with pinned host buffers (copies inside the call)",
+                   "capacity_retries": int(sum(e2e_retries))}
     line["gpu_launches"] = int(per_replay * args.steps)
     line["clocks"] = clocks
     plan.close()
@@ -775,6 +784,7 @@ def run_tomography(args, C, wl_name):
 
     # kernel-only duration of the batched forward launch
     probs = [{"speed": s0, "h": h, "sources": src, "out": outs[i]} for i, src in enumerate(srcs)]
+    fwd_evals = eik.eik_solve_batched(probs, {"sched_flags": eik.SLOWNESS_INPUT, "counters": 1})["evals"]
     solve_ms = [eik.eik_solve_batched(probs, {"sched_flags": eik.SLOWNESS_INPUT})["solve_ms"]
                 for _ in range(3)]
 
@@ -803,6 +813,8 @@ def run_tomography(args, C, wl_name):
                                                     if per_source_ms else None)}
     line["roofline"] = roofline(len(srcs) * (s0.numel() - 1), statistics.mean(solve_ms),
                                 args.traffic_bytes, "persistent_kernel (batched forward)")
+    line["roofline_fp64"] = roofline_fp64(C, fwd_evals, statistics.mean(solve_ms), 2,
+                                          line["roofline"]["kernel"])
     line["e2e"] = {"value": useful_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(h_s.numel() * 8),
                    "d2h_bytes_per_step": int(h_g.numel() * 8)}

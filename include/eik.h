@@ -366,7 +366,8 @@ typedef struct {
  * coordinate descent from `base` (NULL: defaults) over tile, k_delta (unless
  * base->delta > 0), window, band and ctas_per_sm, at most two passes; a change
  * is kept when it saves more than 1 % of the fastest device time.  Then sets
- * capacity (unless base->capacity > 0) to 4x the deepest bucket slot seen.
+ * capacity (unless base->capacity > 0) to 16x the deepest bucket slot seen (at
+ * least 1024).
  * Every trial's output must equal the first trial's bit for bit (a digest of
  * all outputs is compared; the fixed point does not depend on the schedule,
  * Theorem 1): otherwise EIK_ECUDA.  The outputs hold the solution on return.

@@ -1011,7 +1011,9 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
     eik_stats stt;
     st = run(h2, &o, &stt, s);
     if (st != EIK_OK) { if (ntrials) *ntrials = std::min(n, max_trials); return st; }
-    cur.capacity = (int64_t)next_pow2((uint64_t)std::max<int64_t>(64, 4 * stt.max_queue));
+    // the depth varies from run to run with the asynchronous schedule: a wide
+    // margin keeps later solves from overflowing (a retry costs a relaunch)
+    cur.capacity = (int64_t)next_pow2((uint64_t)std::max<int64_t>(1024, 16 * stt.max_queue));
   }
   *best = cur;
   if (ntrials) *ntrials = std::min(n, max_trials);
