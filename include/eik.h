@@ -272,7 +272,7 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
  * reproducible bit for bit.  Device pointers only.  A parallel set-up pass
  * evaluates every weight; then the cells are processed in dependency order by
  * one of two schedules (opts->sched_flags bits 3-4), with the same results:
- *   tiles (default): persistent CTAs take tiles of 16x16 (2D) or 8x8x4 (3D)
+ *   tiles (default): persistent CTAs take tiles of 16x8 (2D) or 8x8x4 (3D)
  *     cells from a queue and run the dependency order inside a tile in shared
  *     memory; a tile is queued when a cell of it may have become ready;
  *   levels: one cooperative launch processes the cells level by level, its

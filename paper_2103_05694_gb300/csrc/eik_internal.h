@@ -305,12 +305,14 @@ cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, A
 // >= total_tiles, set up by the launch).  ndim: of every problem (one tile shape
 // per launch).  The tiles are kAdjTile2 in 2D and kAdjTile3 in 3D.  ctas_per_sm
 // caps the persistent CTAs per SM (0: occupancy).
-// 2D adjoint tile (compile-time; 16x16 measured fastest against 32x16 and 32x8)
+// 2D adjoint tile (compile-time): 16x8 cells, 8 resident CTAs of 128 threads per SM
+// (32-source tomography adjoint 11.6 ms, against 12.9 ms with 16x16 tiles at 4
+// CTAs per SM, 14.0 with 32x8 and 15.7 with 32x16)
 #ifndef EIK_ADJ_TILE2_X
 #define EIK_ADJ_TILE2_X 16
 #endif
 #ifndef EIK_ADJ_TILE2_Y
-#define EIK_ADJ_TILE2_Y 16
+#define EIK_ADJ_TILE2_Y 8
 #endif
 constexpr int kAdjTile2[3] = {EIK_ADJ_TILE2_X, EIK_ADJ_TILE2_Y, 1};
 constexpr int kAdjTile3[3] = {8, 8, 4};
