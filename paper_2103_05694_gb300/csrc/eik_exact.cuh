@@ -338,16 +338,24 @@ __device__ __forceinline__ F2 mul(F2 x, F2 y) {
   const F2 p = two_prod(x.hi, y.hi);
   return fast_two_sum(p.hi, __fadd_rn(p.lo, __fadd_rn(__fmul_rn(x.hi, y.lo), __fmul_rn(x.lo, y.hi))));
 }
-__device__ __forceinline__ F2 scale2(F2 x, float k) {   // k a power of two: exact
-  return F2{__fmul_rn(x.hi, k), __fmul_rn(x.lo, k)};
-}
-__device__ __forceinline__ F2 sqrt(F2 x) {
+// sqrt(x.hi + x.lo) from the hardware's approximate reciprocal square root:
+// one Newton-Raphson step in fp32 (y + (x - y^2) r / 2, r ~ 1/sqrt(x)), then one
+// float-float correction with the same r / 2 in place of 1 / (2y) (the
+// coupled iteration of Karp and Markstein, "High-precision division and
+// square root", ACM TOMS 23(4), 1997).  About 2^-46 relative for normal x.hi;
+// no IEEE special-case path.
+__device__ __forceinline__ F2 sqrt_nr(F2 x) {
   if (!(x.hi > 0.0f)) return F2{0.0f, 0.0f};
-  const float y = sqrtf(x.hi);
+  const float r = rsqrtf(x.hi);
+  const float h = __fmul_rn(0.5f, r);
+  float y = __fmul_rn(x.hi, r);
+  y = __fmaf_rn(__fmaf_rn(-y, y, x.hi), h, y);
   const F2 p = two_prod(y, y);
   const float e = __fadd_rn(__fsub_rn(__fsub_rn(x.hi, p.hi), p.lo), x.lo);   // x - y^2
-  return fast_two_sum(y, __fdividef(e, __fadd_rn(y, y)));
+  return fast_two_sum(y, __fmul_rn(e, h));
 }
+// fp32 estimate of sqrt(x) for x > 0 (active-set decisions only).
+__device__ __forceinline__ float sqrt_est(float x) { return __fmul_rn(x, rsqrtf(x)); }
 // A non-negative finite double (bit pattern) as hi + lo without the FP64
 // pipe: hi keeps the leading 24 bits of the significand (xf::to_f truncates),
 // lo the remaining 29 bits rounded to a float.
@@ -370,12 +378,19 @@ namespace hw {
 // rearranged root d-hat of the Mitigation Strategies section; three axes:
 // u = (S + sqrt(S^2 - 3 (Q - c))) / 3), with b_k = s_k - s0 (exact FP64
 // differences of close values).  About 3 (2D) / 4 (3D) FP64 instructions;
-// u carries about 47 bits, so tau = s0 + u lands within an ulp of d-bar when
+// u carries about 46 bits, so tau = s0 + u lands within an ulp of d-bar when
 // u is small against tau (cells farther than a few dozen cells from a
 // source), else within a few.  Only speed depends on this.
 template <int D>
 __device__ __forceinline__ unsigned long long ffguess(const unsigned long long (&a)[D],
                                                       unsigned long long cb) {
+  // One float-float root for the active set, which fp32 estimates of the one-
+  // and two-axis roots pick (the root is continuous where the active set
+  // changes, so an estimate that errs near a boundary costs nothing): with k
+  // active axes and B_j = b_j for j < k, else 0,
+  //   u = (S + sqrt(S^2 - k (Q - c))) / k,   S = B_1 + B_2,   Q = B_1^2 + B_2^2,
+  // which is sqrt(c) for k = 1, the d-hat form for k = 2 and the three-axis
+  // root for k = 3.
   unsigned long long s0 = a[0], s1 = D > 1 ? a[1] : xf::kInf, s2 = D > 2 ? a[2] : xf::kInf;
   {
     const unsigned long long lo = xf::umin(s0, s1), hi = xf::umax(s0, s1);
@@ -389,35 +404,29 @@ __device__ __forceinline__ unsigned long long ffguess(const unsigned long long (
     }
   }
   const ffa::F2 c = ffa::split(cb);
-  // the roots with one, two and three active axes are computed independently
-  // (no chain from one to the next, no divergence between lanes with
-  // different active sets) and the active set picks one: two axes when
-  // b1 < u1, three when also b2 < u2 (and the discriminant is positive)
-  const ffa::F2 u1 = ffa::sqrt(c);                               // one-sided
-  ffa::F2 u = u1;
-  if (s1 < xf::kInf) {
-    const ffa::F2 b1 = ffa::split(xf::as_u(__dsub_rn(xf::as_d(s1), xf::as_d(s0))));
-    const ffa::F2 X = ffa::add(ffa::scale2(c, 2.0f), ffa::neg(ffa::mul(b1, b1)));
-    const ffa::F2 u2 = ffa::scale2(ffa::add(b1, ffa::sqrt(X)), 0.5f);   // two axes
-    bool three = false;
-    ffa::F2 u3 = u2;
-    if (D > 2) {
-      const ffa::F2 b2 = ffa::split(xf::as_u(__dsub_rn(xf::as_d(s2), xf::as_d(s0))));
-      const ffa::F2 S = ffa::add(b1, b2);
-      const ffa::F2 Q = ffa::add(ffa::mul(b1, b1), ffa::mul(b2, b2));
-      const ffa::F2 disc = ffa::add(ffa::mul(S, S),
-                                    ffa::mul(ffa::F2{-3.0f, 0.0f}, ffa::add(Q, ffa::neg(c))));
-      const ffa::F2 third{__int_as_float(0x3eaaaaab), __int_as_float(static_cast<int>(0xb22aaaabu))};
-      u3 = ffa::mul(ffa::add(S, ffa::sqrt(disc)), third);            // three axes
-      three = s2 < xf::kInf && b2.hi < u2.hi && disc.hi > 0.0f;
-    }
-    if (b1.hi < u1.hi) u = three ? u3 : u2;
+  // b_j = s_j - s0 (+inf when s_j is): exact FP64 differences of close values
+  const ffa::F2 b1 = ffa::split(xf::as_u(__dsub_rn(xf::as_d(s1), xf::as_d(s0))));
+  const ffa::F2 b2 = D > 2 ? ffa::split(xf::as_u(__dsub_rn(xf::as_d(s2), xf::as_d(s0))))
+                           : ffa::F2{__int_as_float(0x7f800000), 0.0f};
+  const float cf = c.hi;
+  const bool two = b1.hi < ffa::sqrt_est(cf);
+  bool three = false;
+  if (D > 2) {
+    const float u2f = __fmul_rn(0.5f, __fadd_rn(b1.hi, ffa::sqrt_est(__fmaf_rn(-b1.hi, b1.hi, __fmul_rn(2.0f, cf)))));
+    const float sf = __fadd_rn(b1.hi, b2.hi);
+    const float qf = __fmaf_rn(b1.hi, b1.hi, __fmul_rn(b2.hi, b2.hi));
+    const float d3 = __fmaf_rn(sf, sf, __fmul_rn(-3.0f, __fsub_rn(qf, cf)));
+    three = two && b2.hi < u2f && d3 > 0.0f;
   }
-  // tau = s0 + (hi + lo) on the FP64 unit: hi + lo as one double (exact, or
-  // within 2^-53 of u when lo is far below hi), then one addition rounded
-  // upward.  d-bar is the double just above the real root, so rounding the
-  // whole sum up once lands on it far more often than rounding s0 + hi to
-  // nearest first (which loses up to half an ulp of tau before lo is added).
+  const ffa::F2 B1 = two ? b1 : ffa::F2{0.0f, 0.0f};
+  const ffa::F2 B2 = three ? b2 : ffa::F2{0.0f, 0.0f};
+  const ffa::F2 S = ffa::add(B1, B2);
+  const ffa::F2 Q = ffa::add(ffa::mul(B1, B1), ffa::mul(B2, B2));
+  const float kf = three ? -3.0f : two ? -2.0f : -1.0f;
+  const ffa::F2 disc = ffa::add(ffa::mul(S, S), ffa::mul(ffa::F2{kf, 0.0f}, ffa::add(Q, ffa::neg(c))));
+  const ffa::F2 inv = three ? ffa::F2{__int_as_float(0x3eaaaaab), __int_as_float(static_cast<int>(0xb22aaaabu))}
+                            : ffa::F2{two ? 0.5f : 1.0f, 0.0f};
+  const ffa::F2 u = ffa::mul(ffa::add(S, ffa::sqrt_nr(disc)), inv);
   const double ud = __dadd_rn(xf::as_d(xf::from_f(u.hi)), xf::as_d(xf::from_f_signed(u.lo)));
   unsigned long long tau = xf::as_u(__dadd_ru(xf::as_d(s0), ud));
   if (!(tau > s0) || tau >= xf::kInf) tau = s0 + 1ull;
