@@ -513,56 +513,16 @@ __device__ __forceinline__ bool neighbour_certified(unsigned long long tau, unsi
   return __fmul_rn(lhs, 1.0001f) < __fmul_rn(rhs, 0.9999f);
 }
 
-// d-bar with the exact G on the FP64 unit: float-float starting point
-// (ffguess), then the exact test G(tau) >= c > G(prev(tau)) with a few ulp
-// steps and bisection as the last resort.  About 13 (2D) FP64 instructions in
-// the common case.
+// The search that finishes d-bar from a point tau and the side of G(tau)
+// (above: G(tau) >= c): walk a few ulps; if the root is farther (float-float
+// carries ~46 bits, too few when tau - s0 is large against tau), one Newton
+// step on G(tau) - c on the FP64 unit, walk again, then bracket and bisect.
 template <int D>
-__device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned long long cb,
-                                   unsigned *path = nullptr) {
+__device__ unsigned long long dbar_search(const unsigned long long (&a)[D], unsigned long long cb,
+                                          unsigned long long tau, bool above, unsigned *path) {
   unsigned long long s0 = a[0];
-  unsigned long long s1 = D > 1 ? a[1] : kInf;
-  unsigned long long s2 = D > 2 ? a[2] : kInf;
-  {
-    const unsigned long long lo = xf::umin(s0, s1), hi = xf::umax(s0, s1);
-    s0 = lo;
-    s1 = hi;
-    if (D > 2) {
-      const unsigned long long l2 = xf::umin(s1, s2), h2 = xf::umax(s1, s2);
-      s2 = h2;
-      s1 = xf::umax(s0, l2);
-      s0 = xf::umin(s0, l2);
-    }
-  }
-  unsigned long long tau = ffguess<D>(a, cb);
-  bool above;
-  if (D == 3) {
-    // G at the starting point first; its side picks the second point: tau - 1
-    // when G(tau) >= c (is tau the smallest?), tau + 1 when G(tau) < c (then
-    // G(tau + 1) >= c makes tau + 1 the smallest).  The float-float starting
-    // point is most often one ulp low in 3D, which this settles without a walk.
-    // The side of the second point is first decided by a rounding-error bound
-    // (no FP64 work); only undecided cells evaluate G there.
-    float msum;
-    const unsigned long long g_here = G_slope<D>(tau, a, msum);
-    const bool ge = g_here >= cb;
-    if (neighbour_certified(tau, g_here, cb, msum, ge)) return ge ? tau : tau + 1ull;
-    const unsigned long long p2 = ge ? tau - 1ull : tau + 1ull;
-    const bool ge2 = G<D>(p2, a) >= cb;
-    if (ge && !ge2) return tau;
-    if (!ge && ge2) return p2;
-    tau = p2;
-    above = ge2;
-  } else {
-    // the exact test at the starting point: two independent G evaluations
-    const unsigned long long g_prev = G<D>(tau - 1ull, a);
-    const unsigned long long g_here = G<D>(tau, a);
-    if (g_here >= cb && g_prev < cb) return tau;
-    above = g_here >= cb;
-  }
-  // walk a few ulps; if the root is farther (float-float carries ~47 bits, too
-  // few when tau - s0 is large against tau), one Newton step on G(tau) - c on
-  // the FP64 unit, walk again, then bracket and bisect
+#pragma unroll
+  for (int k = 1; k < D; ++k) s0 = xf::umin(s0, a[k]);
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     if (above) {
@@ -618,6 +578,60 @@ __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned lo
     if (G<D>(mid, a) >= cb) hi = mid; else lo = mid;
   }
   return hi;
+}
+
+// First stage of the 3D d-bar: G at the starting point t, and the
+// rounding-error bound on t's neighbour on the other side of c.  Returns true
+// with d-bar in `out` when that settles it (t, or t + 1 when G(t) < c);
+// otherwise t and the side of G(t) (ge: G(t) >= c) for dbar_second3.
+__device__ __forceinline__ bool dbar_first3(const unsigned long long (&a)[3], unsigned long long cb,
+                                            unsigned long long &out, unsigned long long &tau, bool &ge) {
+  tau = ffguess<3>(a, cb);
+  float msum;
+  const unsigned long long g_here = G_slope<3>(tau, a, msum);
+  ge = g_here >= cb;
+  if (neighbour_certified(tau, g_here, cb, msum, ge)) {
+    out = ge ? tau : tau + 1ull;
+    return true;
+  }
+  return false;
+}
+
+// Second stage: G at the second point, t - 1 when G(t) >= c (is t the
+// smallest?), t + 1 when G(t) < c (then G(t + 1) >= c makes t + 1 the
+// smallest); the float-float starting point is most often one ulp low in 3D,
+// which this settles without a walk.  Else the search.
+__device__ __forceinline__ unsigned long long dbar_second3(const unsigned long long (&a)[3],
+                                                           unsigned long long cb, unsigned long long tau,
+                                                           bool ge, unsigned *path) {
+  const unsigned long long p2 = ge ? tau - 1ull : tau + 1ull;
+  const bool ge2 = G<3>(p2, a) >= cb;
+  if (ge && !ge2) return tau;
+  if (!ge && ge2) return p2;
+  return dbar_search<3>(a, cb, p2, ge2, path);
+}
+
+// d-bar with the exact G on the FP64 unit: float-float starting point
+// (ffguess), then the exact test G(tau) >= c > G(prev(tau)).  3D: G at the
+// starting point and the rounding-error bound first, G at a second point only
+// when the bound leaves it open.  2D: G at tau and prev(tau), two independent
+// chains.  Then a few ulp steps, Newton and bisection as the last resort.
+// About 13 (2D) FP64 instructions in the common case.
+template <int D>
+__device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned long long cb,
+                                   unsigned *path = nullptr) {
+  if constexpr (D == 3) {
+    unsigned long long out, tau;
+    bool ge;
+    if (dbar_first3(a, cb, out, tau, ge)) return out;
+    return dbar_second3(a, cb, tau, ge, path);
+  } else {
+    const unsigned long long tau = ffguess<D>(a, cb);
+    const unsigned long long g_prev = G<D>(tau - 1ull, a);
+    const unsigned long long g_here = G<D>(tau, a);
+    if (g_here >= cb && g_prev < cb) return tau;
+    return dbar_search<D>(a, cb, tau, g_here >= cb, path);
+  }
 }
 
 template <int D>
