@@ -54,16 +54,16 @@ L2_FLUSH_BYTES = 512 << 20
 # ncu DRAM bytes (read + write) per launch of the persistent kernel in its default
 # configuration, from the one-pass captures summarised in profiles/ (refresh them
 # whenever the kernel changes)
-MEASURED_TRAFFIC = {"layered_2d": 28234752 + 709376, "checker_3d": 279033344 + 108412416}
+MEASURED_TRAFFIC = {"layered_2d": 28471040 + 682240, "checker_3d": 277803520 + 108080384}
 # ncu DRAM bytes of one launch of the 88-problem batch in the default options
 # (the benchmark autotunes, so this is context, not the traffic of the timed launch)
-BATCH_TRAFFIC_DEFAULT_OPTIONS = 11745065984 + 2232886272
+BATCH_TRAFFIC_DEFAULT_OPTIONS = 11741329664 + 2232464896
 
 # FP64 thread instructions (DADD + DMUL + DFMA, ncu sass counters) per operator
 # evaluation of the persistent kernel, by dimension, from one-launch captures
 # summarised in profiles/ (refresh them whenever the kernel changes); None: not
 # measured for this build
-MEASURED_FP64_PER_EVAL = {2: 13.152, 3: 13.035, "batched_3d": 12.70}
+MEASURED_FP64_PER_EVAL = {2: 8.048, 3: 13.039, "batched_3d": 12.701}
 
 WORKLOADS = {
     "layered_2d": "2d_2301x751_layered_h4_1src",

@@ -580,15 +580,17 @@ __device__ unsigned long long dbar_search(const unsigned long long (&a)[D], unsi
   return hi;
 }
 
-// First stage of the 3D d-bar: G at the starting point t, and the
+// First stage of the two-stage d-bar: G at the starting point t, and the
 // rounding-error bound on t's neighbour on the other side of c.  Returns true
 // with d-bar in `out` when that settles it (t, or t + 1 when G(t) < c);
-// otherwise t and the side of G(t) (ge: G(t) >= c) for dbar_second3.
-__device__ __forceinline__ bool dbar_first3(const unsigned long long (&a)[3], unsigned long long cb,
-                                            unsigned long long &out, unsigned long long &tau, bool &ge) {
-  tau = ffguess<3>(a, cb);
+// otherwise t and the side of G(t) (ge: G(t) >= c) for dbar_second.  The bound
+// counts five roundings on any term's path, as in 3D; 2D has fewer.
+template <int D>
+__device__ __forceinline__ bool dbar_first(const unsigned long long (&a)[D], unsigned long long cb,
+                                           unsigned long long &out, unsigned long long &tau, bool &ge) {
+  tau = ffguess<D>(a, cb);
   float msum;
-  const unsigned long long g_here = G_slope<3>(tau, a, msum);
+  const unsigned long long g_here = G_slope<D>(tau, a, msum);
   ge = g_here >= cb;
   if (neighbour_certified(tau, g_here, cb, msum, ge)) {
     out = ge ? tau : tau + 1ull;
@@ -601,37 +603,30 @@ __device__ __forceinline__ bool dbar_first3(const unsigned long long (&a)[3], un
 // smallest?), t + 1 when G(t) < c (then G(t + 1) >= c makes t + 1 the
 // smallest); the float-float starting point is most often one ulp low in 3D,
 // which this settles without a walk.  Else the search.
-__device__ __forceinline__ unsigned long long dbar_second3(const unsigned long long (&a)[3],
-                                                           unsigned long long cb, unsigned long long tau,
-                                                           bool ge, unsigned *path) {
+template <int D>
+__device__ __forceinline__ unsigned long long dbar_second(const unsigned long long (&a)[D],
+                                                          unsigned long long cb, unsigned long long tau,
+                                                          bool ge, unsigned *path) {
   const unsigned long long p2 = ge ? tau - 1ull : tau + 1ull;
-  const bool ge2 = G<3>(p2, a) >= cb;
+  const bool ge2 = G<D>(p2, a) >= cb;
   if (ge && !ge2) return tau;
   if (!ge && ge2) return p2;
-  return dbar_search<3>(a, cb, p2, ge2, path);
+  return dbar_search<D>(a, cb, p2, ge2, path);
 }
 
 // d-bar with the exact G on the FP64 unit: float-float starting point
-// (ffguess), then the exact test G(tau) >= c > G(prev(tau)).  3D: G at the
-// starting point and the rounding-error bound first, G at a second point only
-// when the bound leaves it open.  2D: G at tau and prev(tau), two independent
-// chains.  Then a few ulp steps, Newton and bisection as the last resort.
-// About 13 (2D) FP64 instructions in the common case.
+// (ffguess), then the exact test G(tau) >= c > G(prev(tau)) in two stages: G
+// at the starting point and the rounding-error bound first, G at a second
+// point only when the bound leaves it open; then a few ulp steps, Newton and
+// bisection as the last resort.  About 4 + 8 (3D) / 3 + 5 (2D) FP64
+// instructions when the bound settles it.
 template <int D>
 __device__ unsigned long long dbar(const unsigned long long (&a)[D], unsigned long long cb,
                                    unsigned *path = nullptr) {
-  if constexpr (D == 3) {
-    unsigned long long out, tau;
-    bool ge;
-    if (dbar_first3(a, cb, out, tau, ge)) return out;
-    return dbar_second3(a, cb, tau, ge, path);
-  } else {
-    const unsigned long long tau = ffguess<D>(a, cb);
-    const unsigned long long g_prev = G<D>(tau - 1ull, a);
-    const unsigned long long g_here = G<D>(tau, a);
-    if (g_here >= cb && g_prev < cb) return tau;
-    return dbar_search<D>(a, cb, tau, g_here >= cb, path);
-  }
+  unsigned long long out, tau;
+  bool ge;
+  if (dbar_first<D>(a, cb, out, tau, ge)) return out;
+  return dbar_second<D>(a, cb, tau, ge, path);
 }
 
 template <int D>

@@ -96,7 +96,8 @@ __device__ bool group_ok(const unsigned long long (&a_in)[D], unsigned long long
 }
 
 // counters: 0 sub, 1 sq, 2 add, 3 G2, 4 G3, 5 dbar2, 6 dbar3, 7 group 2D x8,
-// 8 group 3D x8, 9 group 2D x4; [10] trials; [16 + k] first failing trial of check k
+// 8 group 3D x8, 9 group 2D x4, 10 FP64-unit dbar 2D, 11 3D; [15] trials;
+// [16 + k] first failing trial of check k
 __global__ void selftest_kernel(int64_t n, unsigned long long seed, unsigned long long *bad,
                                 unsigned long long *first) {
   // whole warps iterate together (the lane-group checks use warp collectives)
