@@ -688,7 +688,7 @@ def run_batched(args, C, wl_name):
                                           line["roofline"]["kernel"], "batched_3d")
     line["e2e"] = {"value": useful_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                   "call": "eik_solve_batched with pinned host buffers (copies inside the call)",
+                   "call": "eik_solve_batched with pinned host buffers (read and written in place by the library's kernels inside the call)",
                    "capacity_retries": int(sum(e2e_retries))}
     line["gpu_launches"] = int(per_replay * args.steps)
     line["clocks"] = clocks

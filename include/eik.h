@@ -29,8 +29,11 @@
  *
  * Memory: pointer arguments may be device pointers (cudaMalloc, torch CUDA
  * tensors) or host pointers (pageable or pinned); each is classified with
- * cudaPointerGetAttributes.  Host inputs are copied to the device and host
- * outputs copied back inside the call.  The caller owns every buffer it
+ * cudaPointerGetAttributes.  Pinned host memory is mapped into the device's
+ * address space, so the library's kernels read and write it in place over the
+ * chip-to-chip link inside the call.  Speeds are read by the kernel that forms
+ * c; outputs are written by one copy kernel after the solve.  Other host
+ * buffers are copied with cudaMemcpyAsync.  The caller owns every buffer it
  * passes; the library owns its workspace (device scratch sized to the largest
  * problem seen, kept per device until eik_release()).
  *
@@ -184,9 +187,8 @@ eik_status eik_solve(const double *speed, double h, int ndim, const int64_t *dim
                      const int64_t *src_idx, const double *src_t, int64_t nsrc,
                      double *out_t, const eik_opts *opts, eik_stats *stats, void *stream);
 
-/* One problem of a batch.  All pointers of one batch must be of one kind:
- * all device pointers (the batched path does not stage host memory).
- * Problems may share a speed array. */
+/* One problem of a batch.  Each pointer may be a device or a host pointer
+ * (see Memory above).  Problems may share a speed array. */
 typedef struct {
     const double *speed;
     double h;
@@ -379,7 +381,8 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
                         void *stream);
 
 /* Plans: a batch prepared once and solved many times.
- * eik_plan_create checks the problems (device pointers only; all of one ndim),
+ * eik_plan_create checks the problems (device pointers, or pinned host pointers
+ * that each solve reads and writes in place; all of one ndim),
  * copies and de-duplicates their sources, and allocates the plan's own device
  * workspace (synchronous).  eik_plan_enqueue enqueues one complete solve of
  * every problem on `stream` -- constants, initial field, seeds and ONE

@@ -88,6 +88,7 @@ struct Workspace {
   DevBuf<Ctl> ctl;
   DevBuf<unsigned long long> count;
   DevBuf<const double *> sum_ptr;   // eik_sum_ordered's pointer table
+  DevBuf<eik::CopyItem> copies;     // host outputs written by the copy kernel
   DevBuf<double> slab_t;       // eik_solve_slabs: each slab's field (own rows + ghost rows)
   DevBuf<double> slab_x;       // eik_solve_slabs: exchanged boundary rows
   Ctl *ctl_host = nullptr;     // pinned
@@ -98,6 +99,7 @@ struct Workspace {
     r.release(); t_stage.release(); v_stage.release(); state.release(); tile_src.release();
     pend.release();
     slots.release(); seq.release(); src_idx.release(); src_t.release(); seeds.release();
+    copies.release();
     probs.release(); ctl.release(); count.release(); sum_ptr.release(); slab_t.release();
     slab_x.release();
     if (ctl_host) cudaFreeHost(ctl_host);
@@ -219,6 +221,9 @@ bool is_device_ptr(const void *p) {
 
 // Page-locked (pinned or registered) host memory: copies from and to it can
 // be enqueued asynchronously and captured in a CUDA graph.
+#ifndef EIK_MAPPED_COPIES
+#define EIK_MAPPED_COPIES 1
+#endif
 bool is_pinned_host(const void *p) {
   if (!p) return false;
   cudaPointerAttributes a;
@@ -228,6 +233,22 @@ bool is_pinned_host(const void *p) {
     return false;
   }
   return a.type == cudaMemoryTypeHost;
+}
+
+// The device's address of pinned host memory (mapped: with unified addressing
+// all pinned memory is), or NULL when it has none.
+const void *mapped_ptr(const void *host) {
+#if EIK_MAPPED_COPIES
+  void *d = nullptr;
+  if (cudaHostGetDevicePointer(&d, const_cast<void *>(host), 0) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return d;
+#else
+  (void)host;
+  return nullptr;
+#endif
 }
 
 uint64_t next_pow2(uint64_t x) {
@@ -577,7 +598,7 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   for (size_t j = 0; j < speeds.size(); ++j) {
     const HostProblem *owner = nullptr;
     for (size_t i = 0; i < hps.size(); ++i) if (prob_speed[i] == (int)j) { owner = &hps[i]; break; }
-    if (!owner->speed_dev) host_speed_cells += speed_n[j];
+    if (!owner->speed_dev && !mapped_ptr(speeds[j])) host_speed_cells += speed_n[j];
   }
   CK(ws().r.ensure((size_t)r_total), "alloc r");
   CK(ws().src_idx.ensure((size_t)std::max<int64_t>(total_src, 1)), "alloc src_idx");
@@ -664,10 +685,16 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     for (size_t i = 0; i < hps.size(); ++i) if (prob_speed[i] == (int)j) { owner = &hps[i]; break; }
     const double *vsrc = speeds[j];
     if (!owner->speed_dev) {
-      CK(cudaMemcpyAsync(ws().v_stage.p + v_off, vsrc, speed_n[j] * sizeof(double),
-                         cudaMemcpyHostToDevice, stream), "upload speed");
-      vsrc = ws().v_stage.p + v_off;
-      v_off += speed_n[j];
+      // pinned host speeds: init_c reads them in place; else a staged copy
+      const double *m = static_cast<const double *>(mapped_ptr(vsrc));
+      if (m) {
+        vsrc = m;
+      } else {
+        CK(cudaMemcpyAsync(ws().v_stage.p + v_off, vsrc, speed_n[j] * sizeof(double),
+                           cudaMemcpyHostToDevice, stream), "upload speed");
+        vsrc = ws().v_stage.p + v_off;
+        v_off += speed_n[j];
+      }
     }
     CK(eik::launch_init_c(vsrc, speed_h[j], ws().r.p + speed_off[j], speed_n[j], ws().ctl.p, stream,
                           form != 0, from_slowness(opts)), "init_c launch");
@@ -796,12 +823,26 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
     CK(cudaStreamSynchronize(stream), "count");
     acc.good = (int64_t)finite - total_src;
   }
-  // host outputs
+  // host outputs: written by one copy kernel into the mapped pinned buffers
+  // (else a copy per problem)
+  std::vector<eik::CopyItem> items;
+  int64_t max_n = 0;
   for (size_t i = 0; i < hps.size(); ++i) {
-    if (!hps[i].out_dev) {
+    if (hps[i].out_dev) continue;
+    double *m = static_cast<double *>(const_cast<void *>(mapped_ptr(hps[i].out)));
+    if (m) {
+      items.push_back(eik::CopyItem{probs[i].t, m, hps[i].n});
+      max_n = std::max<int64_t>(max_n, hps[i].n);
+    } else {
       CK(cudaMemcpyAsync(hps[i].out, probs[i].t, hps[i].n * sizeof(double), cudaMemcpyDeviceToHost,
                          stream), "download t");
     }
+  }
+  if (!items.empty()) {
+    CK(ws().copies.ensure(items.size()), "alloc copy list");
+    CK(cudaMemcpyAsync(ws().copies.p, items.data(), items.size() * sizeof(eik::CopyItem),
+                       cudaMemcpyHostToDevice, stream), "upload copy list");
+    CK(eik::launch_copy_items(ws().copies.p, (int)items.size(), max_n, stream), "copy launch");
   }
   CK(cudaStreamSynchronize(stream), "download");
   if (stats) *stats = acc;
@@ -1288,9 +1329,14 @@ struct eik_plan {
   int ndim = 2;
   std::vector<Prob> probs;                   // host copies of the device records
   std::vector<const double *> speeds;        // distinct speed arrays (device copies)
-  std::vector<const double *> speed_host;    // their pinned host sources (NULL: device input)
-  std::vector<double *> out_host;            // per problem: pinned host output (NULL: device)
+  std::vector<const double *> speed_host;    // pinned host sources to copy (NULL: device input,
+                                             // or read in place through its mapping)
+  std::vector<double *> out_host;            // per problem: pinned host output to copy (NULL:
+                                             // device, or written by the copy kernel)
   DevBuf<double> v_stage, t_stage;           // device copies of pinned host inputs / outputs
+  DevBuf<eik::CopyItem> copies;              // outputs written through their mapping
+  int ncopies = 0;
+  int64_t copy_max_n = 0;
   std::vector<int64_t> speed_off, speed_n;
   std::vector<double> speed_h;
   int64_t total_tiles = 0, nseeds = 0, total_src = 0, max_cells = 0;
@@ -1314,7 +1360,7 @@ struct eik_plan {
   uint64_t cap = 0;
 
   ~eik_plan() {
-    v_stage.release(); t_stage.release();
+    v_stage.release(); t_stage.release(); copies.release();
     c.release(); state.release(); tile_src.release(); pend.release(); slots.release();
     seq.release(); src_idx.release(); src_t.release(); seeds.release(); probs_d.release(); ctl.release();
     count.release();
@@ -1362,6 +1408,15 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
     }
     prob_speed[i] = found;
   }
+  // pinned host speeds with a device mapping are read in place by init_c
+  for (size_t j = 0; j < pl.speeds.size(); ++j) {
+    if (!pl.speed_host[j]) continue;
+    const double *m = static_cast<const double *>(mapped_ptr(pl.speed_host[j]));
+    if (m) {
+      pl.speeds[j] = m;
+      pl.speed_host[j] = nullptr;
+    }
+  }
   for (auto &hp : hps) pl.total_src += (int64_t)hp.src.size();
   CK(pl.c.ensure((size_t)c_total), "plan: alloc c");
   {  // device copies of pinned host speeds and outputs
@@ -1388,6 +1443,7 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   std::vector<SeedItem> seeds;
   std::vector<int64_t> all_src;
   std::vector<double> all_t0;
+  std::vector<eik::CopyItem> out_items;
   pl.probs.resize(hps.size());
   for (size_t i = 0; i < hps.size(); ++i) {
     HostProblem &hp = hps[i];
@@ -1409,7 +1465,12 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
     } else {
       P.t = pl.t_stage.p + t_off;
       t_off += hp.n;
-      pl.out_host.push_back(hp.out);
+      double *m = static_cast<double *>(const_cast<void *>(mapped_ptr(hp.out)));
+      if (m) {
+        out_items.push_back(eik::CopyItem{P.t, m, hp.n});
+        pl.copy_max_n = std::max<int64_t>(pl.copy_max_n, hp.n);
+      }
+      pl.out_host.push_back(m ? nullptr : hp.out);
     }
     P.src_idx = pl.src_idx.p + all_src.size();
     P.src_t = pl.src_t.p + all_src.size();
@@ -1432,6 +1493,12 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   pl.cap = want_cap;
   CK(pl.slots.ensure((size_t)(want_cap * eik::kNumSlots)), "plan: alloc frontier");
   CK(pl.seq.ensure((size_t)(want_cap * eik::kNumSlots)), "plan: alloc frontier sequence");
+  if (!out_items.empty()) {
+    pl.ncopies = (int)out_items.size();
+    CK(pl.copies.ensure(out_items.size()), "plan: alloc copy list");
+    CK(cudaMemcpyAsync(pl.copies.p, out_items.data(), out_items.size() * sizeof(eik::CopyItem),
+                       cudaMemcpyHostToDevice, stream), "plan: upload copy list");
+  }
   if (!all_src.empty()) {
     CK(cudaMemcpyAsync(pl.src_idx.p, all_src.data(), all_src.size() * sizeof(int64_t),
                        cudaMemcpyHostToDevice, stream), "plan: upload sources");
@@ -1538,6 +1605,8 @@ eik_status eik_plan_enqueue(eik_plan *pl, void *stream) {
   CK(eik::launch_init_t_all(pl->sp.probs, (int)pl->probs.size(), pl->max_cells, s), "init_t launch");
   CK(eik::launch_seed(pl->sp, pl->seeds.p, pl->nseeds, pl->k_delta, pl->delta_fixed, s), "seed launch");
   CK(eik::launch_persistent(pl->sp, pl->grid, s), "solve launch");
+  if (pl->ncopies)
+    CK(eik::launch_copy_items(pl->copies.p, pl->ncopies, pl->copy_max_n, s), "plan: copy launch");
   for (size_t i = 0; i < pl->probs.size(); ++i) {
     if (!pl->out_host[i]) continue;
     const Prob &P = pl->probs[i];

@@ -177,6 +177,17 @@ cudaError_t launch_init_t(double *t, int64_t n, cudaStream_t stream);
 // max_cells: the largest problem's cell count).
 cudaError_t launch_init_t_all(const Prob *dev_probs, int nprob, int64_t max_cells,
                               cudaStream_t stream);
+// One contiguous copy of n doubles; src and dst are device memory or pinned
+// host memory mapped into the device's address space (host <-> device copies
+// run as stores and loads of the SMs over the chip-to-chip link, not on the
+// copy engines).
+struct CopyItem {
+  const double *src;
+  double *dst;
+  int64_t n;
+};
+// All items in one launch (items: device array of nitems; max_n: the largest n).
+cudaError_t launch_copy_items(const CopyItem *items, int nitems, int64_t max_n, cudaStream_t stream);
 // One source of one problem, flattened over the batch for the seed kernel.
 struct SeedItem {
   int64_t prob;

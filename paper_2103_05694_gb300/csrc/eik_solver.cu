@@ -1221,6 +1221,35 @@ cudaError_t launch_init_t_all(const Prob *dev_probs, int nprob, int64_t max_cell
   return cudaGetLastError();
 }
 
+// Item y of the copy list, chunks of 16 bytes where both ends are 16-byte
+// aligned (else 8); blocks of one item stride over it.
+__global__ void copy_items_kernel(const CopyItem *__restrict__ items, int first) {
+  const CopyItem it = items[first + blockIdx.y];
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const bool wide = ((reinterpret_cast<uintptr_t>(it.src) | reinterpret_cast<uintptr_t>(it.dst)) & 15u) == 0u;
+  if (wide) {
+    const int64_t n2 = it.n >> 1;
+    const double2 *s2 = reinterpret_cast<const double2 *>(it.src);
+    double2 *d2 = reinterpret_cast<double2 *>(it.dst);
+    for (int64_t k = i; k < n2; k += stride) d2[k] = s2[k];
+    if ((it.n & 1) && i == 0) it.dst[it.n - 1] = it.src[it.n - 1];
+  } else {
+    for (int64_t k = i; k < it.n; k += stride) it.dst[k] = it.src[k];
+  }
+}
+
+cudaError_t launch_copy_items(const CopyItem *items, int nitems, int64_t max_n, cudaStream_t stream) {
+  if (nitems <= 0 || max_n <= 0) return cudaSuccess;
+  const int gx = per_prob_blocks(nitems, (max_n + 1) / 2);
+  for (int first = 0; first < nitems; first += 65535) {
+    const int ny = nitems - first < 65535 ? nitems - first : 65535;
+    copy_items_kernel<<<dim3(gx, ny), 256, 0, stream>>>(items, first);
+    note_launches(1);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_checksum_all(const Prob *dev_probs, int nprob, int64_t max_cells,
                                unsigned long long *out, cudaStream_t stream) {
   if (nprob <= 0 || max_cells <= 0) return cudaSuccess;
