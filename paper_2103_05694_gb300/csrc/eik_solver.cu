@@ -423,10 +423,22 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 // + 1) * delta are deferred: recorded in the tile's pending mask and the tile
 // re-queued at their bucket.  Only accepted values are written to memory.
 // ---------------------------------------------------------------------------
+#ifndef EIK_LEAN
+#define EIK_LEAN 1
+#endif
 // Register budget: resident_ctas(tile cells) CTAs per SM.
-template <int D, int TX, int TY, int TZ, int ARITH>
+template <int D, int TX, int TY, int TZ, int ARITH, bool LEAN>
 __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     persistent_kernel(SolveParams p) {
+  // LEAN: the instantiation for plain d-bar solves without counters, traces,
+  // lane groups or change tracking (the timed path); those features compile
+  // out of it.
+  const int counters = LEAN ? 0 : p.counters;
+  const int update = LEAN ? 0 : p.update;
+  const int track_changes = LEAN ? 0 : p.track_changes;
+  const bool tracing = !LEAN && p.trace != nullptr;
+  const int lane_group_cells = LEAN ? 0 : p.lane_group_cells;
+  const unsigned long long visit_budget = LEAN ? 0ull : p.visit_budget;
   constexpr int NT = TX * TY * TZ;
   static_assert(NT % 32 == 0 && NT <= 32 * kPendWords, "whole warps, one pending bit per cell");
   constexpr int HZ = (D == 3) ? 1 : 0;
@@ -484,7 +496,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
       long long tile = -1;
       int faces = 0;
       unsigned slot = 0, lo = 0;
-      const long long t_pop = (p.counters || p.trace) ? now_ns() : 0;
+      const long long t_pop = (counters || tracing) ? now_ns() : 0;
 #pragma unroll 1
       for (;;) {
         const unsigned long long e = pop_entry(p, s_stat[13], slot, lo);
@@ -498,12 +510,12 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
         if (tid == 0) {
           atomicAdd(&p.ctl->run[slot * kCounterPad], 0xffffffffu);
           atomicAdd(&p.ctl->work, -1);
-          if (p.counters) atomicAdd(&p.ctl->stats[kStatStale], 1ull);
+          if (counters) atomicAdd(&p.ctl->stats[kStatStale], 1ull);
         }
       }
       if (tid == 0) {
         s_stat[13] = 0;
-        if (p.counters || p.trace) {
+        if (counters || tracing) {
           s_stat[14] = now_ns();
           s_stat[6] += s_stat[14] - t_pop;
         }
@@ -511,7 +523,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
         if (tile >= 0) {
           __threadfence();  // the claim is ordered before the tile's loads
           prob = find_prob(p, static_cast<unsigned long long>(tile));
-          if (p.visit_budget && atomicAdd(&p.ctl->visits_total, 1ull) >= p.visit_budget)
+          if (visit_budget && atomicAdd(&p.ctl->visits_total, 1ull) >= visit_budget)
             raise_status(p.ctl, kEtimeout, 9);   // this visit runs; then every CTA stops
           const double vlim = static_cast<double>(lo + p.window + 1u) * delta;
           s_vlim = bits_of(vlim);
@@ -526,7 +538,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     __syncthreads();
     const long long tile = s_tile;
     if (tile < 0) break;
-    const bool timing = p.counters >= 2 && tid == 0;
+    const bool timing = counters >= 2 && tid == 0;
     if (timing) s_stat[12] = clock64();
     const int faces = s_faces;
     const Prob &P = p.probs[s_prob];
@@ -605,7 +617,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     if (first && tid == 0) {   // band = k * sqrt(c_min) / sqrt(D): one cell's travel time
       const float cm = s_cmin < kInfBits ? xf::to_f(s_cmin) : 0.0f;
       // s_cmin is the smallest c (or r for the explicit roots): one cell's travel time
-      s_band_f = (p.update ? cm : sqrtf(cm)) * band_scale;
+      s_band_f = (update ? cm : sqrtf(cm)) * band_scale;
       s_cmin = kInfBits;
     }
     vlim = s_vlim;
@@ -692,8 +704,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
       // change tracking compares with the cell's value (a recomputed value may
       // also be larger); otherwise a candidate must beat value and pending
       const unsigned long long best =
-          p.track_changes ? bits_of(tv) : umin64(bits_of(tv), is_pending(pv, bits_of(tv)) ? pv : kInfBits);
-      if (p.update) {
+          track_changes ? bits_of(tv) : umin64(bits_of(tv), is_pending(pv, bits_of(tv)) ? pv : kInfBits);
+      if (update) {
         // the explicit forms (not monotone): any neighbour change re-evaluates
         if (accept) need = active && (cxl || cxr || cyl || cyr || czl || czr);
       } else if (accept) {
@@ -719,14 +731,14 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
         unsigned long long amin = a[0];
 #pragma unroll
         for (int k = 1; k < D; ++k) amin = umin64(amin, a[k]);
-        go = amin < kInfBits && (p.track_changes || best > amin);
+        go = amin < kInfBits && (track_changes || best > amin);
         if (go) {
 #pragma unroll
           for (int k = 0; k < D; ++k) s_a[k][tid] = a[k];
           s_best[tid] = best;
         }
       }
-      if (p.counters) {   // evaluations and acceptances of this round (warp-aggregated)
+      if (counters) {   // evaluations and acceptances of this round (warp-aggregated)
         const unsigned ev = __ballot_sync(kFull, need);
         if (lane == 0 && (ev | accbits)) {
           atomicAdd(reinterpret_cast<unsigned long long *>(&s_stat[0]), static_cast<unsigned long long>(__popc(ev)));
@@ -743,7 +755,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
       }
       __syncthreads();                                              // barrier 1
       if (timing) lap(s_stat, 8);
-      // (B) dense arithmetic phase.  Few cells (at most p.lane_group_cells): a
+      // (B) dense arithmetic phase.  Few cells (at most lane_group_cells): a
       //     group of 8 (or 4) lanes per cell evaluates d-bar (guess + one G
       //     pass over a window of points); else one lane per cell.  Only warps
       //     holding work take part.
@@ -755,7 +767,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
         }
         unsigned long long nv = kInfBits;
         bool part = false;
-        if (ARITH == kArithFp64 && cnt <= p.lane_group_cells && cnt * 4 <= NT && !p.update) {
+        if (ARITH == kArithFp64 && cnt <= lane_group_cells && cnt * 4 <= NT && !update) {
           const int L = cnt * 8 <= NT ? 8 : 4;
           if (warp < (cnt * L + 31) / 32) {
             part = true;
@@ -783,9 +795,9 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
 #pragma unroll
             for (int k = 0; k < D; ++k) a[k] = s_a[k][c];
             bool dec;
-            if (D == 2 && p.update) {   // explicit roots: s_c holds r = fl(h/v)
-              nv = forms::explicit_update(p.update, a[0], a[D - 1], from_bits(s_c[c]));
-              if (p.track_changes) {    // the latest value replaces any pending one
+            if (D == 2 && update) {   // explicit roots: s_c holds r = fl(h/v)
+              nv = forms::explicit_update(update, a[0], a[D - 1], from_bits(s_c[c]));
+              if (track_changes) {    // the latest value replaces any pending one
                 dec = nv != s_best[c];
                 if (!dec) s_pv[c] = kInfBits;
               } else {
@@ -794,7 +806,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
             } else {
               dec = ARITH == kArithInt ? xf::relax<D>(s_best[c], a, s_c[c], nv)
                                        : hw::relax<D>(s_best[c], a, s_c[c], nv,
-                                                      p.counters >= 2 ? s_path : nullptr);
+                                                      counters >= 2 ? s_path : nullptr);
             }
             if (dec) s_pv[c] = nv; else nv = kInfBits;
           }
@@ -815,9 +827,9 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     ++R;
 
     // commit and collect the smallest committed time per tile face
-    const bool track = p.track_changes != 0;
+    const bool track = track_changes != 0;
     const bool commit = track ? bits_of(tv) != bits_of(tv0) : bits_of(tv) < bits_of(tv0);
-    if (p.counters) {
+    if (counters) {
       const unsigned cm = __ballot_sync(kFull, commit);
       if (lane == 0 && cm)
         atomicAdd(reinterpret_cast<unsigned long long *>(&s_stat[2]), static_cast<unsigned long long>(__popc(cm)));
@@ -918,8 +930,8 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
       atomicAdd(&p.ctl->work, -1);
       s_stat[3] += 1;
       s_stat[4] += rounds;
-      if (p.counters) s_stat[5] += now_ns() - s_stat[14];
-      if (p.trace) {
+      if (counters) s_stat[5] += now_ns() - s_stat[14];
+      if (tracing) {
         const unsigned long long k = atomicAdd(&p.ctl->trace_n, 1ull);
         if (k < p.trace_cap) {
           TraceRec rec;
@@ -935,7 +947,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     }
   }
 
-  if (p.counters) {
+  if (counters) {
     __syncthreads();
     if (tid == 0) {
       const unsigned long long *st = reinterpret_cast<const unsigned long long *>(s_stat);
@@ -946,7 +958,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
       atomicAdd(&p.ctl->stats[kStatRounds], st[4]);
       atomicAdd(&p.ctl->stats[kStatVisitNs], st[5]);
       atomicAdd(&p.ctl->stats[kStatIdleNs], st[6]);
-      if (p.counters >= 2) {
+      if (counters >= 2) {
 #pragma unroll
         for (int k = 0; k < 5; ++k) atomicAdd(&p.ctl->stats[kStatCycLoad + k], st[7 + k]);
 #pragma unroll
@@ -1311,24 +1323,29 @@ struct ShapeOps {
     if constexpr (WithInt) {
       if (arith == kArithInt) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &nb, persistent_kernel<D, TX, TY, TZ, kArithInt>, TX * TY * TZ, 0);
+            &nb, persistent_kernel<D, TX, TY, TZ, kArithInt, false>, TX * TY * TZ, 0);
         return nb;
       }
     }
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persistent_kernel<D, TX, TY, TZ, kArithFp64>,
-                                                  TX * TY * TZ, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &nb, persistent_kernel<D, TX, TY, TZ, kArithFp64, false>, TX * TY * TZ, 0);
     return nb;
   }
   static cudaError_t launch(const SolveParams &p, int grid, cudaStream_t stream) {
     if (p.arith == kArithInt) {
       if constexpr (WithInt) {
-        persistent_kernel<D, TX, TY, TZ, kArithInt><<<grid, TX * TY * TZ, 0, stream>>>(p);
+        persistent_kernel<D, TX, TY, TZ, kArithInt, false><<<grid, TX * TY * TZ, 0, stream>>>(p);
         return cudaGetLastError();
       } else {
         return cudaErrorInvalidValue;
       }
     }
-    persistent_kernel<D, TX, TY, TZ, kArithFp64><<<grid, TX * TY * TZ, 0, stream>>>(p);
+    const bool lean = EIK_LEAN && p.counters == 0 && p.update == 0 && !p.track_changes &&
+                      p.lane_group_cells == 0 && p.trace == nullptr && p.visit_budget == 0ull;
+    if (lean)
+      persistent_kernel<D, TX, TY, TZ, kArithFp64, true><<<grid, TX * TY * TZ, 0, stream>>>(p);
+    else
+      persistent_kernel<D, TX, TY, TZ, kArithFp64, false><<<grid, TX * TY * TZ, 0, stream>>>(p);
     return cudaGetLastError();
   }
 };
