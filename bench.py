@@ -52,17 +52,18 @@ UNIT = "updates/s"
 B_ALG = 24          # algorithmic bytes per useful update: read c once, read t once, write t once
 L2_FLUSH_BYTES = 512 << 20
 # ncu DRAM bytes (read + write) per launch of the persistent kernel in its default
-# configuration, from the one-pass captures summarised in profiles/ (refresh them
-# whenever the kernel changes)
-MEASURED_TRAFFIC = {"layered_2d": 28471040 + 682240, "checker_3d": 277803520 + 108080384}
+# configuration (the instantiation the timed steps run), from the one-pass
+# captures summarised in profiles/ (refresh them whenever the kernel changes)
+MEASURED_TRAFFIC = {"layered_2d": 28197632 + 660480, "checker_3d": 278078208 + 108945408}
 # ncu DRAM bytes of one launch of the 88-problem batch in the default options
 # (the benchmark autotunes, so this is context, not the traffic of the timed launch)
-BATCH_TRAFFIC_DEFAULT_OPTIONS = 11741329664 + 2232464896
+BATCH_TRAFFIC_DEFAULT_OPTIONS = 11769364736 + 2232731648
 
 # FP64 thread instructions (DADD + DMUL + DFMA, ncu sass counters) per operator
-# evaluation of the persistent kernel, by dimension, from one-launch captures
-# summarised in profiles/ (refresh them whenever the kernel changes); None: not
-# measured for this build
+# evaluation of the persistent kernel, by dimension, from one-launch captures of
+# the counting instantiation (whose evaluation count comes from the same launch;
+# the timed instantiation runs the same d-bar code), summarised in profiles/
+# (refresh them whenever the kernel changes)
 MEASURED_FP64_PER_EVAL = {2: 8.048, 3: 13.039, "batched_3d": 12.701}
 
 WORKLOADS = {

@@ -285,9 +285,10 @@ eik_status eik_solve_noalloc(const double *speed, double h, int ndim, const int6
  * (eik_release frees it).
  * Synchronises `stream`.  stats (optional): good = cells processed, evals =
  * reached cells, solve_ms = device time of the adjoint launches; tiles: visits
- * = tile visits, rounds = in-tile rounds summed over visits, visit_ns /
- * idle_ns = CTA time in visits / waiting for a tile, ctas, detail[0..3] = SM
- * cycles (thread 0 of each CTA, summed) waiting, loading, in rounds, storing;
+ * = tile visits, rounds = in-tile rounds summed over visits, ctas; with
+ * opts->counters also visit_ns / idle_ns = CTA time in visits / waiting for a
+ * tile and detail[0..3] = SM cycles (thread 0 of each CTA, summed) waiting,
+ * loading, in rounds, storing (a build of the kernel with these clocks);
  * levels: rounds = levels. */
 eik_status eik_adjoint(const eik_problem *probs, int nprob, const double *const *dL_dt,
                        double *const *dL_dslowness, const eik_opts *opts, eik_stats *stats,

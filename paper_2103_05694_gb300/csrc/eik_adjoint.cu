@@ -458,7 +458,9 @@ __global__ void adj_tile_seed_kernel(const AdjProb *probs, int nprob, int64_t to
 #ifndef EIK_ADJ_TILE_MINB
 #define EIK_ADJ_TILE_MINB 4
 #endif
-template <int D, int TX, int TY, int TZ>
+// TIMING: per-CTA clocks of the visit phases and of the waits for work (the
+// eik_stats timing fields); without it those reads compile out.
+template <int D, int TX, int TY, int TZ, bool TIMING>
 __global__ void __launch_bounds__(TX * TY * TZ, (EIK_ADJ_TILE_MINB * 256 + TX * TY * TZ - 1) /
                                                      (TX * TY * TZ)) adj_tiles_kernel(
     const AdjProb *probs, int nprob, TileQueue q) {
@@ -487,11 +489,16 @@ __global__ void __launch_bounds__(TX * TY * TZ, (EIK_ADJ_TILE_MINB * 256 + TX * 
 #pragma unroll 1
   for (;;) {
     if (tid == 0) {
-      c0 = clock64();
-      const long long t_wait = grid::now_ns();
+      long long t_wait = 0;
+      if constexpr (TIMING) {
+        c0 = clock64();
+        t_wait = grid::now_ns();
+      }
       long long tile = tq_pop(q, reached);
-      t_claim = grid::now_ns();
-      idle_ns += static_cast<unsigned long long>(t_claim - t_wait);
+      if constexpr (TIMING) {
+        t_claim = grid::now_ns();
+        idle_ns += static_cast<unsigned long long>(t_claim - t_wait);
+      }
       int pi = 0;
       if (tile >= 0) {
         // queued -> being visited; activations from now on set bit 0 again
@@ -506,9 +513,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, (EIK_ADJ_TILE_MINB * 256 + TX * 
       s_tile = tile;
       s_prob = pi;
       s_n[0] = s_n[1] = s_n[2] = 0;
-      const long long c1 = clock64();
-      cyc[0] += static_cast<unsigned long long>(c1 - c0);
-      c0 = c1;
+      if constexpr (TIMING) {
+        const long long c1 = clock64();
+        cyc[0] += static_cast<unsigned long long>(c1 - c0);
+        c0 = c1;
+      }
     }
     __syncthreads();
     const long long tile = s_tile;
@@ -567,7 +576,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (EIK_ADJ_TILE_MINB * 256 + TX * 
     if (out_clear && cnt0 == 0) s_list[0][atomicAdd(&s_n[0], 1)] = static_cast<unsigned short>(tid);
     }
     __syncthreads();
-    if (tid == 0) {
+    if (TIMING && tid == 0) {
       const long long c1 = clock64();
       cyc[1] += static_cast<unsigned long long>(c1 - c0);
       c0 = c1;
@@ -658,7 +667,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (EIK_ADJ_TILE_MINB * 256 + TX * 
       }
       __syncthreads();
     }
-    if (tid == 0) {
+    if (TIMING && tid == 0) {
       const long long c1 = clock64();
       cyc[2] += static_cast<unsigned long long>(c1 - c0);
       c0 = c1;
@@ -711,7 +720,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, (EIK_ADJ_TILE_MINB * 256 + TX * 
         }
       }
     }
-    if (tid == 0) {
+    if (TIMING && tid == 0) {
       visit_ns += static_cast<unsigned long long>(grid::now_ns() - t_claim);
       cyc[3] += static_cast<unsigned long long>(clock64() - c0);
     }
@@ -719,11 +728,13 @@ __global__ void __launch_bounds__(TX * TY * TZ, (EIK_ADJ_TILE_MINB * 256 + TX * 
   if (tid == 0) {
     atomicAdd(&q.ctl->visits, visits);
     atomicAdd(&q.ctl->rounds, rounds);
-    atomicAdd(&q.ctl->visit_ns, visit_ns);
-    atomicAdd(&q.ctl->idle_ns, idle_ns);
     atomicAdd(&q.ctl->ctas, 1ull);
+    if constexpr (TIMING) {
+      atomicAdd(&q.ctl->visit_ns, visit_ns);
+      atomicAdd(&q.ctl->idle_ns, idle_ns);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) atomicAdd(&q.ctl->cycles[i], cyc[i]);
+      for (int i = 0; i < 4; ++i) atomicAdd(&q.ctl->cycles[i], cyc[i]);
+    }
   }
 }
 
@@ -776,7 +787,8 @@ namespace {
 
 template <int D, int TX, int TY, int TZ>
 cudaError_t run_tiles(const AdjProb *probs_dev, int nprob, int64_t total, int64_t total_tiles,
-                      TileQueue q, unsigned long long qcap, int ctas_per_sm, cudaStream_t stream) {
+                      TileQueue q, unsigned long long qcap, int ctas_per_sm, bool timing,
+                      cudaStream_t stream) {
   int64_t g = (total + 255) / 256;
   if (g > 8 * sms()) g = 8 * sms();
   if (g < 1) g = 1;
@@ -792,7 +804,7 @@ cudaError_t run_tiles(const AdjProb *probs_dev, int nprob, int64_t total, int64_
   // CTA waits for tiles that running CTAs queue
   constexpr int NT = TX * TY * TZ;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_tiles_kernel<D, TX, TY, TZ>, NT, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_tiles_kernel<D, TX, TY, TZ, true>, NT, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   if (ctas_per_sm > 0 && per_sm > ctas_per_sm) per_sm = ctas_per_sm;
@@ -800,8 +812,9 @@ cudaError_t run_tiles(const AdjProb *probs_dev, int nprob, int64_t total, int64_
   if (blocks > total_tiles) blocks = total_tiles;
   if (blocks < 1) blocks = 1;
   void *args[] = {const_cast<AdjProb **>(&probs_dev), &nprob, &q};
-  e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(adj_tiles_kernel<D, TX, TY, TZ>),
-                                  dim3(static_cast<unsigned>(blocks)), dim3(NT), args, 0, stream);
+  const void *fn = timing ? reinterpret_cast<const void *>(adj_tiles_kernel<D, TX, TY, TZ, true>)
+                          : reinterpret_cast<const void *>(adj_tiles_kernel<D, TX, TY, TZ, false>);
+  e = cudaLaunchCooperativeKernel(fn, dim3(static_cast<unsigned>(blocks)), dim3(NT), args, 0, stream);
   note_launches(1);
   return e;
 }
@@ -811,7 +824,8 @@ cudaError_t run_tiles(const AdjProb *probs_dev, int nprob, int64_t total, int64_
 cudaError_t launch_adjoint_tiles(const AdjProb *probs_dev, int nprob, int64_t total,
                                  int64_t total_tiles, int ndim, AdjCtl *ctl, unsigned *tile_state,
                                  unsigned long long *queue, unsigned long long qcap,
-                                 int ctas_per_sm, long long timeout_ns, cudaStream_t stream) {
+                                 int ctas_per_sm, long long timeout_ns, bool timing,
+                                 cudaStream_t stream) {
   if (total_tiles < 1 || qcap < static_cast<unsigned long long>(total_tiles) || (qcap & (qcap - 1)))
     return cudaErrorInvalidValue;
   TileQueue q;
@@ -822,9 +836,9 @@ cudaError_t launch_adjoint_tiles(const AdjProb *probs_dev, int nprob, int64_t to
   q.timeout_ns = timeout_ns;
   if (ndim == 3)
     return run_tiles<3, kAdjTile3[0], kAdjTile3[1], kAdjTile3[2]>(probs_dev, nprob, total, total_tiles,
-                                                                  q, qcap, ctas_per_sm, stream);
+                                                                  q, qcap, ctas_per_sm, timing, stream);
   return run_tiles<2, kAdjTile2[0], kAdjTile2[1], kAdjTile2[2]>(probs_dev, nprob, total, total_tiles,
-                                                                q, qcap, ctas_per_sm, stream);
+                                                                q, qcap, ctas_per_sm, timing, stream);
 }
 
 }  // namespace eik

@@ -1799,7 +1799,8 @@ extern "C" eik_status eik_adjoint(const eik_problem *probs, int nprob, const dou
   if (tiles)
     CK(eik::launch_adjoint_tiles(adj().probs.p, nprob, total, total_tiles, hps[0].ndim, adj().ctl.p,
                                  adj().tile_state.p, adj().ring.p, qcap,
-                                 opts ? opts->ctas_per_sm : 0, tmo_ms * 1000000ll, s),
+                                 opts ? opts->ctas_per_sm : 0, tmo_ms * 1000000ll,
+                                 opts && opts->counters, s),
        "adjoint launch");
   else
     CK(eik::launch_adjoint(adj().probs.p, nprob, total, adj().ctl.p, adj().front.p,

@@ -327,9 +327,11 @@ cudaError_t launch_adjoint(const AdjProb *probs_dev, int nprob, int64_t total, A
 #endif
 constexpr int kAdjTile2[3] = {EIK_ADJ_TILE2_X, EIK_ADJ_TILE2_Y, 1};
 constexpr int kAdjTile3[3] = {8, 8, 4};
+// timing: collect the visit and wait clocks (eik_stats timing fields).
 cudaError_t launch_adjoint_tiles(const AdjProb *probs_dev, int nprob, int64_t total,
                                  int64_t total_tiles, int ndim, AdjCtl *ctl, unsigned *tile_state,
                                  unsigned long long *queue, unsigned long long qcap,
-                                 int ctas_per_sm, long long timeout_ns, cudaStream_t stream);
+                                 int ctas_per_sm, long long timeout_ns, bool timing,
+                                 cudaStream_t stream);
 
 }  // namespace eik
