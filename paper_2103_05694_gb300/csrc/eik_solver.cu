@@ -423,9 +423,6 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 // + 1) * delta are deferred: recorded in the tile's pending mask and the tile
 // re-queued at their bucket.  Only accepted values are written to memory.
 // ---------------------------------------------------------------------------
-#ifndef EIK_LEAN
-#define EIK_LEAN 1
-#endif
 // Register budget: resident_ctas(tile cells) CTAs per SM.
 template <int D, int TX, int TY, int TZ, int ARITH, bool LEAN>
 __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
@@ -695,7 +692,20 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
         return old;
       };
       bool cyl, cyr, czl = false, czr = false;
-      const double yl = across(0, -1, -TX, ly > 0, cyl), yr = across(0, 1, TX, ly < TY - 1, cyr);
+      double yl, yr;
+      if constexpr (D == 3 && TX * TY <= 32) {
+        // whole xy-slices per warp: the y neighbours inside the tile are lanes
+        // +-TX of this warp (their values after the acceptance, and whether they
+        // changed), the others the halo
+        const double ys_l = __shfl_up_sync(kFull, tv, TX), ys_r = __shfl_down_sync(kFull, tv, TX);
+        cyl = ly > 0 && ((accbits >> (lane - TX)) & 1u);
+        cyr = ly < TY - 1 && ((accbits >> (lane + TX)) & 1u);
+        yl = ly > 0 ? ys_l : s_t[accept ? bo : b][zc][yc - 1][xc];
+        yr = ly < TY - 1 ? ys_r : s_t[accept ? bo : b][zc][yc + 1][xc];
+      } else {
+        yl = across(0, -1, -TX, ly > 0, cyl);
+        yr = across(0, 1, TX, ly < TY - 1, cyr);
+      }
       double zl = 0.0, zr = 0.0;
       if constexpr (D == 3) {
         zl = across(-1, 0, -TX * TY, lz > 0, czl);
@@ -1340,7 +1350,7 @@ struct ShapeOps {
         return cudaErrorInvalidValue;
       }
     }
-    const bool lean = EIK_LEAN && p.counters == 0 && p.update == 0 && !p.track_changes &&
+    const bool lean = p.counters == 0 && p.update == 0 && !p.track_changes &&
                       p.lane_group_cells == 0 && p.trace == nullptr && p.visit_budget == 0ull;
     if (lean)
       persistent_kernel<D, TX, TY, TZ, kArithFp64, true><<<grid, TX * TY * TZ, 0, stream>>>(p);
