@@ -54,17 +54,17 @@ L2_FLUSH_BYTES = 512 << 20
 # ncu DRAM bytes (read + write) per launch of the persistent kernel in its default
 # configuration (the instantiation the timed steps run), from the one-pass
 # captures summarised in profiles/ (refresh them whenever the kernel changes)
-MEASURED_TRAFFIC = {"layered_2d": 28197632 + 660480, "checker_3d": 278522624 + 109242112}
+MEASURED_TRAFFIC = {"layered_2d": 28197632 + 660480, "checker_3d": 283740928 + 117722880}
 # ncu DRAM bytes of one launch of the 88-problem batch in the default options
 # (the benchmark autotunes, so this is context, not the traffic of the timed launch)
-BATCH_TRAFFIC_DEFAULT_OPTIONS = 11766868992 + 2232635392
+BATCH_TRAFFIC_DEFAULT_OPTIONS = 16184324096 + 2496584192
 
 # FP64 thread instructions (DADD + DMUL + DFMA, ncu sass counters) per operator
 # evaluation of the persistent kernel, by dimension, from one-launch captures of
 # the counting instantiation (whose evaluation count comes from the same launch;
 # the timed instantiation runs the same d-bar code), summarised in profiles/
 # (refresh them whenever the kernel changes)
-MEASURED_FP64_PER_EVAL = {2: 8.048, 3: 13.039, "batched_3d": 12.701}
+MEASURED_FP64_PER_EVAL = {2: 8.048, 3: 12.971, "batched_3d": 12.717}
 
 WORKLOADS = {
     "layered_2d": "2d_2301x751_layered_h4_1src",
@@ -843,7 +843,7 @@ def main():
     ap.add_argument("--window", type=int, default=0)
     ap.add_argument("--band", type=float, default=0.0)
     ap.add_argument("--tile", type=int, default=0,
-                    help="tile shape 1-4 (see eik_opts.tile); 0: automatic")
+                    help="tile shape 1-5 (see eik_opts.tile); 0: automatic")
     ap.add_argument("--schedule", type=int, default=0,
                     help="single grids: 1 = fast iterative method (Algorithm 3), 2 = "
                          "topology-driven (Algorithm 4), 3 = fast sweeping (Algorithm 5); "

@@ -75,7 +75,10 @@ typedef enum {
  *     band 16, 1 CTA per SM (latency-bound: one front);
  *   2D, 8 or more sources: 16x8 tiles, k_delta 4, window 16, band 8, 8 CTAs of
  *     128 threads per SM;
- *   3D: 8x4x4 tiles, k_delta 0.75, window 31, band 6, 8 CTAs of 128 threads per SM.
+ *   3D, fewer than 8 sources: 4x4x4 tiles, k_delta 0.75, window 31, band 6, 14 CTAs
+ *     of 64 threads per SM;
+ *   3D, 8 or more sources: 4x4x4 tiles, k_delta 0.375, window 31, band 6, 16 CTAs
+ *     of 64 threads per SM.
  * (The per-CTA work is latency-bound, so the kernel is compiled for as many
  * resident CTAs as registers allow: 2 per SM for 256-cell tiles, 8 for 128-cell
  * tiles, 16 for 64-cell tiles.)

@@ -39,7 +39,7 @@ class EikOpts(ctypes.Structure):
                 ("schedule", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 # opts["tile"] = k (1..5) selects TILE_SHAPES[ndim][k - 1]; 0 is automatic (16x16 for
-# one 2D front, 16x8 for 2D batches of 8 or more sources, 8x4x4 in 3D)
+# one 2D front, 16x8 for 2D batches of 8 or more sources, 4x4x4 in 3D)
 TILE_SHAPES = {2: [(16, 16), (32, 8), (32, 4), (16, 8), (16, 4)],
                3: [(8, 8, 4), (16, 4, 4), (32, 4, 2), (8, 4, 4), (4, 4, 4)]}
 

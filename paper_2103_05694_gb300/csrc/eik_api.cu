@@ -40,10 +40,20 @@ constexpr uint64_t kMaxCapEntries = uint64_t(1) << 30;   // whole ring storage l
 // and tomography workloads and the 3D checkerboard and batched workloads.
 // adjoint schedule by default: the tile schedule (else level-synchronous)
 constexpr bool kAdjTilesDefault = true;
-constexpr double kDefaultKDelta[2] = {16.0, 2.0};
+constexpr double kDefaultKDelta[2] = {16.0, 2.0};   // single 2D front, 3D integer d-bar
 constexpr int kDefaultWindow[2] = {16, 31};      // single 2D front, 3D (2D batches: 16)
 constexpr double kDefaultBand[2] = {16.0, 6.0};  // single 2D front, 3D (2D batches: 8)
 constexpr int kDefaultCtasPerSm[2] = {1, 2};   // per 256 cells of tile (single 2D front)
+// 3D on the FP64 unit: 4x4x4 tiles; a single front (under 8 sources) takes
+// buckets of 0.75 cell travel times and 14 CTAs of 64 cells per SM, many
+// fronts (a batch) buckets of 0.375 and all 16 CTAs that fit.  A single
+// front's extra CTAs pick up tiles ahead of it and redo them; a batch has
+// enough independent fronts to keep them busy, and narrow buckets cut its
+// speculative evaluations.
+constexpr int kShape3 = 4;
+constexpr double kKDelta3[2] = {0.75, 0.375};   // single front, many fronts
+constexpr int kSingleFrontCtas3Small = 14;      // 3D tiles of at most 64 cells
+constexpr int kManyFronts = 8;                  // sources at which a solve counts as many fronts
 constexpr int kMaxRetries = 4;
 // eik_opts.sched_flags bits of the tomography interface
 constexpr int kFlagSlowness = 1 << 6;     // speed arrays hold slowness s; v = fl(1/s) is used
@@ -348,8 +358,9 @@ struct AutoCfg {
 };
 AutoCfg auto_config(int ndim, int64_t total_sources, bool int_arith) {
   if (int_arith) return {0, kDefaultKDelta[ndim == 3 ? 1 : 0], ndim == 3 ? 8.0 : 16.0, 16};
-  if (ndim == 3) return {3, 0.75, kDefaultBand[1], kDefaultWindow[1]};
-  if (total_sources >= 8) return {3, 4.0, 8.0, 16};
+  if (ndim == 3)
+    return {kShape3, kKDelta3[total_sources >= kManyFronts ? 1 : 0], kDefaultBand[1], kDefaultWindow[1]};
+  if (total_sources >= kManyFronts) return {3, 4.0, 8.0, 16};
   return {0, kDefaultKDelta[0], kDefaultBand[0], kDefaultWindow[0]};
 }
 
@@ -415,7 +426,11 @@ int lane_group_cells(const eik_opts *opts, int64_t tile_cells, int64_t total_til
 int default_ctas_per_sm(int di, int64_t tile_cells, int64_t total_sources) {
   // one 2D front is latency-bound on few tiles: one CTA per SM; otherwise as
   // many CTAs as the register budget of the tile size allows
-  if (di == 0 && total_sources < 8) return (int)std::max<int64_t>(1, kDefaultCtasPerSm[0] * 256 / tile_cells);
+  if (di == 0 && total_sources < kManyFronts)
+    return (int)std::max<int64_t>(1, kDefaultCtasPerSm[0] * 256 / tile_cells);
+  // one 3D front on 64-cell tiles: a little short of the register budget
+  if (di == 1 && total_sources < kManyFronts && tile_cells <= 64)
+    return std::min(kSingleFrontCtas3Small, eik::resident_ctas((int)tile_cells));
   return eik::resident_ctas((int)tile_cells);
 }
 
@@ -975,7 +990,7 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
   double best_ms = 0;
   eik_status st = trial(cur, best_ms);
   if (st != EIK_OK) { if (ntrials) *ntrials = std::min(n, max_trials); return st; }
-  static const double kds[] = {0.5, 0.75, 1, 2, 4, 8, 16, 32};
+  static const double kds[] = {0.25, 0.375, 0.5, 0.75, 1, 2, 4, 8, 16, 32};
   static const int wins[] = {1, 2, 4, 8, 16, 24, 31};
   static const double bands[] = {1, 2, 4, 6, 8, 12, 16};
   constexpr double kGain = 0.01;   // a change must save more than 1 %
