@@ -464,6 +464,15 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
   // [14] claim time; s_path: d-bar path counts (counters >= 2)
   __shared__ long long s_stat[15];
   __shared__ unsigned s_path[4];
+  // the claimed tile's geometry (thread 0 writes it with the claim) and the
+  // solve's bucket and band scalars, in shared memory so that no thread
+  // carries them in registers through the rounds: the grid's time array,
+  // extents, tiles per axis, the tile's coordinates and the problem's first
+  // global tile id
+  __shared__ double *s_T;
+  __shared__ long long s_n[3], s_nt[3], s_tc[3], s_tbase;
+  __shared__ double s_delta;
+  __shared__ float s_inv_delta, s_band_scale;
 
   const int tid = threadIdx.x;
   const unsigned lane = tid & 31;
@@ -474,9 +483,11 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
   if (tid == 0) { s_cmin = kInfBits; s_min[0] = s_min[1] = s_min[2] = kInfBits; s_cnt[0] = s_cnt[1] = 0; }
   if (tid < 15) s_stat[tid] = 0;
   if (tid < 4) s_path[tid] = 0u;
-  const double delta = p.ctl->delta;
-  const float inv_delta = static_cast<float>(p.ctl->inv_delta);
-  const float band_scale = static_cast<float>(p.band) * rsqrtf(static_cast<float>(D));
+  if (tid == 0) {
+    s_delta = p.ctl->delta;
+    s_inv_delta = static_cast<float>(p.ctl->inv_delta);
+    s_band_scale = static_cast<float>(p.band) * rsqrtf(static_cast<float>(D));
+  }
   if (p.test_stall && tid == 0) {   // testing aid: wait on a flag nothing sets
     const long long t0 = now_ns();
     while (ld_rlx(&p.ctl->never_set) == 0u) {
@@ -522,8 +533,16 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
           prob = find_prob(p, static_cast<unsigned long long>(tile));
           if (visit_budget && atomicAdd(&p.ctl->visits_total, 1ull) >= visit_budget)
             raise_status(p.ctl, kEtimeout, 9);   // this visit runs; then every CTA stops
-          const double vlim = static_cast<double>(lo + p.window + 1u) * delta;
+          const double vlim = static_cast<double>(lo + p.window + 1u) * s_delta;
           s_vlim = bits_of(vlim);
+          const Prob &P = p.probs[prob];
+          const long long lt = tile - P.tile_base;
+          const long long rest = lt / P.ntx;
+          s_T = P.t;
+          s_n[0] = P.nx; s_n[1] = P.ny; s_n[2] = P.nz;
+          s_nt[0] = P.ntx; s_nt[1] = P.nty; s_nt[2] = P.ntz;
+          s_tc[0] = lt % P.ntx; s_tc[1] = rest % P.nty; s_tc[2] = rest / P.nty;
+          s_tbase = P.tile_base;
         }
         s_tile = tile;
         s_faces = faces;
@@ -538,23 +557,25 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     const bool timing = counters >= 2 && tid == 0;
     if (timing) s_stat[12] = clock64();
     const int faces = s_faces;
-    const Prob &P = p.probs[s_prob];
-    double *const T = P.t;
-    const int64_t nx = P.nx, ny = P.ny, nz = P.nz;
-    const int64_t lt = tile - P.tile_base;
-    const int64_t tx = lt % P.ntx, rest = lt / P.ntx;
-    const int64_t ty = rest % P.nty, tz = rest / P.nty;
-    const int64_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
-    const int64_t gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-    const bool present = gx < nx && gy < ny && gz < nz;
-    const int64_t gidx = (gz * ny + gy) * nx + gx;
-
-    double tv = present ? ld_time(T + gidx) : from_bits(kInfBits);
-    const unsigned long long cv =
-        present ? static_cast<unsigned long long>(__ldg(reinterpret_cast<const long long *>(P.c) + gidx))
-                : kInfBits;
-    bool active = present;
-    if (p.tile_src[tile] && present && is_source(P, gidx)) active = false;
+    // this thread's cell from the tile's geometry: its global index, and
+    // whether it lies inside the grid
+    auto cell_of = [&](int64_t &gidx) -> bool {
+      const int64_t gx = s_tc[0] * TX + lx, gy = s_tc[1] * TY + ly, gz = s_tc[2] * TZ + lz;
+      gidx = (gz * s_n[1] + gy) * s_n[0] + gx;
+      return gx < s_n[0] && gy < s_n[1] && gz < s_n[2];
+    };
+    double tv;
+    unsigned long long cv;
+    bool active;
+    {
+      int64_t gidx;
+      const bool present = cell_of(gidx);
+      const Prob &P = p.probs[s_prob];
+      tv = present ? ld_time(s_T + gidx) : from_bits(kInfBits);
+      cv = present ? static_cast<unsigned long long>(__ldg(reinterpret_cast<const long long *>(P.c) + gidx))
+                   : kInfBits;
+      active = present && !(p.tile_src[tile] && is_source(P, gidx));
+    }
     s_c[tid] = cv;
     unsigned pword = 0;
     if (lane == 0) pword = ld_rlx(p.pend + static_cast<size_t>(tile) * kPendWords + warp);
@@ -578,6 +599,9 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     {
       constexpr int FX = TY * TZ, FY = TX * TZ, FZ = (D == 3) ? TX * TY : 0;
       constexpr int H = 2 * FX + 2 * FY + 2 * FZ;
+      const double *const T = s_T;
+      const int64_t nx = s_n[0], ny = s_n[1], nz = s_n[2];
+      const int64_t x0 = s_tc[0] * TX, y0 = s_tc[1] * TY, z0 = s_tc[2] * TZ;
 #pragma unroll 1
       for (int i = tid; i < H; i += NT) {
         int64_t hx, hy, hz;
@@ -614,7 +638,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     if (first && tid == 0) {   // band = k * sqrt(c_min) / sqrt(D): one cell's travel time
       const float cm = s_cmin < kInfBits ? xf::to_f(s_cmin) : 0.0f;
       // s_cmin is the smallest c (or r for the explicit roots): one cell's travel time
-      s_band_f = (update ? cm : sqrtf(cm)) * band_scale;
+      s_band_f = (update ? cm : sqrtf(cm)) * s_band_scale;
       s_cmin = kInfBits;
     }
     vlim = s_vlim;
@@ -844,12 +868,14 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
       if (lane == 0 && cm)
         atomicAdd(reinterpret_cast<unsigned long long *>(&s_stat[2]), static_cast<unsigned long long>(__popc(cm)));
     }
-    if (commit) {
+    if (commit) {   // a committed cell lies inside the grid
       const unsigned long long tb = bits_of(tv);
+      int64_t gidx;
+      cell_of(gidx);
       if (track)   // a value may rise: only this tile's visit writes its cells
-        st_rlx(reinterpret_cast<unsigned long long *>(T + gidx), tb);
+        st_rlx(reinterpret_cast<unsigned long long *>(s_T + gidx), tb);
       else
-        atomicMin(reinterpret_cast<unsigned long long *>(T + gidx), tb);
+        atomicMin(reinterpret_cast<unsigned long long *>(s_T + gidx), tb);
       // a face value can change the cell across the face only if it is below
       // that cell's value (causality; the loaded halo value is an upper bound).
       // Change tracking activates on any change.
@@ -869,15 +895,16 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
       const unsigned long long fm = s_facemin[tid];
       if (fm != kInfBits) {
         const int k = tid >> 1, side = tid & 1;
+        const int64_t tx = s_tc[0], ty = s_tc[1], tz = s_tc[2];
         int64_t ntx = tx, nty = ty, ntz = tz;
         bool exists;
-        if (k == 0) { ntx = side ? tx + 1 : tx - 1; exists = side ? (tx + 1 < P.ntx) : (tx > 0); }
-        else if (k == 1) { nty = side ? ty + 1 : ty - 1; exists = side ? (ty + 1 < P.nty) : (ty > 0); }
-        else { ntz = side ? tz + 1 : tz - 1; exists = side ? (tz + 1 < P.ntz) : (tz > 0); }
+        if (k == 0) { ntx = side ? tx + 1 : tx - 1; exists = side ? (tx + 1 < s_nt[0]) : (tx > 0); }
+        else if (k == 1) { nty = side ? ty + 1 : ty - 1; exists = side ? (ty + 1 < s_nt[1]) : (ty > 0); }
+        else { ntz = side ? tz + 1 : tz - 1; exists = side ? (tz + 1 < s_nt[2]) : (tz > 0); }
         if (exists) {
           const unsigned long long nt =
-              static_cast<unsigned long long>(P.tile_base + (ntz * P.nty + nty) * P.ntx + ntx);
-          activate(p, nt, 1u << (tid ^ 1), bucket_of_time(fm, inv_delta));
+              static_cast<unsigned long long>(s_tbase + (ntz * s_nt[1] + nty) * s_nt[0] + ntx);
+          activate(p, nt, 1u << (tid ^ 1), bucket_of_time(fm, s_inv_delta));
         }
       }
       __threadfence();
@@ -896,7 +923,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
       }
       if (!cont && m < kInfBits) {
         const unsigned lo2 = ld_rlx(&p.ctl->cur);
-        const unsigned long long v2 = bits_of(static_cast<double>(lo2 + p.window + 1u) * delta);
+        const unsigned long long v2 = bits_of(static_cast<double>(lo2 + p.window + 1u) * s_delta);
         if (m < v2) {
           cont = 2;
           s_faces = 0;
@@ -929,7 +956,7 @@ __global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
     if (tid == 0) {
       if (timing) lap(s_stat, 11);
       if (m < kInfBits) {   // deferred cells: come back at their bucket, beyond this window
-        unsigned b = bucket_of_time(m, inv_delta);
+        unsigned b = bucket_of_time(m, s_inv_delta);
         const unsigned bmin = s_lo + p.window + 1u;
         if (b < bmin) b = bmin;
         activate(p, static_cast<unsigned long long>(tile), 0u, b);
