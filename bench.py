@@ -54,17 +54,17 @@ L2_FLUSH_BYTES = 512 << 20
 # ncu DRAM bytes (read + write) per launch of the persistent kernel in its default
 # configuration (the instantiation the timed steps run), from the one-pass
 # captures summarised in profiles/ (refresh them whenever the kernel changes)
-MEASURED_TRAFFIC = {"layered_2d": 28197632 + 660480, "checker_3d": 283740928 + 117722880}
+MEASURED_TRAFFIC = {"layered_2d": 28089088 + 668416, "checker_3d": 283825920 + 117156352}
 # ncu DRAM bytes of one launch of the 88-problem batch in the default options
 # (the benchmark autotunes, so this is context, not the traffic of the timed launch)
-BATCH_TRAFFIC_DEFAULT_OPTIONS = 16184324096 + 2496584192
+BATCH_TRAFFIC_DEFAULT_OPTIONS = 16199321088 + 2499080704
 
 # FP64 thread instructions (DADD + DMUL + DFMA, ncu sass counters) per operator
 # evaluation of the persistent kernel, by dimension, from one-launch captures of
 # the counting instantiation (whose evaluation count comes from the same launch;
 # the timed instantiation runs the same d-bar code), summarised in profiles/
 # (refresh them whenever the kernel changes)
-MEASURED_FP64_PER_EVAL = {2: 8.048, 3: 12.971, "batched_3d": 12.717}
+MEASURED_FP64_PER_EVAL = {2: 8.031, 3: 12.982, "batched_3d": 12.717}
 
 WORKLOADS = {
     "layered_2d": "2d_2301x751_layered_h4_1src",

@@ -77,11 +77,13 @@ typedef enum {
  *     128 threads per SM;
  *   3D, fewer than 8 sources: 4x4x4 tiles, k_delta 0.75, window 31, band 6, 14 CTAs
  *     of 64 threads per SM;
- *   3D, 8 or more sources: 4x4x4 tiles, k_delta 0.375, window 31, band 6, 16 CTAs
- *     of 64 threads per SM.
+ *   3D, 8 or more sources: 4x4x4 tiles, k_delta 0.375, window 31, band 6, 20 CTAs
+ *     of 64 threads per SM (a lean build compiled for 20 CTAs; a solve that needs the
+ *     full build runs 16: counters, a trace, the update forms, change tracking, or
+ *     fewer than 8 tiles per CTA, where lists use lane groups).
  * (The per-CTA work is latency-bound, so the kernel is compiled for as many
  * resident CTAs as registers allow: 2 per SM for 256-cell tiles, 8 for 128-cell
- * tiles, 16 for 64-cell tiles.)
+ * tiles, 16 for 64-cell tiles, 20 for the wide lean build of 4x4x4 tiles.)
  * With arith = 2 the first shape (16x16, 8x8x4) and k_delta 16 (2D) / 2 (3D). */
 typedef struct {
     double delta;          /* bucket width in time units; <= 0: auto (k_delta * mean h/v) */

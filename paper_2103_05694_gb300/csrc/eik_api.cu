@@ -46,7 +46,7 @@ constexpr double kDefaultBand[2] = {16.0, 6.0};  // single 2D front, 3D (2D batc
 constexpr int kDefaultCtasPerSm[2] = {1, 2};   // per 256 cells of tile (single 2D front)
 // 3D on the FP64 unit: 4x4x4 tiles; a single front (under 8 sources) takes
 // buckets of 0.75 cell travel times and 14 CTAs of 64 cells per SM, many
-// fronts (a batch) buckets of 0.375 and all 16 CTAs that fit.  A single
+// fronts (a batch) buckets of 0.375 and the 20 CTAs of the wide lean build.  A single
 // front's extra CTAs pick up tiles ahead of it and redo them; a batch has
 // enough independent fronts to keep them busy, and narrow buckets cut its
 // speculative evaluations.
@@ -422,8 +422,10 @@ int lane_group_cells(const eik_opts *opts, int64_t tile_cells, int64_t total_til
 // tiles, scaled up for smaller tiles.  A 2D batch with many sources has as
 // many independent wavefronts, enough work for two CTAs per SM (the 32-source
 // 1024^2 tomography forward: 75 ms against 93 ms with one); a single front
-// runs faster with one.
-int default_ctas_per_sm(int di, int64_t tile_cells, int64_t total_sources) {
+// runs faster with one.  wide_occ: resident CTAs per SM of the shape's wide
+// lean build (0: none), which many fronts fill (the 88-problem 3D batch:
+// 110.9 ms at 20 CTAs per SM against 112.8 ms at 16).
+int default_ctas_per_sm(int di, int64_t tile_cells, int64_t total_sources, int wide_occ) {
   // one 2D front is latency-bound on few tiles: one CTA per SM; otherwise as
   // many CTAs as the register budget of the tile size allows
   if (di == 0 && total_sources < kManyFronts)
@@ -431,7 +433,38 @@ int default_ctas_per_sm(int di, int64_t tile_cells, int64_t total_sources) {
   // one 3D front on 64-cell tiles: a little short of the register budget
   if (di == 1 && total_sources < kManyFronts && tile_cells <= 64)
     return std::min(kSingleFrontCtas3Small, eik::resident_ctas((int)tile_cells));
+  if (total_sources >= kManyFronts && wide_occ > 0) return wide_occ;
   return eik::resident_ctas((int)tile_cells);
+}
+
+// Persistent grid of a launch: the CTAs per SM requested (else the default),
+// capped by what the instantiation to launch holds resident, so that every
+// CTA is resident.  More CTAs than the normal build holds take the wide lean
+// build where the shape has one and the launch is lean (every other field of
+// sp already set); else the normal build's count.  Sets sp.lane_group_cells
+// and sp.wide.
+int64_t size_grid(SolveParams &sp, const eik_opts *opts, int ndim, int shape, int64_t tile_cells,
+                  int64_t total_sources, int64_t total_tiles, int sms) {
+  const int occ = eik::persistent_blocks_per_sm(ndim, sp.arith, shape);
+  const int occ_wide = eik::persistent_wide_blocks_per_sm(ndim, sp.arith, shape);
+  const int per_sm = opts && opts->ctas_per_sm > 0
+                         ? opts->ctas_per_sm
+                         : default_ctas_per_sm(ndim == 3 ? 1 : 0, tile_cells, total_sources, occ_wide);
+  auto grid_of = [&](int per) {
+    return std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per, total_tiles));
+  };
+  sp.wide = 0;
+  int64_t grid = grid_of(std::min(per_sm, std::max(occ, occ_wide)));
+  sp.lane_group_cells = lane_group_cells(opts, tile_cells, total_tiles, grid);
+  if (per_sm > occ) {
+    if (occ_wide > 0 && eik::persistent_launch_is_lean(sp)) {
+      sp.wide = 1;
+    } else {
+      grid = grid_of(occ);
+      sp.lane_group_cells = lane_group_cells(opts, tile_cells, total_tiles, grid);
+    }
+  }
+  return grid;
 }
 
 // Select the current device's workspaces for the call in progress.
@@ -726,7 +759,6 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
   sp.state = ws().state.p;
   sp.tile_src = ws().tile_src.p;
   sp.pend = ws().pend.p;
-  const int di = ndim == 3 ? 1 : 0;
   const AutoCfg ac = auto_config(ndim, total_src, opts && opts->arith == 2);
   sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : ac.window);
   sp.band = opts && opts->band > 0 ? opts->band : ac.band;
@@ -752,16 +784,9 @@ eik_status run(std::vector<HostProblem> &hps, const eik_opts *opts, eik_stats *s
 
   CK(eik::launch_seed(sp, ws().seeds.p, (int64_t)seeds.size(), k_delta, delta_fixed, stream),
      "seed launch");
-  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm
-                                             : default_ctas_per_sm(di, tx * ty * tz, total_src);
-  const int occ = eik::persistent_blocks_per_sm(ndim, sp.arith, shape);
-  if (per_sm > occ) per_sm = occ;
   int dev_sms = 0;
   CK(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, ws().device), "SM count");
-  int64_t grid = (int64_t)dev_sms * per_sm;
-  if (grid > total_tiles) grid = total_tiles;
-  if (grid < 1) grid = 1;
-  sp.lane_group_cells = lane_group_cells(opts, tx * ty * tz, total_tiles, grid);
+  const int64_t grid = size_grid(sp, opts, ndim, shape, tx * ty * tz, total_src, total_tiles, dev_sms);
 
   eik_stats acc;
   std::memset(&acc, 0, sizeof(acc));
@@ -1045,8 +1070,9 @@ eik_status eik_autotune(const eik_problem *probs, int nprob, const eik_opts *bas
       if (st != EIK_OK) break;
     }
     {
-      const int occ = eik::persistent_blocks_per_sm(ndim, int_arith ? eik::kArithInt : eik::kArithFp64,
-                                                    cur.tile - 1);
+      const int ar = int_arith ? eik::kArithInt : eik::kArithFp64;
+      const int occ = std::max(eik::persistent_blocks_per_sm(ndim, ar, cur.tile - 1),
+                               eik::persistent_wide_blocks_per_sm(ndim, ar, cur.tile - 1));
       const int c0 = cur.ctas_per_sm;
       for (int c = 1; c <= occ; ++c) {
         if (c == c0) continue;
@@ -1542,7 +1568,6 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   sp.timeout_ns = tmo_ms * 1000000ll;
   sp.counters = opts ? opts->counters : 0;
   sp.test_stall = 0;
-  const int di = pl.ndim == 3 ? 1 : 0;
   const AutoCfg ac = auto_config(pl.ndim, count_sources(hps), opts && opts->arith == 2);
   sp.window = (unsigned)(opts && opts->window > 0 ? opts->window : ac.window);
   sp.band = opts && opts->band > 0 ? opts->band : ac.band;
@@ -1557,16 +1582,9 @@ eik_status plan_build(eik_plan &pl, std::vector<HostProblem> &hps, const eik_opt
   pl.k_delta = opts && opts->k_delta > 0 ? opts->k_delta : ac.k_delta;
   pl.delta_fixed = opts && opts->delta > 0 ? opts->delta : 0.0;
   pl.from_slowness = from_slowness(opts);
-  int per_sm = opts && opts->ctas_per_sm > 0 ? opts->ctas_per_sm
-                                             : default_ctas_per_sm(di, tx * ty * tz, pl.nseeds);
-  const int occ = eik::persistent_blocks_per_sm(pl.ndim, sp.arith, shape);
-  if (per_sm > occ) per_sm = occ;
   int sms = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl.device), "SM count");
-  int64_t grid = (int64_t)sms * per_sm;
-  if (grid > pl.total_tiles) grid = pl.total_tiles;
-  pl.grid = (int)std::max<int64_t>(grid, 1);
-  sp.lane_group_cells = lane_group_cells(opts, tx * ty * tz, pl.total_tiles, pl.grid);
+  pl.grid = (int)size_grid(sp, opts, pl.ndim, shape, tx * ty * tz, pl.nseeds, pl.total_tiles, sms);
   return EIK_OK;
 }
 

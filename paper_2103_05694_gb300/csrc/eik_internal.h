@@ -110,6 +110,8 @@ struct SolveParams {
   int lane_group_cells;           // lists of at most this many cells use lane groups (0: never)
   struct TraceRec *trace;         // optional visit trace (device), NULL when off
   unsigned long long trace_cap;
+  int wide;                       // lean launches of 4x4x4 3D tiles: the build compiled for
+                                  // EIK_WIDE_CTAS_64 CTAs per SM (fewer registers)
 };
 
 // One tile visit, for timeline analysis (opts.trace).
@@ -137,6 +139,11 @@ constexpr int kNumTileShapes = 5;
 #endif
 #ifndef EIK_MIN_CTAS_64
 #define EIK_MIN_CTAS_64 16
+#endif
+// The lean 3D 4x4x4 kernel also has a wide build, compiled for more resident
+// CTAs per SM with fewer registers: a batch of many fronts keeps them busy.
+#ifndef EIK_WIDE_CTAS_64
+#define EIK_WIDE_CTAS_64 20
 #endif
 constexpr int resident_ctas(int tile_cells) {
   return tile_cells >= 256 ? EIK_MIN_CTAS_256 : tile_cells >= 128 ? EIK_MIN_CTAS_128 : EIK_MIN_CTAS_64;
@@ -213,6 +220,10 @@ cudaError_t launch_checksum_all(const Prob *dev_probs, int nprob, int64_t max_ce
 void note_launches(unsigned long long n);
 unsigned long long kernel_launches();
 int persistent_blocks_per_sm(int ndim, int arith, int tile_shape);
+// Resident CTAs per SM of the shape's wide lean build; 0 when it has none.
+int persistent_wide_blocks_per_sm(int ndim, int arith, int tile_shape);
+// Whether launch_persistent runs the lean instantiation for these parameters.
+bool persistent_launch_is_lean(const SolveParams &p);
 
 // Other schedules of the same update (eik_schedules.cu): opts.schedule.
 constexpr int kScheduleAmm = 0, kScheduleFim = 1, kScheduleTopo = 2, kScheduleFsm = 3;

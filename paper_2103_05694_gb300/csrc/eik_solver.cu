@@ -423,10 +423,12 @@ __device__ __forceinline__ bool is_source(const Prob &P, int64_t idx) {
 // + 1) * delta are deferred: recorded in the tile's pending mask and the tile
 // re-queued at their bucket.  Only accepted values are written to memory.
 // ---------------------------------------------------------------------------
-// Register budget: resident_ctas(tile cells) CTAs per SM.
-template <int D, int TX, int TY, int TZ, int ARITH, bool LEAN>
-__global__ void __launch_bounds__(TX * TY * TZ, resident_ctas(TX * TY * TZ))
+// Register budget: resident_ctas(tile cells) CTAs per SM; the wide build of a
+// lean 64-cell kernel, EIK_WIDE_CTAS_64.
+template <int D, int TX, int TY, int TZ, int ARITH, bool LEAN, bool WIDE = false>
+__global__ void __launch_bounds__(TX * TY * TZ, WIDE ? EIK_WIDE_CTAS_64 : resident_ctas(TX * TY * TZ))
     persistent_kernel(SolveParams p) {
+  static_assert(!WIDE || (LEAN && TX * TY * TZ == 64), "wide builds: lean 64-cell kernels only");
   // LEAN: the instantiation for plain d-bar solves without counters, traces,
   // lane groups or change tracking (the timed path); those features compile
   // out of it.
@@ -1353,8 +1355,22 @@ cudaError_t launch_reseed(const SolveParams &p, const Prob *host_probs, int npro
 
 // Launch / occupancy per (dimension, shape, arithmetic).  The integer-pipe
 // arithmetic exists for the default shapes only.
-template <int D, int TX, int TY, int TZ, bool WithInt>
+bool persistent_launch_is_lean(const SolveParams &p) {
+  return p.arith != kArithInt && p.counters == 0 && p.update == 0 && !p.track_changes &&
+         p.lane_group_cells == 0 && p.trace == nullptr && p.visit_budget == 0ull;
+}
+
+template <int D, int TX, int TY, int TZ, bool WithInt, bool Wide = false>
 struct ShapeOps {
+  static int wide_blocks_per_sm(int arith) {
+    int nb = 0;
+    if constexpr (Wide) {
+      if (arith == kArithFp64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &nb, persistent_kernel<D, TX, TY, TZ, kArithFp64, true, true>, TX * TY * TZ, 0);
+    }
+    return nb;
+  }
   static int blocks_per_sm(int arith) {
     int nb = 0;
     if constexpr (WithInt) {
@@ -1377,11 +1393,15 @@ struct ShapeOps {
         return cudaErrorInvalidValue;
       }
     }
-    const bool lean = p.counters == 0 && p.update == 0 && !p.track_changes &&
-                      p.lane_group_cells == 0 && p.trace == nullptr && p.visit_budget == 0ull;
-    if (lean)
+    if (persistent_launch_is_lean(p)) {
+      if constexpr (Wide) {
+        if (p.wide) {
+          persistent_kernel<D, TX, TY, TZ, kArithFp64, true, true><<<grid, TX * TY * TZ, 0, stream>>>(p);
+          return cudaGetLastError();
+        }
+      }
       persistent_kernel<D, TX, TY, TZ, kArithFp64, true><<<grid, TX * TY * TZ, 0, stream>>>(p);
-    else
+    } else
       persistent_kernel<D, TX, TY, TZ, kArithFp64, false><<<grid, TX * TY * TZ, 0, stream>>>(p);
     return cudaGetLastError();
   }
@@ -1394,7 +1414,7 @@ struct ShapeOps {
         case 1: { using S = ShapeOps<3, 16, 4, 4, false>; CALL; } break;     \
         case 2: { using S = ShapeOps<3, 32, 4, 2, false>; CALL; } break;     \
         case 3: { using S = ShapeOps<3, 8, 4, 4, false>; CALL; } break;      \
-        case 4: { using S = ShapeOps<3, 4, 4, 4, false>; CALL; } break;      \
+        case 4: { using S = ShapeOps<3, 4, 4, 4, false, true>; CALL; } break; \
         default: { using S = ShapeOps<3, kTX3, kTY3, kTZ3, true>; CALL; }    \
       }                                                                      \
     } else {                                                                 \
@@ -1412,6 +1432,12 @@ int persistent_blocks_per_sm(int ndim, int arith, int tile_shape) {
   int nb = 0;
   EIK_SHAPE_SWITCH(ndim, tile_shape, nb = S::blocks_per_sm(arith));
   return nb > 0 ? nb : 1;
+}
+
+int persistent_wide_blocks_per_sm(int ndim, int arith, int tile_shape) {
+  int nb = 0;
+  EIK_SHAPE_SWITCH(ndim, tile_shape, nb = S::wide_blocks_per_sm(arith));
+  return nb > 0 ? nb : 0;
 }
 
 cudaError_t launch_persistent(const SolveParams &p, int grid, cudaStream_t stream) {

@@ -87,14 +87,20 @@ def test_bad_tile_is_einval(opts):
 
 def test_default_launch_configuration_3d():
     """3D defaults: 4x4x4 tiles; one front (under 8 sources) on 14 CTAs per SM,
-    many fronts on the 16 that fit; the same bits as an explicit 8x4x4 solve."""
+    many fronts on the 20 of the wide lean build; a counting solve of many
+    fronts on the 16 the counting build holds; the same bits as an explicit
+    8x4x4 solve."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    for n_src, per_sm in ((1, 14), (8, 16)):
-        p = synth.random_problem(900 + n_src, (64, 64, 64), n_src=n_src, contrast=6.0)
+    for n_src, per_sm in ((1, 14), (8, 20)):
+        # 32,768 tiles: at least 8 per CTA, so no lane groups and the lean build
+        p = synth.random_problem(900 + n_src, (128, 128, 128), n_src=n_src, contrast=6.0)
         speed = torch.from_numpy(np.ascontiguousarray(p.speed)).to(DEV)
         src = torch.from_numpy(p.sources).to(DEV)
         r = eik.solve(speed, p.h, src)
-        assert r.stats["ctas"] == min(per_sm * sms, 16 ** 3), (n_src, r.stats["ctas"])
+        assert r.stats["ctas"] == per_sm * sms, (n_src, r.stats["ctas"])
         r2 = eik.solve(speed, p.h, src, opts={"tile": 4})
-        assert r2.stats["ctas"] == min(8 * sms, 16 * 16 * 8)
+        assert r2.stats["ctas"] == 8 * sms
         _bits_equal(r.t.cpu().numpy(), r2.t.cpu().numpy(), f"{n_src} sources")
+        r3 = eik.solve(speed, p.h, src, opts={"counters": 1})
+        assert r3.stats["ctas"] == min(per_sm, 16) * sms
+        _bits_equal(r.t.cpu().numpy(), r3.t.cpu().numpy(), f"{n_src} sources, counting")
