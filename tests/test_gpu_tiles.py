@@ -104,3 +104,11 @@ def test_default_launch_configuration_3d():
         r3 = eik.solve(speed, p.h, src, opts={"counters": 1})
         assert r3.stats["ctas"] == min(per_sm, 16) * sms
         _bits_equal(r.t.cpu().numpy(), r3.t.cpu().numpy(), f"{n_src} sources, counting")
+        # an explicit request above the normal build's 16 takes the wide build
+        # (lean) or is capped at 16 (counting)
+        r4 = eik.solve(speed, p.h, src, opts={"ctas_per_sm": 18})
+        assert r4.stats["ctas"] == 18 * sms
+        r5 = eik.solve(speed, p.h, src, opts={"ctas_per_sm": 18, "counters": 1})
+        assert r5.stats["ctas"] == 16 * sms
+        _bits_equal(r.t.cpu().numpy(), r4.t.cpu().numpy(), f"{n_src} sources, 18 CTAs per SM")
+        _bits_equal(r.t.cpu().numpy(), r5.t.cpu().numpy(), f"{n_src} sources, 18 CTAs per SM, counting")
