@@ -602,7 +602,9 @@ def run_batched(args, C, wl_name):
     from paper_2103_05694_gb300 import shard
     torch, eik = C.torch, C.eik
     n = args.gpus
-    n_all = 88
+    n_all = args.problems if args.problems > 0 else 88
+    if args.problems > 0:
+        wl_name = f"{wl_name}_first{n_all}"
     mine = shard.problem_shard(n_all, args.rank, n)
     model = synth.smooth_model_3d_128()
     probs = [synth.batched_3d_item(i, model) for i in mine]
@@ -684,7 +686,8 @@ def run_batched(args, C, wl_name):
                                  bad=st["decreases"] - st["good"])
     line["roofline"] = roofline(useful_mine, statistics.mean(solve_ms), args.traffic_bytes,
                                 "persistent_kernel (all problems in one launch)")
-    line["roofline"]["traffic_default_options"] = BATCH_TRAFFIC_DEFAULT_OPTIONS
+    if args.problems == 0:
+        line["roofline"]["traffic_default_options"] = BATCH_TRAFFIC_DEFAULT_OPTIONS
     line["roofline_fp64"] = roofline_fp64(C, st["evals"], statistics.mean(solve_ms), 3,
                                           line["roofline"]["kernel"], "batched_3d")
     line["e2e"] = {"value": useful_all / (e2e_ms / 1e3), "unit": UNIT, "ms_per_step": e2e_ms,
@@ -836,6 +839,9 @@ def main():
     ap.add_argument("--upsample", type=int, default=1,
                     help="2D single grids: nearest-neighbour upsampling by this factor per axis, "
                          "spacing h / factor (Table 3's input scale)")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="batched_3d only: the first N of the 88 problems (profiling cases; "
+                         "no CPU baseline); 0: all")
     ap.add_argument("--sources", type=int, default=0,
                     help="tomography_2d only: use the first N sources (profiling cases)")
     ap.add_argument("--k-delta", type=float, default=0.0)
@@ -862,6 +868,8 @@ def main():
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="ncu dram bytes per launch of the solve kernel, if measured")
     args = ap.parse_args()
+    if args.problems and (args.workload != "batched_3d" or not 0 < args.problems <= 88):
+        raise SystemExit("--problems takes 1..88 and applies to batched_3d only")
     args.rank = int(os.environ.get("RANK", "0"))
     if args.autotune is None:
         args.autotune = args.workload == "batched_3d"
@@ -883,7 +891,7 @@ def main():
         line = run_batched(args, C, wl_name)
     else:
         line = run_tomography(args, C, wl_name)
-    if args.rank == 0 and args.gpus == 1 and not args.no_cpu_baseline:
+    if args.rank == 0 and args.gpus == 1 and not args.no_cpu_baseline and args.problems == 0:
         line["cpu_baseline"] = cpu_baseline(args)
         if args.workload in ("batched_3d", "tomography_2d"):
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(
