@@ -90,7 +90,9 @@ typedef struct {
     double k_delta;        /* auto bucket width in cell travel times; <= 0: default (above) */
     int64_t capacity;      /* initial frontier ring capacity per bucket slot; 0: auto */
     int64_t timeout_ms;    /* limit of any single device wait; 0: 60000 */
-    int ctas_per_sm;       /* persistent CTAs per SM (capped by occupancy); 0: default */
+    int ctas_per_sm;       /* persistent CTAs per SM, capped by what the launched build holds
+                              resident (above; above 16, 4x4x4 3D tiles take the wide lean
+                              build when the solve is lean); 0: default */
     int counters;          /* nonzero: collect eik_stats counters (small cost) */
     int test_stall;        /* testing aid, keep 0: the solve first waits on a device flag
                               that nothing sets, so the wait reaches timeout_ms and the
