@@ -55,6 +55,15 @@ def test_command_line_options():
     assert bench.make_opts(ns) == {}
 
 
+@pytest.mark.parametrize("argv", [["--problems", "89"], ["--problems", "-1"],
+                                  ["--workload", "checker_3d", "--problems", "4"]])
+def test_reduced_batch_option_is_checked(argv, monkeypatch):
+    """--problems takes 1..88 and the batch only; it stops before any GPU work."""
+    monkeypatch.setattr(sys, "argv", ["bench.py"] + argv)
+    with pytest.raises(SystemExit, match="--problems takes 1..88"):
+        bench.main()
+
+
 @pytest.mark.slow
 def test_all_cores_oracle_baseline_runs_every_core():
     """One spawned process per host core solves its share of the tomography
